@@ -1,0 +1,79 @@
+/*
+ * vegas_oracle.h -- plain FP64 CPU oracle for one VEGAS importance-sampling
+ * iteration, the method the paper builds on (Sec. 1 names VEGAS, Lepage 1978
+ * and 1980; Sec. 3 and Sec. 3.2 describe the iterate -> refine loop).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load this library.  It shares no code,
+ * header, table or helper with the CUDA library; the two are written
+ * independently and compared.
+ *
+ * Everything is double precision, computed in the order the algorithm
+ * states, with no blocking or reordering beyond a plain loop over samples.
+ */
+#ifndef VEGAS_ORACLE_H
+#define VEGAS_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Integrand families (oracle's own numbering; tests map them by name). */
+enum {
+    ORACLE_F_CONST = 0,     /* f = 1                                         */
+    ORACLE_F_SUM = 1,       /* f = sum_i x_i   (the toy of Sec. 3.1)          */
+    ORACLE_F_GAUSS_SYM = 2, /* f = (a sqrt(pi))^-d exp(-sum (x_i-1/2)^2/a^2)  */
+    ORACLE_F_GENZ_OSC = 3,  /* f = cos(2 pi u + sum c_i x_i)                  */
+    ORACLE_F_GENZ_GAUSS = 4,/* f = exp(-sum c_i^2 (x_i - w_i)^2)              */
+    ORACLE_F_GENZ_PROD = 5, /* f = prod (c_i^-2 + (x_i - w_i)^2)^-1           */
+    ORACLE_F_GENZ_CORNER = 6,/* f = (1 + sum c_i x_i)^-(d+1)                  */
+    ORACLE_F_LO = 7         /* LO-style 2->2 toy, d = 3 (see the .c file)     */
+};
+
+/* Philox4x32-10 block function (Salmon, Moraes, Dror, Shaw, SC'11). */
+void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+/* Uniform u32 draw r_j of sample s, dimension j, iteration t:
+ * ctr = (s_lo, s_hi, t, j/4), key = (seed, integral_id), word j%4. */
+uint32_t oracle_draw(uint64_t s, uint32_t t, int j, uint32_t seed, uint32_t integral_id);
+
+/* FP64 integrand value at point x[d]. Returns 0 for an unknown family. */
+double oracle_integrand(int family, int d, const double *params, int n_params, const double *x);
+
+/* Number of parameters a family takes for dimension d (-1: unknown family). */
+int oracle_n_params(int family, int d);
+
+/* One sample: bins[d], x[d], Jacobian J, f(x). edges: d rows of N+1. */
+void oracle_sample(int d, int N, const double *edges, int family, const double *params,
+                   int n_params, uint32_t seed, uint32_t integral_id, uint32_t t,
+                   uint64_t s, int32_t *bins, double *x, double *J, double *f);
+
+/* Accumulate samples s in [s_begin, s_end) of iteration t into
+ * *S1 += v, *S2 += v^2, hist[j*N + i_j] += v^2 (v = J f).  Non-finite v are
+ * counted in *n_nonfinite and skipped.  cnt (may be NULL) gets per-bin
+ * sample counts, cnt[j*N + i] += 1. */
+void oracle_iterate(int d, int N, const double *edges, int family, const double *params,
+                    int n_params, uint32_t seed, uint32_t integral_id, uint32_t t,
+                    int64_t s_begin, int64_t s_end, double *S1, double *S2, double *hist,
+                    int64_t *cnt, int64_t *n_nonfinite);
+
+/* Iteration estimate: I = S1/n, var = (S2/n - I^2)/(n-1) (clamped at 0). */
+void oracle_iteration_result(double S1, double S2, int64_t n, double *I, double *var);
+
+/* Grid refinement of every dimension (smooth, normalise, compress with
+ * exponent alpha, rebin to N equal-weight bins).  hist: d rows of N;
+ * edges_in/edges_out: d rows of N+1.  smooth != 0 enables the 3-point
+ * smoothing.  A dimension whose weights sum to zero keeps its old edges. */
+void oracle_refine(int d, int N, const double *hist, const double *edges_in, double alpha,
+                   int smooth, double *edges_out);
+
+/* Inverse-variance combination of m iteration results. */
+void oracle_combine(int m, const double *I, const double *sigma, double *Ibar, double *sbar,
+                    double *chi2_dof);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
