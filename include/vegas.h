@@ -1,0 +1,212 @@
+/*
+ * vegas.h -- C ABI of the GB300 (sm_103a) VEGAS iteration library.
+ *
+ * The method is VEGAS adaptive importance sampling (Lepage 1978, 1980), which
+ * the paper takes as the algorithm of VegasFlow (Sec. 1).  The calls follow the
+ * paper's statement of an integration (Sec. 3.1): an integrand over the unit
+ * hypercube of n_dim dimensions, n_events samples per iteration, an
+ * events_limit per device batch, and run_integration(n_iter) = n_iter rounds
+ * of iterate -> refine, whose per-iteration results are combined.  Each
+ * iteration informs the grid of the next (Sec. 3.2).
+ *
+ * One iteration t of an integral with d dimensions and N bins per dimension:
+ *   for s in [0, n):  r_j = Philox4x32-10(ctr = (s_lo, s_hi, t, j/4),
+ *                                         key = (seed, integral_id))[j % 4]
+ *                     i_j = (r_j * N) >> 32         (64-bit integer product)
+ *                     y_j = low 32 bits of r_j * N, times 2^-32
+ *                     x_j = e_j[i_j] + (e_j[i_j+1] - e_j[i_j]) * y_j
+ *                     J   = prod_j N (e_j[i_j+1] - e_j[i_j])
+ *                     v   = J f(x);  S1 += v; S2 += v^2; h_j[i_j] += v^2
+ *   I_t = S1/n,  sigma_t^2 = (S2/n - I_t^2)/(n - 1)
+ * Refinement per dimension: 3-point smoothing of h_j, normalisation,
+ * compression rho = ((1 - d)/ln(1/d))^alpha, rebinning to N bins of equal
+ * rho-weight.  Combination: inverse-variance weighted mean, sigma, chi^2/dof.
+ *
+ * Conventions for every call:
+ *   - Every call returns a vegas_status; nothing throws across the ABI.
+ *   - Pointers named dev_* are CUDA device pointers; all others are host.
+ *   - A context owns no device memory: the caller allocates the workspace
+ *     (vegas_workspace_bytes) and keeps it alive until vegas_destroy.  It
+ *     owns a small host-side struct only.
+ *   - All device work is enqueued on the caller's stream, in stream order.
+ *     Calls that return host values synchronise that stream.
+ *   - A context must not be used from two threads at once.
+ *   - VEGAS_ECUDA: a CUDA runtime call failed; vegas_last_error_string()
+ *     gives the CUDA error text.
+ */
+#ifndef VEGAS_GB300_H
+#define VEGAS_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    VEGAS_OK = 0,
+    VEGAS_EINVAL = 1,     /* invalid argument or configuration               */
+    VEGAS_ENOMEM = 2,     /* workspace too small                              */
+    VEGAS_ECUDA = 3,      /* a CUDA runtime call failed                       */
+    VEGAS_ETIMEOUT = 4,   /* a bounded device wait ran out                    */
+    VEGAS_EBUSY = 5,      /* no free slot (batched form)                      */
+    VEGAS_ENONFINITE = 6  /* every integrand value of the iteration was non-finite */
+} vegas_status;
+
+/* Arithmetic of the sampling path.
+ *   VEGAS_FP64       : uniforms, grid map, Jacobian, integrand and all sums in FP64.
+ *   VEGAS_FP32_ACC64 : map, Jacobian and integrand in FP32; per-thread sums of
+ *                      v and v^2 in FP64; histograms in FP64 shared memory.
+ *   VEGAS_FP32_KAHAN : map, Jacobian and integrand in FP32; per-thread sums of
+ *                      v and v^2 Kahan-compensated FP32; histograms in FP32
+ *                      shared memory (bounded depth per cell) promoted to FP64
+ *                      once per block.
+ * Refinement and the combination of iterations are FP64 in every mode. */
+typedef enum {
+    VEGAS_FP64 = 0,
+    VEGAS_FP32_ACC64 = 1,
+    VEGAS_FP32_KAHAN = 2
+} vegas_precision;
+
+/* Built-in integrand families over [0,1]^d, parameters as FP64 arrays:
+ *   CONST        f = 1                                   params: none
+ *   SUM          f = sum_i x_i (the toy integrand of Sec. 3.1)   none
+ *   GAUSS_SYM    f = (a sqrt(pi))^-d exp(-sum (x_i - 1/2)^2 / a^2)   [a]
+ *   GENZ_OSC     f = cos(2 pi u + sum c_i x_i)           [u, c_1..c_d]
+ *   GENZ_GAUSS   f = exp(-sum c_i^2 (x_i - w_i)^2)       [c_1..c_d, w_1..w_d]
+ *   GENZ_PROD    f = prod (c_i^-2 + (x_i - w_i)^2)^-1    [c_1..c_d, w_1..w_d]
+ *   GENZ_CORNER  f = (1 + sum c_i x_i)^-(d+1)            [c_1..c_d]
+ *   LO           d = 3 LO-style 2->2 toy: x1, x2 momentum fractions with
+ *                density g(x) = (35/32) x^-1/2 (1-x)^3, c = 2 x3 - 1,
+ *                shat = x1 x2 sqrtS^2, f = g(x1) g(x2) BW(shat) (1+c^2)/shat * 2 * norm
+ *                with BW = 1/((shat - M^2)^2 + M^2 Gamma^2), |c| < cut and
+ *                mll_lo <= sqrt(shat) <= mll_hi.
+ *                params: [sqrtS, M, Gamma, cut, mll_lo, mll_hi, norm]
+ * The paper's integrand is a user function of the sample array (Sec. 3.1);
+ * these families stand in for it. */
+typedef enum {
+    VEGAS_F_CONST = 0,
+    VEGAS_F_SUM = 1,
+    VEGAS_F_GAUSS_SYM = 2,
+    VEGAS_F_GENZ_OSC = 3,
+    VEGAS_F_GENZ_GAUSS = 4,
+    VEGAS_F_GENZ_PROD = 5,
+    VEGAS_F_GENZ_CORNER = 6,
+    VEGAS_F_LO = 7
+} vegas_family;
+
+#define VEGAS_MAX_DIM 32
+#define VEGAS_MAX_BINS 1024
+#define VEGAS_MAX_ITERS 4096
+
+typedef struct {
+    int32_t family;         /* vegas_family                                   */
+    int32_t n_dim;          /* must equal vegas_config.n_dim                  */
+    const double *params;   /* host array, n_params values, copied at create  */
+    int32_t n_params;       /* exactly the count the family takes             */
+} vegas_integrand;
+
+typedef struct {
+    int32_t n_dim;          /* d, 1..VEGAS_MAX_DIM (Sec. 3.1: n_dim)          */
+    int32_t n_bins;         /* N, 2..VEGAS_MAX_BINS                           */
+    int64_t n_events;       /* n samples per iteration, >= 2 (Sec. 3.1)       */
+    int64_t events_limit;   /* max samples per kernel launch; <= 0: no limit
+                               (Sec. 3.1: events_limit).  Samples are made on
+                               the device, so this only splits launches.     */
+    double alpha;           /* grid compression exponent, >= 0                */
+    uint32_t seed;          /* Philox key word 0                              */
+    uint32_t integral_id;   /* Philox key word 1                              */
+    int32_t precision;      /* vegas_precision                                */
+    int32_t smooth;         /* 1: 3-point smoothing before compression        */
+} vegas_config;
+
+typedef struct {
+    double I;               /* iteration estimate                             */
+    double sigma;           /* its standard error                             */
+    int64_t n;              /* samples with finite weight                     */
+    int64_t n_nonfinite;    /* samples skipped because v was NaN or Inf       */
+} vegas_iter_result;
+
+typedef struct {
+    double I;               /* combined estimate over all iterations so far   */
+    double sigma;           /* combined standard error                        */
+    double chi2_dof;        /* chi^2 per degree of freedom (0 for one iteration) */
+    int32_t n_iter;         /* iterations combined                            */
+    int32_t reserved;
+} vegas_result_t;
+
+typedef struct vegas_ctx vegas_ctx;
+
+/* Bytes of device workspace a context with this configuration needs
+ * (0 if the configuration is invalid).  The caller allocates it, 256-byte
+ * aligned, and passes it to vegas_create. */
+size_t vegas_workspace_bytes(const vegas_config *cfg);
+
+/* Validate cfg and integrand, lay out the workspace, upload the uniform grid
+ * e_j[k] = k/N and the parameters, zero the accumulators.  stream: a
+ * cudaStream_t (NULL = legacy default stream).  On success *out owns a host
+ * struct that vegas_destroy frees.  EINVAL for a bad configuration or
+ * parameter count, ENOMEM if ws_bytes is below vegas_workspace_bytes. */
+vegas_status vegas_create(const vegas_config *cfg, const vegas_integrand *integrand,
+                          void *stream, void *dev_workspace, size_t ws_bytes, vegas_ctx **out);
+
+/* Run one iteration on the current grid: sample, accumulate S1, S2 and the
+ * histograms, then form I_t, sigma_t and update the combination on the
+ * device.  Asynchronous if out == NULL; otherwise synchronises the stream and
+ * fills *out.  ENONFINITE (with *out filled) if no sample had a finite weight. */
+vegas_status vegas_iterate(vegas_ctx *ctx, vegas_iter_result *out);
+
+/* Refine the grid from the last iteration's histograms (asynchronous). */
+vegas_status vegas_refine(vegas_ctx *ctx);
+
+/* Synchronise the stream and return the combination of all iterations run. */
+vegas_status vegas_result(vegas_ctx *ctx, vegas_result_t *out);
+
+/* run_integration of Sec. 3.1: n_iter rounds of iterate + refine (no refine
+ * after the last), then vegas_result.  iters (may be NULL) receives n_iter
+ * per-iteration results. */
+vegas_status vegas_run(vegas_ctx *ctx, int32_t n_iter, vegas_iter_result *iters,
+                       vegas_result_t *out);
+
+/* Grid access (host arrays of d rows of N+1 FP64 edges).  set_grid checks
+ * that each row starts at 0, ends at 1 and does not decrease (EINVAL). */
+vegas_status vegas_get_grid(vegas_ctx *ctx, double *edges_host);
+vegas_status vegas_set_grid(vegas_ctx *ctx, const double *edges_host);
+
+/* The last iteration's FP64 sums, host array of 2 + d*N values:
+ * [S1, S2, h_0[0..N-1], ..., h_{d-1}[0..N-1]].  Synchronises the stream. */
+vegas_status vegas_get_sums(vegas_ctx *ctx, double *sums_host);
+
+/* Iteration counter t (the Philox counter word 2 of the next iteration). */
+vegas_status vegas_get_iteration(vegas_ctx *ctx, int32_t *t);
+vegas_status vegas_set_iteration(vegas_ctx *ctx, int32_t t);
+
+/* Per-sample view of iteration t on the current grid, for samples
+ * [s_begin, s_begin + count): dev_bins (int32, count x d, row-major),
+ * dev_x (FP64, count x d) and dev_w (FP64, count: v = J f before any
+ * scaling).  Any output pointer may be NULL.  Computed by the same device
+ * code as vegas_iterate, in the context's precision.  Asynchronous. */
+vegas_status vegas_trace(vegas_ctx *ctx, int32_t t, int64_t s_begin, int64_t count,
+                         int32_t *dev_bins, double *dev_x, double *dev_w);
+
+/* Checkpoint: a byte blob holding config, parameters, FP64 grid, iteration
+ * counter and per-iteration results.  export with buf == NULL sets *size.
+ * import restores them into a context created with the same configuration. */
+vegas_status vegas_export_state(vegas_ctx *ctx, void *buf, size_t *size);
+vegas_status vegas_import_state(vegas_ctx *ctx, const void *buf, size_t size);
+
+/* Device Philox4x32-10 (Salmon et al., SC'11) over n counters:
+ * dev_ctr (n x 4 u32), dev_key (n x 2 u32) -> dev_out (n x 4 u32).
+ * The same device function the sampling kernel uses.  Asynchronous. */
+vegas_status vegas_philox(const uint32_t *dev_ctr, const uint32_t *dev_key, uint32_t *dev_out,
+                          int64_t n, void *stream);
+
+void vegas_destroy(vegas_ctx *ctx);
+const char *vegas_strerror(vegas_status st);
+const char *vegas_last_error_string(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VEGAS_GB300_H */

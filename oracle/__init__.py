@@ -67,6 +67,8 @@ def _load():
                           ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_uint32))
         lib.oracle_philox4x32_10.argtypes = [up, up, up]
         lib.oracle_philox4x32_10.restype = None
+        lib.oracle_philox_many.argtypes = [i64, up, up, up]
+        lib.oracle_philox_many.restype = None
         lib.oracle_draw.argtypes = [u64, u32, i32, u32, u32]
         lib.oracle_draw.restype = u32
         lib.oracle_integrand.argtypes = [i32, i32, dp, i32, dp]
@@ -105,6 +107,18 @@ def philox4x32_10(ctr, key):
     out = np.zeros(4, dtype=np.uint32)
     p = ctypes.POINTER(ctypes.c_uint32)
     lib.oracle_philox4x32_10(c.ctypes.data_as(p), k.ctypes.data_as(p), out.ctypes.data_as(p))
+    return out
+
+
+def philox_many(ctr, key):
+    """Philox4x32-10 of n counters (n x 4 u32) under n keys (n x 2 u32)."""
+    lib = _load()
+    c = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint32).reshape(-1, 4))
+    k = np.ascontiguousarray(np.asarray(key, dtype=np.uint32).reshape(-1, 2))
+    assert c.shape[0] == k.shape[0]
+    out = np.zeros_like(c)
+    p = ctypes.POINTER(ctypes.c_uint32)
+    lib.oracle_philox_many(c.shape[0], c.ctypes.data_as(p), k.ctypes.data_as(p), out.ctypes.data_as(p))
     return out
 
 

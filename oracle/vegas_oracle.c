@@ -64,6 +64,10 @@ void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t
     out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
+void oracle_philox_many(int64_t n, const uint32_t *ctr, const uint32_t *key, uint32_t *out) {
+    for (int64_t i = 0; i < n; ++i) oracle_philox4x32_10(ctr + 4 * i, key + 2 * i, out + 4 * i);
+}
+
 uint32_t oracle_draw(uint64_t s, uint32_t t, int j, uint32_t seed, uint32_t integral_id) {
     uint32_t ctr[4], key[2], out[4];
     ctr[0] = (uint32_t)(s & 0xFFFFFFFFu);

@@ -35,6 +35,9 @@ enum {
 /* Philox4x32-10 block function (Salmon, Moraes, Dror, Shaw, SC'11). */
 void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 
+/* n independent blocks: out[4i..4i+3] = Philox(ctr[4i..4i+3], key[2i..2i+1]). */
+void oracle_philox_many(int64_t n, const uint32_t *ctr, const uint32_t *key, uint32_t *out);
+
 /* Uniform u32 draw r_j of sample s, dimension j, iteration t:
  * ctr = (s_lo, s_hi, t, j/4), key = (seed, integral_id), word j%4. */
 uint32_t oracle_draw(uint64_t s, uint32_t t, int j, uint32_t seed, uint32_t integral_id);

@@ -1,0 +1,108 @@
+"""ctypes binding of ``libvegas.so`` (the C ABI in ``include/vegas.h``).
+
+Argument marshalling only: every step of an iteration runs in the library's
+CUDA kernels.  PyTorch supplies device memory (the workspace) and streams.
+There is no CPU fallback: if the library is missing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libvegas.so")
+
+VEGAS_OK, VEGAS_EINVAL, VEGAS_ENOMEM, VEGAS_ECUDA, VEGAS_ETIMEOUT, VEGAS_EBUSY, VEGAS_ENONFINITE = range(7)
+VEGAS_FP64, VEGAS_FP32_ACC64, VEGAS_FP32_KAHAN = 0, 1, 2
+PRECISIONS = {"fp64": VEGAS_FP64, "fp32_acc64": VEGAS_FP32_ACC64, "fp32_kahan": VEGAS_FP32_KAHAN}
+FAMILIES = {"const": 0, "sum": 1, "gauss_sym": 2, "genz_osc": 3, "genz_gauss": 4,
+            "genz_prod": 5, "genz_corner": 6, "lo": 7}
+MAX_DIM, MAX_BINS, MAX_ITERS = 32, 1024, 4096
+
+
+class VegasConfig(ctypes.Structure):
+    _fields_ = [("n_dim", ctypes.c_int32), ("n_bins", ctypes.c_int32),
+                ("n_events", ctypes.c_int64), ("events_limit", ctypes.c_int64),
+                ("alpha", ctypes.c_double), ("seed", ctypes.c_uint32),
+                ("integral_id", ctypes.c_uint32), ("precision", ctypes.c_int32),
+                ("smooth", ctypes.c_int32)]
+
+
+class VegasIntegrand(ctypes.Structure):
+    _fields_ = [("family", ctypes.c_int32), ("n_dim", ctypes.c_int32),
+                ("params", ctypes.POINTER(ctypes.c_double)), ("n_params", ctypes.c_int32)]
+
+
+class VegasIterResult(ctypes.Structure):
+    _fields_ = [("I", ctypes.c_double), ("sigma", ctypes.c_double), ("n", ctypes.c_int64),
+                ("n_nonfinite", ctypes.c_int64)]
+
+
+class VegasResult(ctypes.Structure):
+    _fields_ = [("I", ctypes.c_double), ("sigma", ctypes.c_double),
+                ("chi2_dof", ctypes.c_double), ("n_iter", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class VegasError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        lib = load()
+        msg = lib.vegas_strerror(status).decode()
+        extra = lib.vegas_last_error_string().decode() if status == VEGAS_ECUDA else ""
+        super().__init__("%s: %s%s" % (what, msg, (" (" + extra + ")") if extra else ""))
+
+
+_lib = None
+
+# Every symbol include/vegas.h declares, with its ctypes signature.
+_P = ctypes.c_void_p
+_SIGS = {
+    "vegas_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(VegasConfig)]),
+    "vegas_create": (ctypes.c_int, [ctypes.POINTER(VegasConfig), ctypes.POINTER(VegasIntegrand),
+                                    _P, _P, ctypes.c_size_t, ctypes.POINTER(_P)]),
+    "vegas_iterate": (ctypes.c_int, [_P, ctypes.POINTER(VegasIterResult)]),
+    "vegas_refine": (ctypes.c_int, [_P]),
+    "vegas_result": (ctypes.c_int, [_P, ctypes.POINTER(VegasResult)]),
+    "vegas_run": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(VegasIterResult),
+                                 ctypes.POINTER(VegasResult)]),
+    "vegas_get_grid": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
+    "vegas_set_grid": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
+    "vegas_get_sums": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
+    "vegas_get_iteration": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),
+    "vegas_set_iteration": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "vegas_trace": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, _P, _P, _P]),
+    "vegas_export_state": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_size_t)]),
+    "vegas_import_state": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
+    "vegas_philox": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _P]),
+    "vegas_destroy": (None, [_P]),
+    "vegas_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "vegas_last_error_string": (ctypes.c_char_p, []),
+}
+
+
+def declared_symbols():
+    return list(_SIGS)
+
+
+def load():
+    """Load libvegas.so (built by ``build.build()``); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libvegas.so is not built (%s); run paper_2010_09341_gb300.build.build()"
+                          % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def check(status, what=""):
+    if status != VEGAS_OK:
+        raise VegasError(status, what)
+    return status

@@ -1,0 +1,584 @@
+// vegas_api.cu -- the C ABI of include/vegas.h.
+//
+// Host code only: validation, workspace layout, per-integral constants and
+// kernel launches.  Every arithmetic step of an iteration (sampling, sums,
+// iteration result, combination, refinement) runs in the device kernels.
+#include "../../include/vegas.h"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "vegas_kernels.cuh"
+
+using namespace vegas;
+
+namespace {
+
+thread_local char g_last_error[256] = "";
+
+void set_error(const char *what, cudaError_t e) {
+    snprintf(g_last_error, sizeof(g_last_error), "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define VEGAS_CK(call)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) {                         \
+            set_error(#call, e_);                        \
+            return VEGAS_ECUDA;                          \
+        }                                                \
+    } while (0)
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+struct Layout {
+    size_t edges, table, acc, last, nonfinite, iters, comb, total;
+};
+
+Layout layout_for(int d, int N) {
+    Layout L;
+    size_t off = 0;
+    L.edges = off;
+    off = align_up(off + sizeof(double) * d * (N + 1));
+    L.table = off;
+    off = align_up(off + 16 * static_cast<size_t>(d) * N);
+    L.acc = off;
+    off = align_up(off + sizeof(double) * (2 + static_cast<size_t>(d) * N));
+    L.last = off;
+    off = align_up(off + sizeof(double) * (2 + static_cast<size_t>(d) * N));
+    L.nonfinite = off;
+    off = align_up(off + sizeof(unsigned long long));
+    L.iters = off;
+    off = align_up(off + sizeof(IterRec) * VEGAS_MAX_ITERS);
+    L.comb = off;
+    off = align_up(off + sizeof(CombRec));
+    L.total = off;
+    return L;
+}
+
+int n_params_for(int family, int d) {
+    switch (family) {
+    case VEGAS_F_CONST: return 0;
+    case VEGAS_F_SUM: return 0;
+    case VEGAS_F_GAUSS_SYM: return 1;
+    case VEGAS_F_GENZ_OSC: return 1 + d;
+    case VEGAS_F_GENZ_GAUSS: return 2 * d;
+    case VEGAS_F_GENZ_PROD: return 2 * d;
+    case VEGAS_F_GENZ_CORNER: return d;
+    case VEGAS_F_LO: return 7;
+    default: return -1;
+    }
+}
+
+int mode_of(int precision) {
+    switch (precision) {
+    case VEGAS_FP64: return ACC_F64;
+    case VEGAS_FP32_ACC64: return ACC_F32_SUM64;
+    case VEGAS_FP32_KAHAN: return ACC_F32_KAHAN;
+    default: return -1;
+    }
+}
+
+const void *sample_fn(int mode, int fam, int tier, bool priv) {
+    switch (mode) {
+    case ACC_F64: return sample_kernel_f64(fam, tier, priv);
+    case ACC_F32_SUM64: return sample_kernel_f32sum64(fam, tier, priv);
+    default: return sample_kernel_f32kahan(fam, tier, priv);
+    }
+}
+
+struct DeviceInfo {
+    int sms = 0;
+    size_t smem_optin = 0;
+};
+
+DeviceInfo device_info(cudaError_t *err) {
+    int dev = 0;
+    DeviceInfo di;
+    *err = cudaGetDevice(&dev);
+    if (*err != cudaSuccess) return di;
+    *err = cudaDeviceGetAttribute(&di.sms, cudaDevAttrMultiProcessorCount, dev);
+    if (*err != cudaSuccess) return di;
+    int v = 0;
+    *err = cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    di.smem_optin = static_cast<size_t>(v);
+    return di;
+}
+
+// f's constant factors and the per-dimension constants of each family.
+// Returns false if a parameter is out of its domain.
+bool prepare_family(int family, int d, const double *p, FamilyConsts &fc, double &norm,
+                    double &fmax) {
+    memset(&fc, 0, sizeof(fc));
+    const double log2e = 1.4426950408889634;
+    norm = 1.0;
+    fmax = 1.0;
+    switch (family) {
+    case VEGAS_F_CONST: break;
+    case VEGAS_F_SUM: fmax = d; break;
+    case VEGAS_F_GAUSS_SYM: {
+        const double a = p[0];
+        if (!(a > 0.0) || !std::isfinite(a)) return false;
+        fc.s[0] = -log2e / (a * a);
+        norm = std::pow(a * std::sqrt(M_PI), -static_cast<double>(d));
+        fmax = norm;
+        break;
+    }
+    case VEGAS_F_GENZ_OSC:
+        fc.s[1] = 2.0 * M_PI * p[0];
+        for (int j = 0; j < d; ++j) fc.p[j] = p[1 + j];
+        break;
+    case VEGAS_F_GENZ_GAUSS:
+        fc.s[0] = -log2e;
+        for (int j = 0; j < d; ++j) {
+            fc.p[j] = p[j];
+            fc.q[j] = p[d + j];
+        }
+        break;
+    case VEGAS_F_GENZ_PROD:
+        for (int j = 0; j < d; ++j) {
+            if (!(p[j] != 0.0) || !std::isfinite(p[j])) return false;
+            fc.p[j] = p[j];
+            fc.q[j] = p[d + j];
+            norm *= p[j] * p[j];
+        }
+        fmax = norm;
+        break;
+    case VEGAS_F_GENZ_CORNER:
+        for (int j = 0; j < d; ++j) {
+            if (!(p[j] >= 0.0)) return false;
+            fc.p[j] = p[j];
+        }
+        fc.s[0] = -static_cast<double>(d + 1);
+        break;
+    case VEGAS_F_LO: {
+        const double sqrtS = p[0], M = p[1], G = p[2], cut = p[3], mlo = p[4], mhi = p[5], nrm = p[6];
+        if (!(sqrtS > 0 && M > 0 && G > 0 && cut > 0 && mlo >= 0 && mhi > mlo)) return false;
+        fc.s[0] = sqrtS * sqrtS;
+        fc.s[1] = M * M;
+        fc.s[2] = M * M * G * G;
+        fc.s[3] = cut;
+        fc.s[4] = mlo * mlo;
+        fc.s[5] = mhi * mhi;
+        const double gn = 35.0 / 32.0;
+        norm = 2.0 * gn * gn * nrm;
+        // size of f near the resonance: g(x)^2 ~ 1/sqrt(tau0), BW/shat ~ 1/(M^2 G)^2
+        fmax = std::fabs(norm) * (sqrtS / M) / (M * M * M * M * G * G);
+        break;
+    }
+    default: return false;
+    }
+    if (!std::isfinite(norm) || !(fmax > 0.0) || !std::isfinite(fmax)) return false;
+    return true;
+}
+
+}  // namespace
+
+struct vegas_ctx {
+    vegas_config cfg;
+    int family;
+    int mode;
+    std::vector<double> params;
+    cudaStream_t stream;
+    char *ws;
+    size_t ws_bytes;
+    Layout L;
+    double *edges;
+    void *table;
+    double *acc;
+    double *last;
+    unsigned long long *nonfinite;
+    IterRec *iters;
+    CombRec *comb;
+    int t;          // Philox iteration word of the next iteration
+    int n_done;     // iterations recorded in iters[]
+    FamilyConsts fc;
+    double jinit;
+    double scale;   // v is accumulated as v * scale (a power of two)
+    double nblk4;
+    const void *kfn;
+    size_t smem;
+    int threads;
+    int max_blocks;
+};
+
+extern "C" {
+
+const char *vegas_strerror(vegas_status st) {
+    switch (st) {
+    case VEGAS_OK: return "ok";
+    case VEGAS_EINVAL: return "invalid argument";
+    case VEGAS_ENOMEM: return "workspace too small";
+    case VEGAS_ECUDA: return "CUDA error";
+    case VEGAS_ETIMEOUT: return "device wait timed out";
+    case VEGAS_EBUSY: return "no free slot";
+    case VEGAS_ENONFINITE: return "every integrand value was non-finite";
+    default: return "unknown status";
+    }
+}
+
+const char *vegas_last_error_string(void) { return g_last_error; }
+
+static bool config_ok(const vegas_config *c) {
+    if (!c) return false;
+    if (c->n_dim < 1 || c->n_dim > VEGAS_MAX_DIM) return false;
+    if (c->n_bins < 2 || c->n_bins > VEGAS_MAX_BINS) return false;
+    if (c->n_events < 2) return false;
+    if (!(c->alpha >= 0.0) || !std::isfinite(c->alpha)) return false;
+    if (mode_of(c->precision) < 0) return false;
+    return true;
+}
+
+size_t vegas_workspace_bytes(const vegas_config *cfg) {
+    if (!config_ok(cfg)) return 0;
+    return layout_for(cfg->n_dim, cfg->n_bins).total;
+}
+
+vegas_status vegas_create(const vegas_config *cfg, const vegas_integrand *itg, void *stream,
+                          void *dev_workspace, size_t ws_bytes, vegas_ctx **out) {
+    if (!out) return VEGAS_EINVAL;
+    *out = nullptr;
+    if (!config_ok(cfg) || !itg) return VEGAS_EINVAL;
+    const int d = cfg->n_dim, N = cfg->n_bins;
+    if (itg->n_dim != d) return VEGAS_EINVAL;
+    const int np = n_params_for(itg->family, d);
+    if (np < 0 || itg->n_params != np || (np > 0 && !itg->params)) return VEGAS_EINVAL;
+    if (itg->family == VEGAS_F_LO && d != 3) return VEGAS_EINVAL;
+    const Layout L = layout_for(d, N);
+    if (!dev_workspace || (reinterpret_cast<uintptr_t>(dev_workspace) % kAlign) != 0)
+        return VEGAS_EINVAL;
+    if (ws_bytes < L.total) return VEGAS_ENOMEM;
+
+    FamilyConsts fc;
+    double norm = 1.0, fmax = 1.0;
+    if (!prepare_family(itg->family, d, itg->params, fc, norm, fmax)) return VEGAS_EINVAL;
+
+    cudaError_t err;
+    const DeviceInfo di = device_info(&err);
+    if (err != cudaSuccess) {
+        set_error("device query", err);
+        return VEGAS_ECUDA;
+    }
+    const int mode = mode_of(cfg->precision);
+    const int tier = tier_of(d);
+    // 1 KB margin for the kernel's static shared memory (block reduction)
+    const size_t budget = di.smem_optin > 1024 ? di.smem_optin - 1024 : 0;
+    bool priv = sample_smem(mode, true, d, N) <= budget;
+    const size_t smem = sample_smem(mode, priv, d, N);
+    if (smem > budget) return VEGAS_EINVAL;  // d N too large for shared memory
+    const void *fn = sample_fn(mode, itg->family, tier, priv);
+    if (!fn) return VEGAS_EINVAL;
+    VEGAS_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(smem)));
+    const int threads = 512;
+    int occ = 0;
+    VEGAS_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem));
+    if (occ < 1) return VEGAS_EINVAL;
+
+    vegas_ctx *c = new vegas_ctx();
+    c->cfg = *cfg;
+    c->family = itg->family;
+    c->mode = mode;
+    c->params.assign(itg->params, itg->params + np);
+    c->stream = static_cast<cudaStream_t>(stream);
+    c->ws = static_cast<char *>(dev_workspace);
+    c->ws_bytes = ws_bytes;
+    c->L = L;
+    c->edges = reinterpret_cast<double *>(c->ws + L.edges);
+    c->table = c->ws + L.table;
+    c->acc = reinterpret_cast<double *>(c->ws + L.acc);
+    c->last = reinterpret_cast<double *>(c->ws + L.last);
+    c->nonfinite = reinterpret_cast<unsigned long long *>(c->ws + L.nonfinite);
+    c->iters = reinterpret_cast<IterRec *>(c->ws + L.iters);
+    c->comb = reinterpret_cast<CombRec *>(c->ws + L.comb);
+    c->t = 0;
+    c->n_done = 0;
+    c->fc = fc;
+    // v is accumulated scaled by a power of two near 1/max f so that v^2 and
+    // the histograms stay far from the FP32 range limits; the finalize kernel
+    // divides it out exactly.
+    c->scale = std::ldexp(1.0, -static_cast<int>(std::lround(std::log2(fmax))));
+    const double Nd = static_cast<double>(N);
+    if (mode == ACC_F64) c->jinit = norm * c->scale * std::pow(Nd, d);
+    else c->jinit = norm * c->scale * std::pow(Nd, d % 4);
+    c->nblk4 = Nd * Nd * Nd * Nd;
+    c->kfn = fn;
+    c->smem = smem;
+    c->threads = threads;
+    c->max_blocks = occ * di.sms;
+
+    // uniform grid, zeroed accumulators
+    std::vector<double> e(static_cast<size_t>(d) * (N + 1));
+    for (int j = 0; j < d; ++j)
+        for (int k = 0; k <= N; ++k) e[static_cast<size_t>(j) * (N + 1) + k] = static_cast<double>(k) / N;
+    cudaError_t ce = cudaMemcpyAsync(c->edges, e.data(), e.size() * sizeof(double),
+                                     cudaMemcpyHostToDevice, c->stream);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(c->acc, 0, (L.nonfinite + 8) - L.acc, c->stream);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(c->comb, 0, sizeof(CombRec), c->stream);
+    if (ce == cudaSuccess) ce = launch_table_from_edges(c->edges, c->table, mode, d, N, c->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
+    if (ce != cudaSuccess) {
+        set_error("vegas_create", ce);
+        delete c;
+        return VEGAS_ECUDA;
+    }
+    *out = c;
+    return VEGAS_OK;
+}
+
+static SampleArgs make_args(const vegas_ctx *c, long long s_begin, long long n, int t) {
+    SampleArgs a;
+    a.table = c->table;
+    a.acc = c->acc;
+    a.n_nonfinite = c->nonfinite;
+    a.s_begin = s_begin;
+    a.n = n;
+    a.d = c->cfg.n_dim;
+    a.N = c->cfg.n_bins;
+    a.key0 = c->cfg.seed;
+    a.key1 = c->cfg.integral_id;
+    a.iter = static_cast<uint32_t>(t);
+    a.jinit = c->jinit;
+    a.nblk4 = c->nblk4;
+    a.fc = c->fc;
+    return a;
+}
+
+static vegas_status launch_sampling(vegas_ctx *c, long long s_begin, long long n) {
+    SampleArgs a = make_args(c, s_begin, n, c->t);
+    // a few samples per thread at least; otherwise fill every SM
+    const long long want = (n + static_cast<long long>(c->threads) * 4 - 1) /
+                           (static_cast<long long>(c->threads) * 4);
+    const int blocks = static_cast<int>(std::max(1LL, std::min<long long>(c->max_blocks, want)));
+    void *params[] = {&a};
+    VEGAS_CK(cudaLaunchKernel(c->kfn, dim3(blocks), dim3(c->threads), params, c->smem, c->stream));
+    return VEGAS_OK;
+}
+
+vegas_status vegas_iterate(vegas_ctx *c, vegas_iter_result *out) {
+    if (!c) return VEGAS_EINVAL;
+    if (c->n_done >= VEGAS_MAX_ITERS) return VEGAS_EINVAL;
+    const long long n = c->cfg.n_events;
+    const long long lim = c->cfg.events_limit > 0 ? c->cfg.events_limit : n;
+    for (long long s0 = 0; s0 < n; s0 += lim) {
+        const vegas_status st = launch_sampling(c, s0, std::min(lim, n - s0));
+        if (st != VEGAS_OK) return st;
+    }
+    VEGAS_CK(launch_finalize(c->acc, c->last, c->nonfinite, c->iters, c->comb, c->n_done, n,
+                             c->cfg.n_dim, c->cfg.n_bins, 1.0 / c->scale, c->stream));
+    const int rec = c->n_done;
+    c->n_done += 1;
+    c->t += 1;
+    if (!out) return VEGAS_OK;
+    IterRec r;
+    VEGAS_CK(cudaMemcpyAsync(&r, c->iters + rec, sizeof(r), cudaMemcpyDeviceToHost, c->stream));
+    VEGAS_CK(cudaStreamSynchronize(c->stream));
+    out->I = r.I;
+    out->sigma = r.sigma;
+    out->n = r.n;
+    out->n_nonfinite = r.n_nonfinite;
+    return r.n <= 0 ? VEGAS_ENONFINITE : VEGAS_OK;
+}
+
+vegas_status vegas_refine(vegas_ctx *c) {
+    if (!c) return VEGAS_EINVAL;
+    if (c->n_done == 0) return VEGAS_OK;  // nothing sampled yet: keep the grid
+    VEGAS_CK(launch_refine(c->last, c->edges, c->table, c->mode, c->cfg.n_dim, c->cfg.n_bins,
+                           c->cfg.alpha, c->cfg.smooth, c->stream));
+    return VEGAS_OK;
+}
+
+vegas_status vegas_result(vegas_ctx *c, vegas_result_t *out) {
+    if (!c || !out) return VEGAS_EINVAL;
+    CombRec r;
+    VEGAS_CK(cudaMemcpyAsync(&r, c->comb, sizeof(r), cudaMemcpyDeviceToHost, c->stream));
+    VEGAS_CK(cudaStreamSynchronize(c->stream));
+    out->I = r.I;
+    out->sigma = r.sigma;
+    out->chi2_dof = r.chi2_dof;
+    out->n_iter = r.n_iter;
+    out->reserved = 0;
+    return VEGAS_OK;
+}
+
+vegas_status vegas_run(vegas_ctx *c, int32_t n_iter, vegas_iter_result *iters, vegas_result_t *out) {
+    if (!c || n_iter < 1 || !out) return VEGAS_EINVAL;
+    if (c->n_done + n_iter > VEGAS_MAX_ITERS) return VEGAS_EINVAL;
+    const int first = c->n_done;
+    for (int k = 0; k < n_iter; ++k) {
+        vegas_status st = vegas_iterate(c, nullptr);
+        if (st != VEGAS_OK) return st;
+        if (k + 1 < n_iter) {
+            st = vegas_refine(c);
+            if (st != VEGAS_OK) return st;
+        }
+    }
+    if (iters) {
+        std::vector<IterRec> rs(n_iter);
+        VEGAS_CK(cudaMemcpyAsync(rs.data(), c->iters + first, sizeof(IterRec) * n_iter,
+                                 cudaMemcpyDeviceToHost, c->stream));
+        VEGAS_CK(cudaStreamSynchronize(c->stream));
+        for (int k = 0; k < n_iter; ++k) {
+            iters[k].I = rs[k].I;
+            iters[k].sigma = rs[k].sigma;
+            iters[k].n = rs[k].n;
+            iters[k].n_nonfinite = rs[k].n_nonfinite;
+        }
+    }
+    return vegas_result(c, out);
+}
+
+vegas_status vegas_get_grid(vegas_ctx *c, double *edges_host) {
+    if (!c || !edges_host) return VEGAS_EINVAL;
+    const size_t bytes = sizeof(double) * c->cfg.n_dim * (c->cfg.n_bins + 1);
+    VEGAS_CK(cudaMemcpyAsync(edges_host, c->edges, bytes, cudaMemcpyDeviceToHost, c->stream));
+    VEGAS_CK(cudaStreamSynchronize(c->stream));
+    return VEGAS_OK;
+}
+
+vegas_status vegas_set_grid(vegas_ctx *c, const double *e) {
+    if (!c || !e) return VEGAS_EINVAL;
+    const int d = c->cfg.n_dim, N = c->cfg.n_bins;
+    for (int j = 0; j < d; ++j) {
+        const double *row = e + static_cast<size_t>(j) * (N + 1);
+        if (row[0] != 0.0 || row[N] != 1.0) return VEGAS_EINVAL;
+        for (int k = 0; k < N; ++k)
+            if (!(row[k + 1] >= row[k])) return VEGAS_EINVAL;
+    }
+    VEGAS_CK(cudaMemcpyAsync(c->edges, e, sizeof(double) * d * (N + 1), cudaMemcpyHostToDevice,
+                             c->stream));
+    VEGAS_CK(launch_table_from_edges(c->edges, c->table, c->mode, d, N, c->stream));
+    VEGAS_CK(cudaStreamSynchronize(c->stream));
+    return VEGAS_OK;
+}
+
+vegas_status vegas_get_sums(vegas_ctx *c, double *sums_host) {
+    if (!c || !sums_host) return VEGAS_EINVAL;
+    const size_t cnt = 2 + static_cast<size_t>(c->cfg.n_dim) * c->cfg.n_bins;
+    VEGAS_CK(cudaMemcpyAsync(sums_host, c->last, cnt * sizeof(double), cudaMemcpyDeviceToHost,
+                             c->stream));
+    VEGAS_CK(cudaStreamSynchronize(c->stream));
+    return VEGAS_OK;
+}
+
+vegas_status vegas_get_iteration(vegas_ctx *c, int32_t *t) {
+    if (!c || !t) return VEGAS_EINVAL;
+    *t = c->t;
+    return VEGAS_OK;
+}
+
+vegas_status vegas_set_iteration(vegas_ctx *c, int32_t t) {
+    if (!c || t < 0) return VEGAS_EINVAL;
+    c->t = t;
+    return VEGAS_OK;
+}
+
+vegas_status vegas_trace(vegas_ctx *c, int32_t t, int64_t s_begin, int64_t count, int32_t *bins,
+                         double *x, double *w) {
+    if (!c || t < 0 || s_begin < 0 || count < 0) return VEGAS_EINVAL;
+    if (count == 0) return VEGAS_OK;
+    SampleArgs a = make_args(c, s_begin, count, t);
+    VEGAS_CK(launch_trace(a, c->family, c->mode, 1.0 / c->scale, bins, x, w, c->stream));
+    return VEGAS_OK;
+}
+
+// ------------------------------------------------------------ checkpoint
+namespace {
+struct BlobHeader {
+    uint32_t magic;
+    uint32_t version;
+    vegas_config cfg;
+    int32_t family;
+    int32_t n_params;
+    int32_t t;
+    int32_t n_done;
+};
+constexpr uint32_t kMagic = 0x56454741u;  // "VEGA"
+}  // namespace
+
+vegas_status vegas_export_state(vegas_ctx *c, void *buf, size_t *size) {
+    if (!c || !size) return VEGAS_EINVAL;
+    const int d = c->cfg.n_dim, N = c->cfg.n_bins;
+    const size_t ne = static_cast<size_t>(d) * (N + 1);
+    const size_t need = sizeof(BlobHeader) + sizeof(double) * c->params.size() +
+                        sizeof(double) * ne + sizeof(IterRec) * c->n_done + sizeof(CombRec);
+    if (!buf) {
+        *size = need;
+        return VEGAS_OK;
+    }
+    if (*size < need) return VEGAS_ENOMEM;
+    char *p = static_cast<char *>(buf);
+    BlobHeader h;
+    memset(&h, 0, sizeof(h));
+    h.magic = kMagic;
+    h.version = 1;
+    h.cfg = c->cfg;
+    h.family = c->family;
+    h.n_params = static_cast<int32_t>(c->params.size());
+    h.t = c->t;
+    h.n_done = c->n_done;
+    memcpy(p, &h, sizeof(h));
+    p += sizeof(h);
+    memcpy(p, c->params.data(), sizeof(double) * c->params.size());
+    p += sizeof(double) * c->params.size();
+    VEGAS_CK(cudaMemcpyAsync(p, c->edges, sizeof(double) * ne, cudaMemcpyDeviceToHost, c->stream));
+    p += sizeof(double) * ne;
+    if (c->n_done > 0)
+        VEGAS_CK(cudaMemcpyAsync(p, c->iters, sizeof(IterRec) * c->n_done, cudaMemcpyDeviceToHost,
+                                 c->stream));
+    p += sizeof(IterRec) * c->n_done;
+    VEGAS_CK(cudaMemcpyAsync(p, c->comb, sizeof(CombRec), cudaMemcpyDeviceToHost, c->stream));
+    VEGAS_CK(cudaStreamSynchronize(c->stream));
+    *size = need;
+    return VEGAS_OK;
+}
+
+vegas_status vegas_import_state(vegas_ctx *c, const void *buf, size_t size) {
+    if (!c || !buf || size < sizeof(BlobHeader)) return VEGAS_EINVAL;
+    const char *p = static_cast<const char *>(buf);
+    BlobHeader h;
+    memcpy(&h, p, sizeof(h));
+    p += sizeof(h);
+    if (h.magic != kMagic || h.version != 1) return VEGAS_EINVAL;
+    const vegas_config &a = h.cfg, &b = c->cfg;
+    if (a.n_dim != b.n_dim || a.n_bins != b.n_bins || a.n_events != b.n_events ||
+        a.seed != b.seed || a.integral_id != b.integral_id || a.precision != b.precision ||
+        a.alpha != b.alpha || a.smooth != b.smooth || h.family != c->family ||
+        h.n_params != static_cast<int32_t>(c->params.size()))
+        return VEGAS_EINVAL;
+    if (h.n_done < 0 || h.n_done > VEGAS_MAX_ITERS || h.t < 0) return VEGAS_EINVAL;
+    const int d = b.n_dim, N = b.n_bins;
+    const size_t ne = static_cast<size_t>(d) * (N + 1);
+    const size_t need = sizeof(BlobHeader) + sizeof(double) * h.n_params + sizeof(double) * ne +
+                        sizeof(IterRec) * h.n_done + sizeof(CombRec);
+    if (size < need) return VEGAS_EINVAL;
+    if (memcmp(p, c->params.data(), sizeof(double) * h.n_params) != 0) return VEGAS_EINVAL;
+    p += sizeof(double) * h.n_params;
+    VEGAS_CK(cudaMemcpyAsync(c->edges, p, sizeof(double) * ne, cudaMemcpyHostToDevice, c->stream));
+    p += sizeof(double) * ne;
+    if (h.n_done > 0)
+        VEGAS_CK(cudaMemcpyAsync(c->iters, p, sizeof(IterRec) * h.n_done, cudaMemcpyHostToDevice,
+                                 c->stream));
+    p += sizeof(IterRec) * h.n_done;
+    VEGAS_CK(cudaMemcpyAsync(c->comb, p, sizeof(CombRec), cudaMemcpyHostToDevice, c->stream));
+    VEGAS_CK(launch_table_from_edges(c->edges, c->table, c->mode, d, N, c->stream));
+    VEGAS_CK(cudaStreamSynchronize(c->stream));
+    c->t = h.t;
+    c->n_done = h.n_done;
+    return VEGAS_OK;
+}
+
+vegas_status vegas_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int64_t n,
+                          void *stream) {
+    if (n < 0 || (n > 0 && (!ctr || !key || !out))) return VEGAS_EINVAL;
+    VEGAS_CK(launch_philox(ctr, key, out, n, static_cast<cudaStream_t>(stream)));
+    return VEGAS_OK;
+}
+
+void vegas_destroy(vegas_ctx *c) { delete c; }
+
+}  // extern "C"

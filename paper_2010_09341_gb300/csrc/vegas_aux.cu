@@ -1,0 +1,406 @@
+// vegas_aux.cu -- the small kernels around the sampling kernel: iteration
+// result and combination, grid refinement, table building, per-sample trace
+// and a bare Philox kernel.
+//
+// All of them are FP64: the refinement and the combination of iterations need
+// it (a rebinned edge is a difference of running sums; chi^2 is a sum of
+// squared deviations), and they touch O(d N) values, so their cost is
+// launch latency, not arithmetic.
+#include "vegas_kernels.cuh"
+
+namespace vegas {
+
+// ------------------------------------------------------------- finalize
+// Iteration estimate (Lepage 1978): I = S1/n, sigma^2 = (S2/n - I^2)/(n-1).
+// Combination over iterations: inverse-variance weighted mean, its sigma and
+// chi^2/dof = sum (I_j - I)^2 / sigma_j^2 / (m - 1).  Iterations with zero
+// variance are exact: if any exist, their plain mean is the result with
+// sigma 0.
+__global__ void __launch_bounds__(256)
+finalize_kernel(double *acc, double *last, unsigned long long *n_nonfinite, IterRec *iters,
+                CombRec *comb, int t, long long n, int total, double inv1, double inv2) {
+    __shared__ double sh[3][8];
+    __shared__ double mean_s;
+    __shared__ int nzero_s;
+    for (int c = threadIdx.x; c < total; c += blockDim.x) {
+        last[c] = acc[c] * (c == 0 ? inv1 : inv2);
+        acc[c] = 0.0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const long long nf = static_cast<long long>(*n_nonfinite);
+        *n_nonfinite = 0ull;
+        const long long ne = n - nf;
+        IterRec r;
+        r.n = ne;
+        r.n_nonfinite = nf;
+        if (ne >= 2) {
+            const double I = last[0] / static_cast<double>(ne);
+            double var = (last[1] / static_cast<double>(ne) - I * I) / static_cast<double>(ne - 1);
+            r.I = I;
+            r.sigma = var > 0.0 ? sqrt(var) : 0.0;
+        } else if (ne == 1) {
+            r.I = last[0];
+            r.sigma = 0.0;
+        } else {
+            r.I = 0.0;
+            r.sigma = 0.0;
+        }
+        iters[t] = r;
+    }
+    __syncthreads();
+    // combination over iters[0..t] (includes the record just written)
+    const int m = t + 1;
+    double wsum = 0.0, wisum = 0.0, zsum = 0.0;
+    int nzero = 0;
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+        const IterRec r = iters[j];
+        if (r.n <= 0) continue;  // an all-non-finite iteration carries no information
+        if (r.sigma == 0.0) {
+            ++nzero;
+            zsum += r.I;
+        } else {
+            const double w = 1.0 / (r.sigma * r.sigma);
+            wsum += w;
+            wisum += w * r.I;
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    wsum = warp_sum(wsum);
+    wisum = warp_sum(wisum);
+    zsum = warp_sum(zsum);
+    nzero = __reduce_add_sync(0xFFFFFFFFu, nzero);
+    __shared__ int nz_w[8];
+    if (lane == 0) {
+        sh[0][warp] = wsum;
+        sh[1][warp] = wisum;
+        sh[2][warp] = zsum;
+        nz_w[warp] = nzero;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0, b = 0, z = 0;
+        int nz = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            a += sh[0][k];
+            b += sh[1][k];
+            z += sh[2][k];
+            nz += nz_w[k];
+        }
+        nzero_s = nz;
+        if (nz > 0) mean_s = z / nz;
+        else mean_s = a > 0.0 ? b / a : 0.0;
+        sh[0][0] = a;
+    }
+    __syncthreads();
+    const double mean = mean_s;
+    double chi = 0.0;
+    int used = 0;
+    if (nzero_s == 0) {
+        for (int j = threadIdx.x; j < m; j += blockDim.x) {
+            const IterRec r = iters[j];
+            if (r.n <= 0) continue;
+            const double dv = (r.I - mean) / r.sigma;
+            chi += dv * dv;
+            ++used;
+        }
+    }
+    chi = warp_sum(chi);
+    used = __reduce_add_sync(0xFFFFFFFFu, used);
+    __syncthreads();
+    if (lane == 0) {
+        sh[1][warp] = chi;
+        nz_w[warp] = used;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double c = 0.0;
+        int u = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            c += sh[1][k];
+            u += nz_w[k];
+        }
+        CombRec out;
+        out.n_iter = m;
+        out.I = mean;
+        if (nzero_s > 0) {
+            out.sigma = 0.0;
+            out.chi2_dof = 0.0;
+        } else {
+            out.sigma = sh[0][0] > 0.0 ? 1.0 / sqrt(sh[0][0]) : 0.0;
+            out.chi2_dof = u > 1 ? c / static_cast<double>(u - 1) : 0.0;
+        }
+        out.status = iters[t].n <= 0 ? 6 : 0;
+        *comb = out;
+    }
+}
+
+cudaError_t launch_finalize(double *acc, double *last, unsigned long long *n_nonfinite,
+                            IterRec *iters, CombRec *comb, int t, long long n, int d, int N,
+                            double inv_scale, cudaStream_t stream) {
+    const int total = 2 + d * N;
+    finalize_kernel<<<1, 256, 0, stream>>>(acc, last, n_nonfinite, iters, comb, t, n, total,
+                                           inv_scale, inv_scale * inv_scale);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------- refine
+// Grid refinement of one dimension per block (Lepage 1980):
+//   smooth   d_0 = (h_0+h_1)/2, d_k = (h_{k-1}+h_k+h_{k+1})/3, d_{N-1} = (h_{N-2}+h_{N-1})/2
+//   normalise d_k /= sum d
+//   compress rho_k = ((1 - d_k)/ln(1/d_k))^alpha   (0 at d = 0, 1 at d = 1)
+//   rebin    new edge k (1..N-1) where the running rho sum reaches k sum(rho)/N,
+//            interpolated linearly inside the old bin; zero-weight bins are
+//            skipped and an edge on an old edge takes the lower bin.
+// A dimension whose weights sum to zero keeps its grid.
+template <class T2, class T>
+__device__ __forceinline__ void write_entry(void *table, int idx, double e, double w) {
+    reinterpret_cast<T2 *>(table)[idx] = T2{static_cast<T>(e - w), static_cast<T>(w)};
+}
+
+__device__ __forceinline__ void store_table(void *table, int mode, int idx, double e, double w) {
+    if (mode == ACC_F64) write_entry<double2, double>(table, idx, e, w);
+    else write_entry<float2, float>(table, idx, e, w);
+}
+
+constexpr int kRefineThreads = 128;
+
+__global__ void __launch_bounds__(kRefineThreads)
+refine_kernel(const double *last, double *edges, void *table, int mode, int N, double alpha,
+              int smooth) {
+    extern __shared__ double rs[];
+    double *eo = rs;            // old edges, N+1
+    double *rho = rs + (N + 1); // compressed weights, N
+    double *cum = rho + N;      // inclusive running sum, N
+    __shared__ double red[kRefineThreads / 32];
+    __shared__ double total_s;
+    const int j = blockIdx.x;
+    const double *h = last + 2 + static_cast<size_t>(j) * N;
+    double *e = edges + static_cast<size_t>(j) * (N + 1);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int k = tid; k <= N; k += blockDim.x) eo[k] = e[k];
+
+    // smoothing, kept in rho[] for now
+    double part = 0.0;
+    for (int k = tid; k < N; k += blockDim.x) {
+        double v;
+        if (!smooth) v = h[k];
+        else if (k == 0) v = (h[0] + h[1]) / 2.0;
+        else if (k == N - 1) v = (h[N - 2] + h[N - 1]) / 2.0;
+        else v = (h[k - 1] + h[k] + h[k + 1]) / 3.0;
+        rho[k] = v;
+        part += v;
+    }
+    part = warp_sum(part);
+    if (lane == 0) red[warp] = part;
+    __syncthreads();
+    if (tid == 0) {
+        double s = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += red[k];
+        total_s = s;
+    }
+    __syncthreads();
+    const double total = total_s;
+    if (!(total > 0.0) || !isfinite(total)) return;  // keep the grid (table unchanged)
+
+    // normalise and compress
+    for (int k = tid; k < N; k += blockDim.x) {
+        const double dk = rho[k] / total;
+        double r;
+        if (dk <= 0.0) r = 0.0;
+        else if (dk >= 1.0) r = 1.0;
+        else r = pow((1.0 - dk) / log(1.0 / dk), alpha);
+        rho[k] = r;
+    }
+    __syncthreads();
+
+    // inclusive scan of rho: each thread a contiguous chunk, then chunk offsets
+    const int chunk = (N + blockDim.x - 1) / blockDim.x;
+    const int k0 = tid * chunk, k1 = min(N, k0 + chunk);
+    double run = 0.0;
+    for (int k = k0; k < k1; ++k) {
+        run += rho[k];
+        cum[k] = run;
+    }
+    double incl = run;  // warp inclusive scan of chunk totals
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) red[warp] = incl;
+    __syncthreads();
+    double off = incl - run;
+    for (int w = 0; w < warp; ++w) off += red[w];
+    for (int k = k0; k < k1; ++k) cum[k] += off;
+    __syncthreads();
+    const double rsum = cum[N - 1];
+    if (!(rsum > 0.0)) return;
+    const double delta = rsum / static_cast<double>(N);
+
+    // rebin: new edge k is in the first old bin whose inclusive sum reaches k delta
+    for (int k = tid; k <= N; k += blockDim.x) {
+        double ek;
+        if (k == 0) ek = 0.0;
+        else if (k == N) ek = 1.0;
+        else {
+            const double target = static_cast<double>(k) * delta;
+            int lo = 0, hi = N - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (cum[mid] >= target) hi = mid;
+                else lo = mid + 1;
+            }
+            const int b = lo;
+            const double before = b > 0 ? cum[b - 1] : 0.0;
+            double frac = rho[b] > 0.0 ? (target - before) / rho[b] : 1.0;
+            frac = fmin(fmax(frac, 0.0), 1.0);
+            ek = eo[b] + frac * (eo[b + 1] - eo[b]);
+        }
+        rs[3 * N + 1 + k] = ek;  // new edges after cum[]
+    }
+    __syncthreads();
+    const double *en = rs + 3 * N + 1;
+    for (int k = tid; k <= N; k += blockDim.x) e[k] = en[k];
+    for (int k = tid; k < N; k += blockDim.x) {
+        store_table(table, mode, j * N + k, en[k], en[k + 1] - en[k]);
+    }
+}
+
+cudaError_t launch_refine(const double *last, double *edges, void *table, int mode, int d, int N,
+                          double alpha, int smooth, cudaStream_t stream) {
+    const size_t smem = static_cast<size_t>(4 * N + 2) * sizeof(double);
+    refine_kernel<<<d, kRefineThreads, smem, stream>>>(last, edges, table, mode, N, alpha, smooth);
+    return cudaGetLastError();
+}
+
+__global__ void table_kernel(const double *edges, void *table, int mode, int d, int N) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= d * N) return;
+    const int j = idx / N, k = idx - j * N;
+    const double *e = edges + static_cast<size_t>(j) * (N + 1);
+    store_table(table, mode, idx, e[k], e[k + 1] - e[k]);
+}
+
+cudaError_t launch_table_from_edges(const double *edges, void *table, int mode, int d, int N,
+                                    cudaStream_t stream) {
+    const int total = d * N;
+    table_kernel<<<(total + 255) / 256, 256, 0, stream>>>(edges, table, mode, d, N);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- trace
+// One thread per sample; the same split, map, Jacobian and integrand code as
+// the sampling kernel, reading the table from global memory.
+template <int FAM, int MODE, int MAXD>
+__global__ void trace_kernel(const SampleArgs a, double inv_scale, int32_t *bins, double *xs,
+                             double *ws) {
+    using T = typename ModeTraits<MODE>::T;
+    using T2 = typename Prec<T>::T2;
+    const long long k = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (k >= a.n) return;
+    const int d = a.d, N = a.N;
+    const T2 *tab = static_cast<const T2 *>(a.table);
+    Integrand<FAM, T, MAXD> fam;
+    fam.load(a.fc, d);
+    const unsigned long long s = static_cast<unsigned long long>(a.s_begin + k);
+    const uint32_t slo = static_cast<uint32_t>(s), shi = static_cast<uint32_t>(s >> 32);
+    T J = static_cast<T>(a.jinit);
+    const T n4 = static_cast<T>(a.nblk4);
+    fam.begin();
+#pragma unroll
+    for (int q = 0; q < (MAXD + 3) / 4; ++q) {
+        if (4 * q < d) {
+            const uint4 r = philox4x32_10(make_uint4(slo, shi, a.iter, static_cast<uint32_t>(q)),
+                                          a.key0, a.key1);
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                const int j = 4 * q + w;
+                if (j < MAXD && j < d) {
+                    const Split sp = split_bin(word(r, w), static_cast<uint32_t>(N));
+                    const uint32_t cell = static_cast<uint32_t>(j * N) + sp.bin;
+                    const T2 ent = tab[cell];
+                    const T m = Prec<T>::mant(sp.lo);
+                    const T x = fma(ent.y, m, ent.x);
+                    J *= ent.y;
+                    if (sizeof(T) == 4 && (j & 3) == 3) J *= n4;
+                    fam.dim(j, x);
+                    if (bins) bins[k * d + j] = static_cast<int32_t>(sp.bin);
+                    if (xs) xs[k * d + j] = static_cast<double>(x);
+                }
+            }
+        }
+    }
+    const T v = J * fam.finish(d);
+    if (ws) ws[k] = static_cast<double>(v) * inv_scale;
+}
+
+template <int MODE, int FAM>
+static const void *trace_pick(int tier) {
+    switch (tier) {
+    case 0: return reinterpret_cast<const void *>(&trace_kernel<FAM, MODE, 4>);
+    case 1: return reinterpret_cast<const void *>(&trace_kernel<FAM, MODE, 8>);
+    case 2: return reinterpret_cast<const void *>(&trace_kernel<FAM, MODE, 16>);
+    default: return reinterpret_cast<const void *>(&trace_kernel<FAM, MODE, 32>);
+    }
+}
+
+template <int MODE>
+static const void *trace_pick_fam(int fam, int tier) {
+    switch (fam) {
+    case F_CONST: return trace_pick<MODE, F_CONST>(tier);
+    case F_SUM: return trace_pick<MODE, F_SUM>(tier);
+    case F_GAUSS_SYM: return trace_pick<MODE, F_GAUSS_SYM>(tier);
+    case F_GENZ_OSC: return trace_pick<MODE, F_GENZ_OSC>(tier);
+    case F_GENZ_GAUSS: return trace_pick<MODE, F_GENZ_GAUSS>(tier);
+    case F_GENZ_PROD: return trace_pick<MODE, F_GENZ_PROD>(tier);
+    case F_GENZ_CORNER: return trace_pick<MODE, F_GENZ_CORNER>(tier);
+    case F_LO: return tier == 0 ? reinterpret_cast<const void *>(&trace_kernel<F_LO, MODE, 4>) : nullptr;
+    default: return nullptr;
+    }
+}
+
+cudaError_t launch_trace(const SampleArgs &a, int fam, int mode, double inv_scale, int32_t *bins,
+                         double *x, double *w, cudaStream_t stream) {
+    const int tier = tier_of(a.d);
+    const void *fn = nullptr;
+    // FP32 modes share the map/integrand arithmetic; the accumulation mode
+    // only changes how sums are kept, which the trace does not do.
+    if (mode == ACC_F64) fn = trace_pick_fam<ACC_F64>(fam, tier);
+    else fn = trace_pick_fam<ACC_F32_KAHAN>(fam, tier);
+    if (!fn) return cudaErrorInvalidValue;
+    if (a.n <= 0) return cudaSuccess;
+    const unsigned threads = 256;
+    const unsigned blocks = static_cast<unsigned>((a.n + threads - 1) / threads);
+    SampleArgs args = a;
+    void *params[] = {&args, &inv_scale, &bins, &x, &w};
+    return cudaLaunchKernel(fn, dim3(blocks), dim3(threads), params, 0, stream);
+}
+
+// --------------------------------------------------------------- Philox
+__global__ void philox_kernel(const uint4 *ctr, const uint2 *key, uint4 *out, long long n) {
+    const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint2 k = key[i];
+    out[i] = philox4x32_10(ctr[i], k.x, k.y);
+}
+
+cudaError_t launch_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out, long long n,
+                          cudaStream_t stream) {
+    if (n <= 0) return cudaSuccess;
+    const unsigned blocks = static_cast<unsigned>((n + 255) / 256);
+    philox_kernel<<<blocks, 256, 0, stream>>>(reinterpret_cast<const uint4 *>(ctr),
+                                              reinterpret_cast<const uint2 *>(key),
+                                              reinterpret_cast<uint4 *>(out), n);
+    return cudaGetLastError();
+}
+
+size_t sample_smem(int mode, bool priv, int d, int N) {
+    switch (mode) {
+    case ACC_F64: return priv ? sample_smem_bytes<ACC_F64, true>(d, N) : sample_smem_bytes<ACC_F64, false>(d, N);
+    case ACC_F32_SUM64: return priv ? sample_smem_bytes<ACC_F32_SUM64, true>(d, N) : sample_smem_bytes<ACC_F32_SUM64, false>(d, N);
+    default: return priv ? sample_smem_bytes<ACC_F32_KAHAN, true>(d, N) : sample_smem_bytes<ACC_F32_KAHAN, false>(d, N);
+    }
+}
+
+}  // namespace vegas

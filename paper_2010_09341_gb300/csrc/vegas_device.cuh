@@ -1,0 +1,205 @@
+// vegas_device.cuh -- device building blocks of one VEGAS iteration on sm_103a.
+//
+// The iteration (VEGAS, Lepage 1978/1980; the method of the paper, Sec. 1):
+// per sample draw d uniforms, find each uniform's bin, interpolate inside the
+// bin, multiply the per-dimension Jacobian factors, evaluate the integrand and
+// accumulate v = J f, v^2 and the per-bin histograms of v^2.
+//
+// Everything a sample needs lives in registers: the Philox words are drawn,
+// split and consumed without touching memory.  The grid table and the
+// histograms live in shared memory.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace vegas {
+
+// ---------------------------------------------------------------- Philox
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as
+// easy as 1, 2, 3", SC'11): ten rounds of two 32x32->64 multiplies and
+// xors, with the key advanced by the Weyl constants between rounds.
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
+constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;
+constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0 = static_cast<uint64_t>(kPhiloxM0) * c.x;
+        const uint64_t p1 = static_cast<uint64_t>(kPhiloxM1) * c.z;
+        const uint32_t rk0 = k0 + static_cast<uint32_t>(r) * kPhiloxW0;
+        const uint32_t rk1 = k1 + static_cast<uint32_t>(r) * kPhiloxW1;
+        c = make_uint4(static_cast<uint32_t>(p1 >> 32) ^ c.y ^ rk0, static_cast<uint32_t>(p1),
+                       static_cast<uint32_t>(p0 >> 32) ^ c.w ^ rk1, static_cast<uint32_t>(p0));
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint32_t word(const uint4 &r, int k) {
+    return k == 0 ? r.x : (k == 1 ? r.y : (k == 2 ? r.z : r.w));
+}
+
+// ------------------------------------------------------------ bin split
+// y N with y = r 2^-32 is split with one 32x32->64 integer multiply: the high
+// word is the bin, the low word the in-bin position.  Bins are therefore the
+// same integers in every precision.  The in-bin position is returned as a
+// number m in [1, 2) whose mantissa holds the low word's top bits, so that
+// x = (e - w) + w m with a single fused multiply-add.
+struct Split {
+    uint32_t bin;
+    uint32_t lo;
+};
+
+__device__ __forceinline__ Split split_bin(uint32_t r, uint32_t N) {
+    const uint64_t t = static_cast<uint64_t>(r) * N;
+    return Split{static_cast<uint32_t>(t >> 32), static_cast<uint32_t>(t)};
+}
+
+// FP32: m = 1 + (lo >> 9) 2^-23, exact.
+__device__ __forceinline__ float unit_mantissa_f32(uint32_t lo) {
+    return __uint_as_float(0x3F800000u | (lo >> 9));
+}
+
+// FP64: m = 1 + lo 2^-32, exact (all 32 bits fit in the 52-bit mantissa).
+__device__ __forceinline__ double unit_mantissa_f64(uint32_t lo) {
+    return __hiloint2double(static_cast<int>(0x3FF00000u | (lo >> 12)), static_cast<int>(lo << 20));
+}
+
+template <class T> struct Prec;
+template <> struct Prec<float> {
+    using T2 = float2;
+    __device__ static __forceinline__ float mant(uint32_t lo) { return unit_mantissa_f32(lo); }
+};
+template <> struct Prec<double> {
+    using T2 = double2;
+    __device__ static __forceinline__ double mant(uint32_t lo) { return unit_mantissa_f64(lo); }
+};
+
+// ----------------------------------------------------------- integrands
+// Family ids match vegas_family in vegas.h.
+enum Family : int {
+    F_CONST = 0,
+    F_SUM = 1,
+    F_GAUSS_SYM = 2,
+    F_GENZ_OSC = 3,
+    F_GENZ_GAUSS = 4,
+    F_GENZ_PROD = 5,
+    F_GENZ_CORNER = 6,
+    F_LO = 7
+};
+
+// Per-integral constants a family needs, prepared on the host in FP64:
+//   p[j], q[j] per dimension (meaning per family below), s0..s7 scalars.
+// The kernel keeps them in registers (per-dimension arrays are indexed with
+// compile-time indices after unrolling).
+struct FamilyConsts {
+    double p[32];
+    double q[32];
+    double s[8];
+};
+
+__device__ __forceinline__ float fexp2(float x) { return exp2f(x); }
+__device__ __forceinline__ double fexp2(double x) { return exp2(x); }
+__device__ __forceinline__ float flog2(float x) { return log2f(x); }
+__device__ __forceinline__ double flog2(double x) { return log2(x); }
+__device__ __forceinline__ float fcos(float x) { return cosf(x); }
+__device__ __forceinline__ double fcos(double x) { return cos(x); }
+__device__ __forceinline__ float frsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double frsqrt(double x) { return rsqrt(x); }
+__device__ __forceinline__ float frcp(float x) { return 1.0f / x; }
+__device__ __forceinline__ double frcp(double x) { return 1.0 / x; }
+
+// The integrand is split into a per-dimension update (called as each x_j is
+// produced) and a final step.  Normalisation constants that do not depend on
+// x (the Gaussian's (a sqrt(pi))^-d, the product-peak's scale) are folded into
+// the initial weight on the host, so the kernels return f up to that factor.
+//
+//   CONST        acc unused                        f = 1
+//   SUM          acc += x                          f = acc
+//   GAUSS_SYM    acc += (x - 1/2)^2                f = 2^(s0 acc), s0 = -log2(e)/a^2
+//   GENZ_OSC     acc += p_j x  (acc0 = 2 pi u)     f = cos(acc)
+//   GENZ_GAUSS   acc += (p_j (x - q_j))^2          f = 2^(-log2(e) acc), p_j = c_j
+//   GENZ_PROD    prod *= q_j^2... see below        f = 1/prod
+//   GENZ_CORNER  acc += p_j x  (acc0 = 1)          f = 2^(-(d+1) log2 acc)
+//   LO           x kept in registers               f from s0..s6
+template <int FAM, class T, int MAXD> struct Integrand {
+    T pj[MAXD];
+    T qj[MAXD];
+    T s0, s1, s2, s3, s4, s5, s6;
+    T acc;
+    T x0, x1, x2;
+
+    __device__ __forceinline__ void load(const FamilyConsts &fc, int d) {
+#pragma unroll
+        for (int j = 0; j < MAXD; ++j) {
+            pj[j] = static_cast<T>(j < d ? fc.p[j] : 0.0);
+            qj[j] = static_cast<T>(j < d ? fc.q[j] : 0.0);
+        }
+        s0 = static_cast<T>(fc.s[0]);
+        s1 = static_cast<T>(fc.s[1]);
+        s2 = static_cast<T>(fc.s[2]);
+        s3 = static_cast<T>(fc.s[3]);
+        s4 = static_cast<T>(fc.s[4]);
+        s5 = static_cast<T>(fc.s[5]);
+        s6 = static_cast<T>(fc.s[6]);
+    }
+
+    __device__ __forceinline__ void begin() {
+        if (FAM == F_GENZ_OSC) acc = s1;          // 2 pi u
+        else if (FAM == F_GENZ_CORNER) acc = T(1);
+        else if (FAM == F_GENZ_PROD) acc = T(1);
+        else acc = T(0);
+    }
+
+    __device__ __forceinline__ void dim(int j, T x) {
+        if (FAM == F_SUM) {
+            acc += x;
+        } else if (FAM == F_GAUSS_SYM) {
+            const T t = x - T(0.5);
+            acc = fma(t, t, acc);
+        } else if (FAM == F_GENZ_OSC || FAM == F_GENZ_CORNER) {
+            acc = fma(pj[j], x, acc);
+        } else if (FAM == F_GENZ_GAUSS) {
+            const T t = pj[j] * (x - qj[j]);
+            acc = fma(t, t, acc);
+        } else if (FAM == F_GENZ_PROD) {
+            // (c^-2 + (x-w)^2) c^2 = 1 + (c (x-w))^2; the c^2 factors are in
+            // the initial weight.  Multiply the denominators, invert once.
+            const T t = pj[j] * (x - qj[j]);
+            acc *= fma(t, t, T(1));
+        } else if (FAM == F_LO) {
+            if (j == 0) x0 = x;
+            else if (j == 1) x1 = x;
+            else if (j == 2) x2 = x;
+        }
+    }
+
+    __device__ __forceinline__ T finish(int d) {
+        if (FAM == F_CONST) return T(1);
+        if (FAM == F_SUM) return acc;
+        if (FAM == F_GAUSS_SYM) return fexp2(s0 * acc);
+        if (FAM == F_GENZ_OSC) return fcos(acc);
+        if (FAM == F_GENZ_GAUSS) return fexp2(s0 * acc);
+        if (FAM == F_GENZ_PROD) return frcp(acc);
+        if (FAM == F_GENZ_CORNER) return fexp2(s0 * flog2(acc));
+        if (FAM == F_LO) {
+            // s0 = sqrtS^2, s1 = M^2, s2 = (M Gamma)^2, s3 = cut,
+            // s4 = mll_lo^2, s5 = mll_hi^2; the constant 2 (35/32)^2 norm is
+            // in the initial weight.
+            const T shat = x0 * x1 * s0;
+            const T c = fma(T(2), x2, T(-1));
+            const bool in = (shat >= s4) && (shat <= s5) && (fabs(c) < s3);
+            const T om0 = T(1) - x0, om1 = T(1) - x1;
+            const T g = om0 * om0 * om0 * om1 * om1 * om1 * frsqrt(x0 * x1);
+            const T dm = shat - s1;
+            const T den = fma(dm, dm, s2) * shat;
+            const T val = g * fma(c, c, T(1)) * frcp(den);
+            return in ? val : T(0);
+        }
+        return T(0);
+    }
+};
+
+}  // namespace vegas

@@ -1,0 +1,62 @@
+// vegas_kernels.cuh -- declarations shared by the kernel translation units and
+// the C-ABI host code of the VEGAS library.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "vegas_sample.cuh"
+
+namespace vegas {
+
+// One record per iteration, written on the device by the finalize kernel.
+struct IterRec {
+    double I;
+    double sigma;
+    long long n;            // samples with finite weight
+    long long n_nonfinite;
+};
+
+// Running combination over all iterations so far (finalize kernel).
+struct CombRec {
+    double I;
+    double sigma;
+    double chi2_dof;
+    int n_iter;
+    int status;             // 0 ok, 6 = every weight of the last iteration non-finite
+};
+
+// Sampling kernel lookup: one translation unit per accumulation mode.
+// tier: 0 -> MAXD 4, 1 -> 8, 2 -> 16, 3 -> 32.
+const void *sample_kernel_f64(int fam, int tier, bool priv);
+const void *sample_kernel_f32sum64(int fam, int tier, bool priv);
+const void *sample_kernel_f32kahan(int fam, int tier, bool priv);
+
+inline int tier_of(int d) { return d <= 4 ? 0 : (d <= 8 ? 1 : (d <= 16 ? 2 : 3)); }
+
+size_t sample_smem(int mode, bool priv, int d, int N);
+
+// Finalize: move the accumulators (unscaled) to `last`, zero them, form
+// I_t and sigma_t, store iters[t] and recombine all iterations into *comb.
+cudaError_t launch_finalize(double *acc, double *last, unsigned long long *n_nonfinite,
+                            IterRec *iters, CombRec *comb, int t, long long n, int d, int N,
+                            double inv_scale, cudaStream_t stream);
+
+// Refine every dimension from the histograms in last[2..] and write the new
+// FP64 edges and the sampling table of the given mode.
+cudaError_t launch_refine(const double *last, double *edges, void *table, int mode, int d, int N,
+                          double alpha, int smooth, cudaStream_t stream);
+
+// Build the sampling table of `mode` from FP64 edges.
+cudaError_t launch_table_from_edges(const double *edges, void *table, int mode, int d, int N,
+                                    cudaStream_t stream);
+
+// Per-sample trace on the given table (same device arithmetic as sampling).
+cudaError_t launch_trace(const SampleArgs &a, int fam, int mode, double inv_scale, int32_t *bins,
+                         double *x, double *w, cudaStream_t stream);
+
+cudaError_t launch_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out, long long n,
+                          cudaStream_t stream);
+
+}  // namespace vegas

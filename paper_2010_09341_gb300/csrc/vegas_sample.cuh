@@ -1,0 +1,216 @@
+// vegas_sample.cuh -- the fused sample + map + integrand + accumulate kernel.
+//
+// One launch covers samples [s_begin, s_begin + n) of iteration t.  Each block
+// takes a contiguous range, each thread every blockDim-th sample of it.
+// Per sample (VEGAS, Lepage 1978; the paper's method, Sec. 1):
+//   r   = Philox4x32-10 words (ceil(d/4) calls, registers only)
+//   i_j = bin of r_j, x_j = (e - w)_j[i_j] + w_j[i_j] m_j,  m_j in [1, 2)
+//   J   = C prod_j w_j[i_j]            (C = N^d times constant factors of f)
+//   v   = J f(x);  S1 += v, S2 += v^2, h_j[i_j] += v^2
+//
+// Shared memory holds, per (dimension, bin) cell, TP copies of the table
+// entry (e - w, w) and HP copies of the histogram cell, so that the 32 lanes
+// of a warp read and update distinct banks whatever bins they draw
+// (lane-private copies).  When the copies do not fit, a single-copy layout is
+// used (PRIV = false) and bank conflicts are accepted.
+#pragma once
+
+#include "vegas_device.cuh"
+
+namespace vegas {
+
+enum AccMode : int { ACC_F64 = 0, ACC_F32_SUM64 = 1, ACC_F32_KAHAN = 2 };
+
+struct SampleArgs {
+    const void *table;        // [d][N] entries (e - w, w): double2 or float2
+    double *acc;              // [2 + d N] FP64 accumulators: S1, S2, histograms
+    unsigned long long *n_nonfinite;
+    long long s_begin;        // first sample index of this launch
+    long long n;              // samples in this launch
+    int d, N;
+    uint32_t key0, key1;      // Philox key (seed, integral id)
+    uint32_t iter;            // Philox counter word 2
+    double jinit;             // initial weight C (includes N^d and scale)
+    double nblk4;             // N^4 (FP32 path multiplies it in every 4 dims)
+    FamilyConsts fc;
+};
+
+template <int MODE> struct ModeTraits;
+template <> struct ModeTraits<ACC_F64> {
+    using T = double;   // map, Jacobian, integrand
+    using H = double;   // shared histogram cell
+    static constexpr int TP = 8;    // 16-byte entries: 8 lanes per wavefront
+    static constexpr int HP = 16;   // 8-byte cells: 16 lanes per wavefront
+};
+template <> struct ModeTraits<ACC_F32_SUM64> {
+    using T = float;
+    using H = double;
+    static constexpr int TP = 16;   // 8-byte entries
+    static constexpr int HP = 16;
+};
+template <> struct ModeTraits<ACC_F32_KAHAN> {
+    using T = float;
+    using H = float;
+    static constexpr int TP = 16;
+    static constexpr int HP = 32;   // 4-byte cells: a whole warp per wavefront
+};
+
+template <int MODE, bool PRIV>
+__host__ __device__ constexpr size_t sample_smem_bytes(int d, int N) {
+    using Tr = ModeTraits<MODE>;
+    return static_cast<size_t>(d) * N *
+           ((PRIV ? Tr::TP : 1) * 2 * sizeof(typename Tr::T) + (PRIV ? Tr::HP : 1) * sizeof(typename Tr::H));
+}
+
+__device__ __forceinline__ void red_add_shared(float *p, float v) { atomicAdd(p, v); }
+__device__ __forceinline__ void red_add_shared(double *p, double v) { atomicAdd(p, v); }
+
+// Warp-level FP64 sum.
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    return v;
+}
+
+template <int FAM, int MODE, int MAXD, bool PRIV>
+__global__ void __launch_bounds__(512)
+vegas_sample_kernel(const SampleArgs a) {
+    using Tr = ModeTraits<MODE>;
+    using T = typename Tr::T;
+    using T2 = typename Prec<T>::T2;
+    using H = typename Tr::H;
+    constexpr int TP = PRIV ? Tr::TP : 1;
+    constexpr int HP = PRIV ? Tr::HP : 1;
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int d = a.d;
+    const int N = a.N;
+    const int cells = d * N;
+    T2 *tab = reinterpret_cast<T2 *>(smem_raw);
+    H *hist = reinterpret_cast<H *>(smem_raw + static_cast<size_t>(cells) * TP * sizeof(T2));
+
+    // stage the grid table (TP copies per cell) and zero the histogram
+    const T2 *gtab = static_cast<const T2 *>(a.table);
+    for (int k = threadIdx.x; k < cells * TP; k += blockDim.x) tab[k] = gtab[k / TP];
+    for (int k = threadIdx.x; k < cells * HP; k += blockDim.x) hist[k] = H(0);
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31;
+    const T2 *tab_l = tab + (lane % TP);
+    H *hist_l = hist + (lane % HP);
+
+    Integrand<FAM, T, MAXD> fam;
+    fam.load(a.fc, d);
+    const T jinit = static_cast<T>(a.jinit);
+    const T n4 = static_cast<T>(a.nblk4);
+
+    // contiguous sample range of this block
+    const long long per = (a.n + gridDim.x - 1) / gridDim.x;
+    const long long lo = static_cast<long long>(blockIdx.x) * per;
+    const long long hi = min(a.n, lo + per);
+
+    double s1d = 0.0, s2d = 0.0;       // ACC_F64 / ACC_F32_SUM64
+    float s1f = 0.f, c1f = 0.f, s2f = 0.f, c2f = 0.f;  // ACC_F32_KAHAN
+    unsigned int nonfinite = 0;
+
+    for (long long k = lo + threadIdx.x; k < hi; k += blockDim.x) {
+        const unsigned long long s = static_cast<unsigned long long>(a.s_begin + k);
+        const uint32_t slo = static_cast<uint32_t>(s), shi = static_cast<uint32_t>(s >> 32);
+        uint32_t hoff[MAXD];
+        T J = jinit;
+        fam.begin();
+#pragma unroll
+        for (int q = 0; q < (MAXD + 3) / 4; ++q) {
+            if (4 * q < d) {
+                const uint4 r = philox4x32_10(make_uint4(slo, shi, a.iter, static_cast<uint32_t>(q)),
+                                              a.key0, a.key1);
+#pragma unroll
+                for (int w = 0; w < 4; ++w) {
+                    const int j = 4 * q + w;
+                    if (j < MAXD && j < d) {
+                        const Split sp = split_bin(word(r, w), static_cast<uint32_t>(N));
+                        const uint32_t cell = static_cast<uint32_t>(j * N) + sp.bin;
+                        const T2 ent = tab_l[cell * TP];
+                        const T m = Prec<T>::mant(sp.lo);
+                        const T x = fma(ent.y, m, ent.x);
+                        J *= ent.y;
+                        if (sizeof(T) == 4 && (j & 3) == 3) J *= n4;
+                        hoff[j] = cell * HP;
+                        fam.dim(j, x);
+                    }
+                }
+            }
+        }
+        T v = J * fam.finish(d);
+        if (!isfinite(v)) {
+            v = T(0);
+            ++nonfinite;
+        }
+        const T v2 = v * v;
+        if (MODE == ACC_F32_KAHAN) {
+            const float y1 = static_cast<float>(v) - c1f;
+            const float t1 = s1f + y1;
+            c1f = (t1 - s1f) - y1;
+            s1f = t1;
+            const float y2 = static_cast<float>(v2) - c2f;
+            const float t2 = s2f + y2;
+            c2f = (t2 - s2f) - y2;
+            s2f = t2;
+        } else {
+            const double vd = static_cast<double>(v);
+            s1d += vd;
+            s2d = fma(vd, vd, s2d);
+        }
+        const H hv = static_cast<H>(v2);
+#pragma unroll
+        for (int j = 0; j < MAXD; ++j) {
+            if (j < d) red_add_shared(hist_l + hoff[j], hv);
+        }
+    }
+
+    // block reduction of S1, S2 and the non-finite count
+    double b1, b2;
+    if (MODE == ACC_F32_KAHAN) {
+        b1 = static_cast<double>(s1f) - static_cast<double>(c1f);
+        b2 = static_cast<double>(s2f) - static_cast<double>(c2f);
+    } else {
+        b1 = s1d;
+        b2 = s2d;
+    }
+    b1 = warp_sum(b1);
+    b2 = warp_sum(b2);
+    unsigned int nf = __reduce_add_sync(0xFFFFFFFFu, nonfinite);
+    __shared__ double red1[16], red2[16];
+    __shared__ unsigned int rednf[16];
+    const int warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        red1[warp] = b1;
+        red2[warp] = b2;
+        rednf[warp] = nf;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        double x1 = lane < nw ? red1[lane] : 0.0;
+        double x2 = lane < nw ? red2[lane] : 0.0;
+        unsigned int xn = lane < nw ? rednf[lane] : 0u;
+        x1 = warp_sum(x1);
+        x2 = warp_sum(x2);
+        xn = __reduce_add_sync(0xFFFFFFFFu, xn);
+        if (lane == 0) {
+            atomicAdd(a.acc + 0, x1);
+            atomicAdd(a.acc + 1, x2);
+            if (xn) atomicAdd(a.n_nonfinite, static_cast<unsigned long long>(xn));
+        }
+    }
+    // histogram flush: one warp per cell, lanes over the HP copies
+    const int nwarps = blockDim.x >> 5;
+    for (int c = warp; c < cells; c += nwarps) {
+        double h = 0.0;
+        for (int k = lane; k < HP; k += 32) h += static_cast<double>(hist[c * HP + k]);
+        h = warp_sum(h);
+        if (lane == 0 && h != 0.0) atomicAdd(a.acc + 2 + c, h);
+    }
+}
+
+}  // namespace vegas

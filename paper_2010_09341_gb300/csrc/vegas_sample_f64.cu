@@ -1,0 +1,6 @@
+// Sampling kernels of mode ACC_F64 (see vegas_sample.cuh).
+#include "vegas_pick.cuh"
+
+namespace vegas {
+const void *sample_kernel_f64(int fam, int tier, bool priv) { return pick_kernel<ACC_F64>(fam, tier, priv); }
+}  // namespace vegas

@@ -1,0 +1,225 @@
+"""Python face of the C ABI: the same call names as ``include/vegas.h``.
+
+Marshalling only.  Device memory (the workspace, trace outputs) comes from
+PyTorch; the stream is PyTorch's current CUDA stream unless one is given.
+:class:`Integrator` mirrors the paper's usage (Sec. 3.1): construct with
+``n_dim``, ``n_events`` and ``events_limit``, ``compile`` an integrand,
+``run_integration(n_iter)``.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _native as nat
+from ._native import check
+
+
+@dataclass
+class Config:
+    n_dim: int
+    n_events: int
+    n_bins: int = 50
+    events_limit: int = 0
+    alpha: float = 1.5
+    seed: int = 0
+    integral_id: int = 0
+    precision: str = "fp32_kahan"
+    smooth: bool = True
+
+    def to_c(self) -> nat.VegasConfig:
+        return nat.VegasConfig(int(self.n_dim), int(self.n_bins), int(self.n_events),
+                               int(self.events_limit), float(self.alpha), int(self.seed),
+                               int(self.integral_id), nat.PRECISIONS[self.precision],
+                               1 if self.smooth else 0)
+
+
+class Context:
+    """A live vegas_ctx plus the PyTorch workspace it points into."""
+
+    def __init__(self, handle, cfg: Config, family: str, params, workspace, stream):
+        self.handle = handle
+        self.cfg = cfg
+        self.family = family
+        self.params = np.asarray(params, dtype=np.float64)
+        self.workspace = workspace
+        self.stream = stream
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            try:
+                nat.load().vegas_destroy(h)
+            except Exception:
+                pass
+            self.handle = None
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream, ctypes.c_void_p(stream.cuda_stream)
+
+
+def vegas_workspace_bytes(cfg: Config) -> int:
+    c = cfg.to_c()
+    return int(nat.load().vegas_workspace_bytes(ctypes.byref(c)))
+
+
+def vegas_create(cfg: Config, family: str, params=(), stream=None, workspace=None) -> Context:
+    lib = nat.load()
+    c = cfg.to_c()
+    nbytes = lib.vegas_workspace_bytes(ctypes.byref(c))
+    if nbytes == 0:
+        raise nat.VegasError(nat.VEGAS_EINVAL, "vegas_workspace_bytes")
+    if workspace is None:
+        workspace = torch.empty(int(nbytes), dtype=torch.uint8, device="cuda")
+    p = np.ascontiguousarray(np.asarray(params, dtype=np.float64))
+    itg = nat.VegasIntegrand(nat.FAMILIES[family], int(cfg.n_dim),
+                             p.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if p.size else None,
+                             int(p.size))
+    stream, sp = _stream_ptr(stream)
+    h = ctypes.c_void_p()
+    check(lib.vegas_create(ctypes.byref(c), ctypes.byref(itg), sp,
+                           ctypes.c_void_p(workspace.data_ptr()), ctypes.c_size_t(workspace.numel()),
+                           ctypes.byref(h)), "vegas_create")
+    return Context(h, cfg, family, p, workspace, stream)
+
+
+def vegas_iterate(ctx: Context, sync: bool = True):
+    """One iteration; with sync returns (I, sigma, n, n_nonfinite)."""
+    lib = nat.load()
+    if not sync:
+        check(lib.vegas_iterate(ctx.handle, None), "vegas_iterate")
+        return None
+    r = nat.VegasIterResult()
+    st = lib.vegas_iterate(ctx.handle, ctypes.byref(r))
+    if st not in (nat.VEGAS_OK, nat.VEGAS_ENONFINITE):
+        check(st, "vegas_iterate")
+    return r.I, r.sigma, r.n, r.n_nonfinite
+
+
+def vegas_refine(ctx: Context):
+    check(nat.load().vegas_refine(ctx.handle), "vegas_refine")
+
+
+def vegas_result(ctx: Context):
+    r = nat.VegasResult()
+    check(nat.load().vegas_result(ctx.handle, ctypes.byref(r)), "vegas_result")
+    return {"I": r.I, "sigma": r.sigma, "chi2_dof": r.chi2_dof, "n_iter": r.n_iter}
+
+
+def vegas_run(ctx: Context, n_iter: int):
+    its = (nat.VegasIterResult * n_iter)()
+    r = nat.VegasResult()
+    check(nat.load().vegas_run(ctx.handle, int(n_iter), its, ctypes.byref(r)), "vegas_run")
+    return {"I": r.I, "sigma": r.sigma, "chi2_dof": r.chi2_dof, "n_iter": r.n_iter,
+            "iters": [(x.I, x.sigma, x.n, x.n_nonfinite) for x in its]}
+
+
+def vegas_get_grid(ctx: Context) -> np.ndarray:
+    d, N = ctx.cfg.n_dim, ctx.cfg.n_bins
+    e = np.zeros((d, N + 1), dtype=np.float64)
+    check(nat.load().vegas_get_grid(ctx.handle, e.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+          "vegas_get_grid")
+    return e
+
+
+def vegas_set_grid(ctx: Context, edges) -> None:
+    d, N = ctx.cfg.n_dim, ctx.cfg.n_bins
+    e = np.ascontiguousarray(np.asarray(edges, dtype=np.float64).reshape(d, N + 1))
+    check(nat.load().vegas_set_grid(ctx.handle, e.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+          "vegas_set_grid")
+
+
+def vegas_get_sums(ctx: Context):
+    """(S1, S2, hist[d, N]) of the last iteration, FP64."""
+    d, N = ctx.cfg.n_dim, ctx.cfg.n_bins
+    s = np.zeros(2 + d * N, dtype=np.float64)
+    check(nat.load().vegas_get_sums(ctx.handle, s.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+          "vegas_get_sums")
+    return s[0], s[1], s[2:].reshape(d, N)
+
+
+def vegas_get_iteration(ctx: Context) -> int:
+    t = ctypes.c_int32()
+    check(nat.load().vegas_get_iteration(ctx.handle, ctypes.byref(t)), "vegas_get_iteration")
+    return int(t.value)
+
+
+def vegas_set_iteration(ctx: Context, t: int) -> None:
+    check(nat.load().vegas_set_iteration(ctx.handle, int(t)), "vegas_set_iteration")
+
+
+def vegas_trace(ctx: Context, t: int, s_begin: int, count: int):
+    """Per-sample (bins[count, d] int32, x[count, d] f64, w[count] f64) as CUDA tensors."""
+    d = ctx.cfg.n_dim
+    bins = torch.empty((count, d), dtype=torch.int32, device="cuda")
+    x = torch.empty((count, d), dtype=torch.float64, device="cuda")
+    w = torch.empty((count,), dtype=torch.float64, device="cuda")
+    check(nat.load().vegas_trace(ctx.handle, int(t), int(s_begin), int(count),
+                                 ctypes.c_void_p(bins.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                                 ctypes.c_void_p(w.data_ptr())), "vegas_trace")
+    return bins, x, w
+
+
+def vegas_export_state(ctx: Context) -> bytes:
+    lib = nat.load()
+    size = ctypes.c_size_t(0)
+    check(lib.vegas_export_state(ctx.handle, None, ctypes.byref(size)), "vegas_export_state")
+    buf = ctypes.create_string_buffer(size.value)
+    check(lib.vegas_export_state(ctx.handle, buf, ctypes.byref(size)), "vegas_export_state")
+    return buf.raw[: size.value]
+
+
+def vegas_import_state(ctx: Context, blob: bytes) -> None:
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    check(nat.load().vegas_import_state(ctx.handle, buf, ctypes.c_size_t(len(blob))),
+          "vegas_import_state")
+
+
+def vegas_philox(ctr: torch.Tensor, key: torch.Tensor, stream=None) -> torch.Tensor:
+    """Device Philox4x32-10: ctr (n, 4) and key (n, 2) int32/uint32 CUDA tensors."""
+    assert ctr.is_cuda and key.is_cuda and ctr.shape[-1] == 4 and key.shape[-1] == 2
+    ctr = ctr.contiguous()
+    key = key.contiguous()
+    out = torch.empty_like(ctr)
+    _, sp = _stream_ptr(stream)
+    check(nat.load().vegas_philox(ctypes.c_void_p(ctr.data_ptr()), ctypes.c_void_p(key.data_ptr()),
+                                  ctypes.c_void_p(out.data_ptr()), int(ctr.shape[0]), sp),
+          "vegas_philox")
+    return out
+
+
+def vegas_destroy(ctx: Context) -> None:
+    if ctx.handle:
+        nat.load().vegas_destroy(ctx.handle)
+        ctx.handle = None
+
+
+class Integrator:
+    """The paper's usage pattern (Sec. 3.1) over the C ABI.
+
+    >>> it = Integrator(n_dim=10, n_events=10**6, events_limit=10**5)
+    >>> it.compile("sum")
+    >>> res = it.run_integration(n_iter=5)
+    """
+
+    def __init__(self, n_dim, n_events, events_limit=0, n_bins=50, alpha=1.5, seed=0,
+                 integral_id=0, precision="fp32_kahan", smooth=True, stream=None):
+        self.cfg = Config(n_dim, n_events, n_bins, events_limit, alpha, seed, integral_id,
+                          precision, smooth)
+        self.stream = stream
+        self.ctx = None
+
+    def compile(self, family: str, params=()):
+        self.ctx = vegas_create(self.cfg, family, params, stream=self.stream)
+        return self
+
+    def run_integration(self, n_iter: int):
+        if self.ctx is None:
+            raise RuntimeError("compile() an integrand first")
+        return vegas_run(self.ctx, n_iter)

@@ -1,0 +1,279 @@
+"""GPU path (C ABI, sm_103a kernels) against the FP64 oracle.
+
+Tolerances (stated per quantity):
+  * bin indices and Philox words: bit-exact (integer work);
+  * iteration estimate I_t: relative 1e-12 for the FP64 path, 1e-5 for the
+    FP32 paths, on the same input grid;
+  * S2 and the histograms (normalised by their sum): same tolerances;
+  * refined edges from identical histograms: absolute 1e-13.
+"""
+import ctypes
+import math
+
+import numpy as np
+import pytest
+
+import closed_forms as CF
+import oracle as O
+from gpu_helpers import PRECS, TOL, curand_ref_lib, native, params_for, random_grid
+
+pytestmark = pytest.mark.gpu
+
+
+def _make(V, family, d, N, n, prec, seed=0, iid=0, limit=0, alpha=1.5, params=None):
+    p = params_for(family, d) if params is None else params
+    cfg = V.Config(n_dim=d, n_events=n, n_bins=N, events_limit=limit, alpha=alpha, seed=seed,
+                   integral_id=iid, precision=prec)
+    return V.vegas_create(cfg, family, p), p
+
+
+# ------------------------------------------------------------------ Philox
+def test_device_philox_matches_oracle_and_curand():
+    V = native()
+    import torch
+    rng = np.random.default_rng(11)
+    n = 1 << 20
+    ctr = rng.integers(0, 2 ** 32, size=(n, 4), dtype=np.uint64).astype(np.uint32)
+    key = rng.integers(0, 2 ** 32, size=(n, 2), dtype=np.uint64).astype(np.uint32)
+    ctr[:16] = 0
+    key[:16] = 0
+    ctr[16:32] = 0xFFFFFFFF
+    key[16:32] = 0xFFFFFFFF
+    tc = torch.from_numpy(ctr.view(np.int32)).cuda()
+    tk = torch.from_numpy(key.view(np.int32)).cuda()
+    mine = V.vegas_philox(tc, tk).cpu().numpy().view(np.uint32)
+    torch.cuda.synchronize()
+    ref = O.philox_many(ctr, key)
+    assert np.array_equal(mine, ref)
+    lib = curand_ref_lib()
+    out = torch.empty_like(tc)
+    assert lib.curand_ref_philox(ctypes.c_void_p(tc.data_ptr()), ctypes.c_void_p(tk.data_ptr()),
+                                 ctypes.c_void_p(out.data_ptr()), n) == 0
+    assert np.array_equal(mine, out.cpu().numpy().view(np.uint32))
+
+
+# ---------------------------------------------------------- per-sample trace
+TRACE_CASES = [("gauss_sym", 4, 50), ("genz_osc", 8, 50), ("genz_gauss", 5, 17),
+               ("genz_prod", 9, 64), ("genz_corner", 16, 50), ("sum", 20, 10),
+               ("lo", 3, 100), ("const", 32, 2)]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("family,d,N", TRACE_CASES)
+def test_trace_bins_bit_exact(family, d, N, prec):
+    V = native()
+    ctx, p = _make(V, family, d, N, 1000, prec, seed=5, iid=9)
+    e = random_grid(d, N, seed=d * N)
+    V.vegas_set_grid(ctx, e)
+    t = 3
+    starts = [(0, 1500), ((1 << 32) - 700, 1400)]  # crosses the s_hi word
+    for s0, cnt in starts:
+        bins, x, w = V.vegas_trace(ctx, t, s0, cnt)
+        bins, x, w = bins.cpu().numpy(), x.cpu().numpy(), w.cpu().numpy()
+        ks = list(range(0, cnt, 7 if d > 8 else 3))
+        vs = []
+        for k in ks:
+            ob, ox, J, f = O.sample(d, N, e, family, p, 5, 9, t, s0 + k)
+            assert np.array_equal(bins[k], ob), (k, bins[k], ob)
+            if prec == "fp64":
+                assert np.allclose(x[k], ox, rtol=0, atol=4e-16)
+            else:
+                assert np.allclose(x[k], ox, rtol=0, atol=3e-7)
+            vs.append(J * f)
+        vs = np.array(vs)
+        ws = w[ks]
+        if prec == "fp64":
+            assert np.all(np.abs(ws - vs) <= 1e-13 * np.abs(vs) + 1e-300)
+        else:
+            # FP32 per-sample error is relative to the integrand's scale: where
+            # f is tiny (tails, zeros of cos, (1-x)^3 near x = 1) cancellation
+            # makes its own relative error large.
+            scale = np.mean(np.abs(vs))
+            ok = np.abs(ws - vs) <= 2e-5 * np.abs(vs) + 2e-6 * scale
+            if family == "lo":  # cut edges within FP32 rounding of a point
+                ok |= (vs == 0.0) != (ws == 0.0)
+            assert np.all(ok), np.max(np.abs(ws - vs) / (np.abs(vs) + scale))
+
+
+# --------------------------------------------------------------- iteration
+ITER_CASES = [("gauss_sym", 4, 50, 100_000), ("genz_osc", 8, 50, 200_003),
+              ("genz_gauss", 5, 50, 50_033), ("genz_prod", 9, 30, 77_777),
+              ("genz_corner", 6, 50, 100_000), ("sum", 10, 50, 65_536),
+              ("lo", 3, 100, 300_000), ("const", 3, 2, 2), ("gauss_sym", 1, 1024, 4099),
+              ("genz_gauss", 32, 20, 20_011)]
+
+
+def _compare_iteration(V, ctx, p, family, d, N, n, prec, e, t, seed=0, iid=0):
+    I, sigma, n_ok, n_nf = V.vegas_iterate(ctx)
+    S1, S2, h = V.vegas_get_sums(ctx)
+    acc = O.iterate(d, N, e, family, p, seed, iid, t, n, threads=8)
+    Io, var = O.iteration_result(acc["S1"], acc["S2"], n - acc["n_nonfinite"])
+    tol = TOL[prec]
+    assert n_nf == acc["n_nonfinite"] == 0
+    assert abs(I - Io) <= tol * abs(Io) + 1e-300, (I, Io)
+    assert abs(S2 - acc["S2"]) <= tol * abs(acc["S2"]) + 1e-300
+    hs = acc["hist"].sum()
+    if hs > 0:
+        assert np.max(np.abs(h - acc["hist"])) <= tol * hs, np.max(np.abs(h - acc["hist"])) / hs
+    if var > 0 and prec == "fp64":
+        assert abs(sigma - math.sqrt(var)) <= 1e-9 * math.sqrt(var)
+    return acc
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("family,d,N,n", ITER_CASES)
+def test_iteration_parity_on_shared_grid(family, d, N, n, prec):
+    if family == "lo" and prec != "fp64":
+        pytest.skip("LO cuts: FP32 points within rounding of a cut edge; covered below")
+    V = native()
+    ctx, p = _make(V, family, d, N, n, prec)
+    e = random_grid(d, N, seed=1, spread=0.5)
+    V.vegas_set_grid(ctx, e)
+    _compare_iteration(V, ctx, p, family, d, N, n, prec, e, 0)
+
+
+@pytest.mark.parametrize("prec", ["fp32_acc64", "fp32_kahan"])
+def test_lo_fp32_parity(prec):
+    """The LO toy has hard cuts: the FP32 path may classify a point within
+    rounding of a cut differently.  The estimate still agrees to 1e-4 and the
+    histograms to 1e-4 of their sum."""
+    V = native()
+    d, N, n = 3, 100, 300_000
+    ctx, p = _make(V, "lo", d, N, n, prec)
+    e = O.uniform_edges(d, N)
+    I, _, _, _ = V.vegas_iterate(ctx)
+    _, _, h = V.vegas_get_sums(ctx)
+    acc = O.iterate(d, N, e, "lo", p, 0, 0, 0, n, threads=8)
+    Io = acc["S1"] / n
+    assert abs(I - Io) <= 1e-4 * abs(Io)
+    assert np.max(np.abs(h - acc["hist"])) <= 1e-4 * acc["hist"].sum()
+
+
+def test_refine_parity_from_identical_histograms():
+    V = native()
+    for prec in PRECS:
+        d, N, n = 6, 50, 200_000
+        ctx, p = _make(V, "genz_gauss", d, N, n, prec)
+        e = random_grid(d, N, seed=3, spread=0.3)
+        V.vegas_set_grid(ctx, e)
+        V.vegas_iterate(ctx)
+        _, _, h = V.vegas_get_sums(ctx)
+        V.vegas_refine(ctx)
+        eg = V.vegas_get_grid(ctx)
+        eo = O.refine(d, N, h, e, 1.5)
+        assert np.max(np.abs(eg - eo)) < 1e-13
+        assert np.all(eg[:, 0] == 0.0) and np.all(eg[:, -1] == 1.0)
+        assert np.all(np.diff(eg, axis=1) >= 0)
+
+
+def test_full_run_fp64_matches_oracle_every_iteration():
+    """Configuration: d = 4 symmetric Gaussian a = 0.1, 50 bins, 1e5 samples,
+    5 iterations, alpha = 1.5, seed 0, FP64 throughout.  Every iteration,
+    the refined grids and the combination agree with the oracle to 1e-12; the
+    result is within 3 sigma of erf(5)^4."""
+    V = native()
+    d, N, n, m = 4, 50, 100_000, 5
+    ctx, p = _make(V, "gauss_sym", d, N, n, "fp64")
+    res = V.vegas_run(ctx, m)
+    ref = O.integrate(d, N, "gauss_sym", p, n, m, alpha=1.5, seed=0)
+    for (I, s, _, _), (Io, so) in zip(res["iters"], ref["iters"]):
+        assert abs(I - Io) <= 1e-12 * abs(Io)
+        assert abs(s - so) <= 1e-9 * so
+    assert abs(res["I"] - ref["I"]) <= 1e-12 * abs(ref["I"])
+    assert abs(res["sigma"] - ref["sigma"]) <= 1e-9 * ref["sigma"]
+    assert abs(res["chi2_dof"] - ref["chi2_dof"]) <= 1e-6 * max(1.0, ref["chi2_dof"])
+    assert abs(res["I"] - CF.gauss_sym(4, 0.1)) < 3 * res["sigma"]
+
+
+@pytest.mark.parametrize("prec", ["fp32_acc64", "fp32_kahan"])
+def test_fp32_run_per_iteration_on_gpu_grid(prec):
+    """FP32 runs diverge from FP64 ones through the grid; per iteration, with
+    the oracle fed the GPU's own grid, the estimates agree to 1e-5, and the
+    combined result is within 3 sigma of the closed form."""
+    V = native()
+    d, N, n, m = 8, 50, 200_000, 6
+    ctx, p = _make(V, "gauss_sym", d, N, n, prec)
+    for t in range(m):
+        e = V.vegas_get_grid(ctx)
+        _compare_iteration(V, ctx, p, "gauss_sym", d, N, n, prec, e, t)
+        V.vegas_refine(ctx)
+    r = V.vegas_result(ctx)
+    assert r["n_iter"] == m
+    assert abs(r["I"] - CF.gauss_sym(8, 0.1)) < 3 * r["sigma"]
+
+
+def test_events_limit_split_matches_single_launch():
+    V = native()
+    d, N, n = 5, 50, 123_457
+    a, p = _make(V, "genz_prod", d, N, n, "fp64")
+    b, _ = _make(V, "genz_prod", d, N, n, "fp64", limit=10_000)
+    ra = V.vegas_run(a, 3)
+    rb = V.vegas_run(b, 3)
+    for x, y in zip(ra["iters"], rb["iters"]):
+        assert abs(x[0] - y[0]) <= 1e-13 * abs(x[0])
+    assert np.max(np.abs(V.vegas_get_grid(a) - V.vegas_get_grid(b))) < 1e-13
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_kahan"])
+def test_checkpoint_resume(prec):
+    """Export after 3 iterations, continue 2 more; a fresh context that imports
+    the blob and runs 2 iterations gives the same results.  Shared-memory
+    atomics add in a run-dependent order, so equality holds to the path's
+    rounding (FP64 1e-12, FP32 1e-6), not bit for bit."""
+    V = native()
+    d, N, n = 6, 40, 60_000
+    a, p = _make(V, "genz_gauss", d, N, n, prec)
+    V.vegas_run(a, 3)
+    V.vegas_refine(a)
+    blob = V.vegas_export_state(a)
+    ra = V.vegas_run(a, 2)
+    b, _ = _make(V, "genz_gauss", d, N, n, prec)
+    V.vegas_import_state(b, blob)
+    assert V.vegas_get_iteration(b) == 3
+    rb = V.vegas_run(b, 2)
+    tol = 1e-12 if prec == "fp64" else 1e-6
+    for x, y in zip(ra["iters"], rb["iters"]):
+        assert abs(x[0] - y[0]) <= tol * abs(x[0]) and x[2:] == y[2:]
+    assert np.max(np.abs(V.vegas_get_grid(a) - V.vegas_get_grid(b))) < (1e-13 if prec == "fp64" else 1e-6)
+    assert rb["n_iter"] == 5 and abs(ra["I"] - rb["I"]) <= tol * abs(ra["I"])
+
+
+def test_integrator_paper_usage_sum_toy():
+    """The usage of Sec. 3.1: n_dim = 10, n_events = 1e6, events_limit = 1e5,
+    f = sum x_i, 5 iterations; the exact value is 5."""
+    V = native()
+    it = V.Integrator(n_dim=10, n_events=10 ** 6, events_limit=10 ** 5, precision="fp32_kahan")
+    it.compile("sum")
+    r = it.run_integration(n_iter=5)
+    assert abs(r["I"] - 5.0) < 3 * r["sigma"]
+    assert r["sigma"] < 1e-3
+
+
+def test_invalid_arguments_rejected():
+    V = native()
+    from paper_2010_09341_gb300 import _native as nat
+    with pytest.raises(nat.VegasError):
+        V.vegas_create(V.Config(n_dim=3, n_events=1000), "genz_gauss", [1.0, 2.0])
+    with pytest.raises(nat.VegasError):
+        V.vegas_create(V.Config(n_dim=4, n_events=1000), "lo", params_for("lo", 3))
+    ctx, _ = _make(V, "gauss_sym", 2, 10, 1000, "fp64")
+    bad = O.uniform_edges(2, 10)
+    bad[0, 3] = 0.9
+    with pytest.raises(nat.VegasError):
+        V.vegas_set_grid(ctx, bad)
+
+
+# -------------------------------------------------------- full-size checks
+@pytest.mark.parametrize("family", ["gauss_sym", "genz_osc"])
+@pytest.mark.parametrize("prec", ["fp32_acc64", "fp64"])
+def test_full_size_d8_iteration(family, prec):
+    """d = 8, 50 bins, 1e7 samples, the launch configuration the benchmark
+    times: the whole iteration against the oracle run on all host cores."""
+    import os
+    V = native()
+    d, N, n = 8, 50, 10_000_000
+    p = params_for(family, d, seed=1) if family == "genz_osc" else params_for(family, d)
+    ctx, _ = _make(V, family, d, N, n, prec, params=p)
+    e = random_grid(d, N, seed=2, spread=0.4)
+    V.vegas_set_grid(ctx, e)
+    _compare_iteration(V, ctx, p, family, d, N, n, prec, e, 0)
