@@ -1,0 +1,379 @@
+#!/usr/bin/env python
+"""Benchmark of one VEGAS iteration on GB300 (sm_103a) through the C ABI.
+
+Workload (one step = one Vegas iteration, sampling + finalize + refine, of two
+integrals, 2e7 samples in all):
+  * d = 8 symmetric Gaussian f = (a sqrt(pi))^-8 exp(-sum (x - 1/2)^2/a^2), a = 0.1
+  * d = 8 Genz oscillatory f = cos(2 pi 0.3 + sum c_i x_i), c_i ~ U(0, 1), seed 1
+  * 50 bins per dimension, 1e7 samples per iteration each, alpha = 1.5,
+  * FP32 sampling / grid map / integrand, FP64 accumulators (VEGAS_FP32_ACC64).
+The paper's own workload (the single-top LO integrand, Sec. 3.1) is not
+available; these seeded synthetic integrands stand in for it.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle instead, on the host cores, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Vegas samples/s (% of roofline)"
+UNIT = "samples/s"
+D, NBINS, NEVENTS, ALPHA = 8, 50, 10_000_000, 1.5
+PRECISION = "fp32_acc64"
+WORKLOAD = "d=8 Gaussian a=0.1 + d=8 Genz oscillatory (c~U(0,1) seed 1), 50 bins, 1e7 samples/iter each, FP32 sampling, FP64 accumulators"
+
+# Nominal unit counts used for the issue roofline (derived, per SM per clock).
+ISSUE_PER_SM_CLK = 128.0      # 4 schedulers x 32 lanes: one warp instruction each per clock
+MUFU_PER_SM_CLK = 16.0        # special-function lanes
+FP64_TFLOPS_NOMINAL = 1.25    # GB300 dense FP64 (FMA = 2 flop)
+
+
+def _integrals():
+    from paper_2010_09341_gb300 import workloads as W
+    return [("gauss_sym", W.gauss_sym_params(0.1)), ("genz_osc", W.genz_osc_params(D, seed=1))]
+
+
+# ------------------------------------------------------------- op counting
+def ops_per_sample(family: str, d: int, precision: str):
+    """Algorithmic operations of one sample, by pipe (thread-level counts).
+
+    Philox4x32-10: 10 rounds x (2 wide multiplies + 2 three-input xors) per
+    4 words (round keys are per-thread constants).  Per dimension: 1 wide
+    multiply (bin split), 2 (mantissa build), 1 table address, 1 table load,
+    1 FMA (x), 1 multiply (J), 1 histogram address, 1 shared atomic, plus the
+    integrand's per-dimension ops; J *= N^4 once per 4 dimensions.  Per
+    sample: integrand finish, v = J f, v^2, non-finite test (2), the two sums
+    (FP64: convert + add + FMA; Kahan: 8 FP32 ops), loop (3).
+    """
+    per_dim_f = {"gauss_sym": 2, "genz_osc": 1, "genz_gauss": 3, "genz_prod": 4,
+                 "genz_corner": 1, "sum": 1, "const": 0, "lo": 0}[family]
+    finish = {"gauss_sym": 2, "genz_osc": 4, "genz_gauss": 2, "genz_prod": 1,
+              "genz_corner": 3, "sum": 0, "const": 0, "lo": 20}[family]
+    mufu = {"gauss_sym": 1, "genz_osc": 1, "genz_gauss": 1, "genz_prod": 1,
+            "genz_corner": 2, "sum": 0, "const": 0, "lo": 2}[family]
+    philox = 40 * math.ceil(d / 4)
+    per_dim = (9 + per_dim_f) * d + d // 4
+    fp64 = 0
+    if precision == "fp32_kahan":
+        acc = 8
+    else:
+        acc = 3
+        fp64 = 3
+    total = philox + per_dim + finish + 2 + 2 + acc + 3
+    return {"total": total, "fp64": fp64, "mufu": mufu}
+
+
+def roofline_samples_per_s(ops, sms: int, clk_hz: float) -> dict:
+    """min over pipes of SMs x clock x rate / ops-per-sample."""
+    fp64_per_sm_clk = FP64_TFLOPS_NOMINAL * 1e12 / 2.0 / (sms * clk_hz)
+    bounds = {"issue": sms * clk_hz * ISSUE_PER_SM_CLK / ops["total"]}
+    if ops["fp64"]:
+        bounds["fp64"] = sms * clk_hz * fp64_per_sm_clk / ops["fp64"]
+    if ops["mufu"]:
+        bounds["mufu"] = sms * clk_hz * MUFU_PER_SM_CLK / ops["mufu"]
+    return bounds
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self._t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------- reference arm
+def oracle_rate(threads: int, seconds: float = 0.3):
+    """Calibration: oracle samples/s on ``threads`` host threads."""
+    import oracle as O
+    e = O.uniform_edges(D, NBINS)
+    n = 5_000 * threads
+    done = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        for fam, p in _integrals():
+            O.iterate(D, NBINS, e, fam, p, 0, 1, 0, n, threads=threads)
+            done += n
+    return done / (time.perf_counter() - t0)
+
+
+def oracle_samples_per_s(seconds: float, threads: int, rate=None, t=0):
+    """Time the FP64 oracle on host threads over a bounded sample of the
+    workload (both integrals, iteration t, uniform grid), about ``seconds``."""
+    import oracle as O
+    e = O.uniform_edges(D, NBINS)
+    if rate is None:
+        rate = oracle_rate(threads)
+    n = max(threads * 100, int(rate * seconds / 2))
+    t0 = time.perf_counter()
+    for k, (fam, p) in enumerate(_integrals()):
+        O.iterate(D, NBINS, e, fam, p, 0, k, t, n, threads=threads)
+    dt = time.perf_counter() - t0
+    return 2 * n / dt, 2 * n, dt
+
+
+def run_reference(args):
+    """The oracle as it stands, timed on this host's cores: each step a
+    bounded sample of the workload, the whole run sized to a few minutes."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    threads = os.cpu_count() or 1
+    rate = oracle_rate(threads)
+    per_step_s = min(args.ref_seconds, 120.0 / max(1, args.steps + args.warmup))
+    for w in range(args.warmup):
+        oracle_samples_per_s(per_step_s, threads, rate, t=w)
+    per_step = []
+    n_total = 0
+    for k in range(args.steps):
+        _, n, dt = oracle_samples_per_s(per_step_s, threads, rate, t=k)
+        per_step.append(dt)
+        n_total += n
+    value = n_total / sum(per_step)
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sum(per_step) / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "parallelism": "host threads",
+                   "sample": "each step: %d samples per integral, grid uniform"
+                   % (n_total // (2 * args.steps))},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": "%d samples over %d steps (%.1f s)"
+                         % (n_total, args.steps, sum(per_step))},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+    return 0
+
+
+# ----------------------------------------------------------------- GPU arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    assert args.warmup >= 3, "at least 3 warm-up steps"
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    from paper_2010_09341_gb300 import build as B
+    if rank == 0:
+        B.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2010_09341_gb300 import vegas as V
+
+    stream = torch.cuda.current_stream()
+    ctxs = []
+    for k, (fam, p) in enumerate(_integrals()):
+        cfg = V.Config(n_dim=D, n_events=NEVENTS, n_bins=NBINS, alpha=ALPHA, seed=0,
+                       integral_id=rank * 2 + k, precision=PRECISION)
+        ctxs.append(V.vegas_create(cfg, fam, p, stream=stream))
+    samples_per_step = NEVENTS * len(ctxs)
+    l2_flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def step():
+        for c in ctxs:
+            V.vegas_iterate(c, sync=False)
+            V.vegas_refine(c)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    for c in ctxs:
+        V.vegas_profile(c, True)
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        l2_flush.zero_()  # L2 flush between steps, outside the step events
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    kern_ms = {c.family: V.vegas_profile_read(c) for c in ctxs}
+    for c in ctxs:
+        V.vegas_profile(c, False)
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    max_ms = float(t.item())
+    value = world * samples_per_step * args.steps / (max_ms / 1e3)
+
+    # ---- roofline of the dominant kernel (the sampling kernel)
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    sms = props.multi_processor_count
+    clk_max_hz = (clk.get("sm_max_mhz") or 2070.0) * 1e6
+    per_fam = {}
+    ach_ops = 0.0      # algorithmic ops executed by the timed sampling launches
+    roof_s = 0.0       # time those launches would take at the roofline
+    kern_total_ms = 0.0
+    for c in ctxs:
+        ms = kern_ms[c.family]
+        mean_ms = sum(ms) / max(1, len(ms))
+        ops = ops_per_sample(c.family, D, PRECISION)
+        bounds = roofline_samples_per_s(ops, sms, clk_max_hz)
+        roof = min(bounds.values())
+        ach = NEVENTS / (mean_ms / 1e3)
+        per_fam[c.family] = {"kernel_ms": mean_ms, "samples_per_s": ach, "ops_per_sample": ops,
+                             "roofline_samples_per_s": roof,
+                             "bound_pipe": min(bounds, key=bounds.get),
+                             "frac": ach / roof}
+        ach_ops += ops["total"] * NEVENTS * len(ms)
+        roof_s += NEVENTS * len(ms) / roof
+        kern_total_ms += sum(ms)
+    achieved_gops = ach_ops / (kern_total_ms / 1e3) / 1e9
+    peak_gops = ach_ops / roof_s / 1e9
+    roofline = {"bound": "alu", "achieved": achieved_gops, "peak": peak_gops, "unit": "Gop/s",
+                "frac": achieved_gops / peak_gops, "traffic": None,
+                "kernel": "vegas_sample_kernel", "peak_basis":
+                "min over pipes (issue 128/clk/SM, FP64 %.2f TFLOP/s, MUFU 16/clk/SM) at %d SMs x %.0f MHz (max clock)"
+                % (FP64_TFLOPS_NOMINAL, sms, clk_max_hz / 1e6), "per_integral": per_fam}
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        grids = [np.ascontiguousarray(V.vegas_get_grid(c)) for c in ctxs]
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            for c, g in zip(ctxs, grids):
+                V.vegas_set_grid(c, g)        # host -> device: grid state
+                V.vegas_iterate(c, sync=True)  # device -> host: iteration result
+                V.vegas_refine(c)
+                g[...] = V.vegas_get_grid(c)  # device -> host: refined grid
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        tt = torch.tensor([dt], dtype=torch.float64, device="cuda")
+        if world > 1:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        dt = float(tt.item())
+        gbytes = sum(8 * c.cfg.n_dim * (c.cfg.n_bins + 1) for c in ctxs)
+        e2e = {"value": world * samples_per_step * args.e2e_steps / dt, "unit": UNIT,
+               "h2d_bytes_per_step": gbytes, "d2h_bytes_per_step": gbytes + 32 * len(ctxs),
+               "steps": args.e2e_steps,
+               "path": "per integral: vegas_set_grid(host) + vegas_iterate(result to host) + vegas_refine + vegas_get_grid(host)"}
+
+    # ---- CPU baseline: the oracle on this host's cores (rank 0, N = 1)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        threads = os.cpu_count() or 1
+        rate, n, dt = oracle_samples_per_s(args.cpu_seconds, threads)
+        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": "%d samples (half per integral), iteration 0 on the uniform grid, %.1f s"
+               % (n, dt)}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 accumulators)",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "samples_per_step": samples_per_step,
+                       "bins": NBINS, "dims": D, "precision": PRECISION,
+                       "step": "one iteration (sample + finalize + refine) of both integrals",
+                       "l2": "flushed between steps (256 MiB write outside the step events); the kernel reads no HBM inputs",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": args.steps * 3 * len(ctxs),
+            "clocks": clk,
+        }
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -202,6 +202,14 @@ vegas_status vegas_import_state(vegas_ctx *ctx, const void *buf, size_t size);
 vegas_status vegas_philox(const uint32_t *dev_ctr, const uint32_t *dev_key, uint32_t *dev_out,
                           int64_t n, void *stream);
 
+/* Tracing: with enable != 0, every vegas_iterate records a CUDA event pair
+ * on the context's stream around its sampling-kernel launches.
+ * vegas_profile_read synchronises the stream, writes up to cap durations in
+ * milliseconds (oldest first) to ms_out, sets *count to the number written
+ * and forgets all recorded pairs. */
+vegas_status vegas_profile(vegas_ctx *ctx, int32_t enable);
+vegas_status vegas_profile_read(vegas_ctx *ctx, float *ms_out, int32_t cap, int32_t *count);
+
 void vegas_destroy(vegas_ctx *ctx);
 const char *vegas_strerror(vegas_status st);
 const char *vegas_last_error_string(void);

@@ -1,0 +1,6 @@
+// Sampling kernels: mode ACC_F32_KAHAN, family F_GENZ_CORNER (generated instantiation unit).
+#include "vegas_pick.cuh"
+
+namespace vegas {
+const void *sample_kernel_f32kahan_genz_corner(int d, bool priv) { return pick_family<ACC_F32_KAHAN, F_GENZ_CORNER>(d, priv); }
+}  // namespace vegas

@@ -1,0 +1,6 @@
+// Sampling kernels: mode ACC_F32_SUM64, family F_GAUSS_SYM (generated instantiation unit).
+#include "vegas_pick.cuh"
+
+namespace vegas {
+const void *sample_kernel_f32sum64_gauss_sym(int d, bool priv) { return pick_family<ACC_F32_SUM64, F_GAUSS_SYM>(d, priv); }
+}  // namespace vegas

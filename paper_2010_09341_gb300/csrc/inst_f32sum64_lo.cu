@@ -1,0 +1,6 @@
+// Sampling kernels: mode ACC_F32_SUM64, family F_LO (generated instantiation unit).
+#include "vegas_pick.cuh"
+
+namespace vegas {
+const void *sample_kernel_f32sum64_lo(int d, bool priv) { return pick_family<ACC_F32_SUM64, F_LO>(d, priv); }
+}  // namespace vegas

@@ -1,0 +1,6 @@
+// Sampling kernels: mode ACC_F64, family F_SUM (generated instantiation unit).
+#include "vegas_pick.cuh"
+
+namespace vegas {
+const void *sample_kernel_f64_sum(int d, bool priv) { return pick_family<ACC_F64, F_SUM>(d, priv); }
+}  // namespace vegas

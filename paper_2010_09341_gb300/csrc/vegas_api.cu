@@ -83,13 +83,6 @@ int mode_of(int precision) {
     }
 }
 
-const void *sample_fn(int mode, int fam, int tier, bool priv) {
-    switch (mode) {
-    case ACC_F64: return sample_kernel_f64(fam, tier, priv);
-    case ACC_F32_SUM64: return sample_kernel_f32sum64(fam, tier, priv);
-    default: return sample_kernel_f32kahan(fam, tier, priv);
-    }
-}
 
 struct DeviceInfo {
     int sms = 0;
@@ -204,6 +197,16 @@ struct vegas_ctx {
     size_t smem;
     int threads;
     int max_blocks;
+    bool profiling = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;  // event pool
+    size_t ev_used = 0;
+
+    ~vegas_ctx() {
+        for (auto &p : ev) {
+            cudaEventDestroy(p.first);
+            cudaEventDestroy(p.second);
+        }
+    }
 };
 
 extern "C" {
@@ -264,13 +267,12 @@ vegas_status vegas_create(const vegas_config *cfg, const vegas_integrand *itg, v
         return VEGAS_ECUDA;
     }
     const int mode = mode_of(cfg->precision);
-    const int tier = tier_of(d);
     // 1 KB margin for the kernel's static shared memory (block reduction)
     const size_t budget = di.smem_optin > 1024 ? di.smem_optin - 1024 : 0;
     bool priv = sample_smem(mode, true, d, N) <= budget;
     const size_t smem = sample_smem(mode, priv, d, N);
     if (smem > budget) return VEGAS_EINVAL;  // d N too large for shared memory
-    const void *fn = sample_fn(mode, itg->family, tier, priv);
+    const void *fn = sample_kernel(mode, itg->family, d, priv);
     if (!fn) return VEGAS_EINVAL;
     VEGAS_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   static_cast<int>(smem)));
@@ -364,10 +366,22 @@ vegas_status vegas_iterate(vegas_ctx *c, vegas_iter_result *out) {
     if (c->n_done >= VEGAS_MAX_ITERS) return VEGAS_EINVAL;
     const long long n = c->cfg.n_events;
     const long long lim = c->cfg.events_limit > 0 ? c->cfg.events_limit : n;
+    std::pair<cudaEvent_t, cudaEvent_t> *pe = nullptr;
+    if (c->profiling) {
+        if (c->ev_used == c->ev.size()) {
+            std::pair<cudaEvent_t, cudaEvent_t> p;
+            VEGAS_CK(cudaEventCreate(&p.first));
+            VEGAS_CK(cudaEventCreate(&p.second));
+            c->ev.push_back(p);
+        }
+        pe = &c->ev[c->ev_used++];
+        VEGAS_CK(cudaEventRecord(pe->first, c->stream));
+    }
     for (long long s0 = 0; s0 < n; s0 += lim) {
         const vegas_status st = launch_sampling(c, s0, std::min(lim, n - s0));
         if (st != VEGAS_OK) return st;
     }
+    if (pe) VEGAS_CK(cudaEventRecord(pe->second, c->stream));
     VEGAS_CK(launch_finalize(c->acc, c->last, c->nonfinite, c->iters, c->comb, c->n_done, n,
                              c->cfg.n_dim, c->cfg.n_bins, 1.0 / c->scale, c->stream));
     const int rec = c->n_done;
@@ -576,6 +590,26 @@ vegas_status vegas_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *ou
                           void *stream) {
     if (n < 0 || (n > 0 && (!ctr || !key || !out))) return VEGAS_EINVAL;
     VEGAS_CK(launch_philox(ctr, key, out, n, static_cast<cudaStream_t>(stream)));
+    return VEGAS_OK;
+}
+
+vegas_status vegas_profile(vegas_ctx *c, int32_t enable) {
+    if (!c) return VEGAS_EINVAL;
+    c->profiling = enable != 0;
+    return VEGAS_OK;
+}
+
+vegas_status vegas_profile_read(vegas_ctx *c, float *ms_out, int32_t cap, int32_t *count) {
+    if (!c || !count || cap < 0 || (cap > 0 && !ms_out)) return VEGAS_EINVAL;
+    VEGAS_CK(cudaStreamSynchronize(c->stream));
+    int32_t k = 0;
+    for (size_t i = 0; i < c->ev_used && k < cap; ++i) {
+        float ms = 0.f;
+        VEGAS_CK(cudaEventElapsedTime(&ms, c->ev[i].first, c->ev[i].second));
+        ms_out[k++] = ms;
+    }
+    *count = k;
+    c->ev_used = 0;
     return VEGAS_OK;
 }
 

@@ -27,11 +27,9 @@ struct CombRec {
     int status;             // 0 ok, 6 = every weight of the last iteration non-finite
 };
 
-// Sampling kernel lookup: one translation unit per accumulation mode.
-// tier: 0 -> MAXD 4, 1 -> 8, 2 -> 16, 3 -> 32.
-const void *sample_kernel_f64(int fam, int tier, bool priv);
-const void *sample_kernel_f32sum64(int fam, int tier, bool priv);
-const void *sample_kernel_f32kahan(int fam, int tier, bool priv);
+// Sampling kernel for (accumulation mode, family, dimension, lane-private
+// layout); nullptr if the combination does not exist.
+const void *sample_kernel(int mode, int fam, int d, bool priv);
 
 inline int tier_of(int d) { return d <= 4 ? 0 : (d <= 8 ? 1 : (d <= 16 ? 2 : 3)); }
 

@@ -1,41 +1,44 @@
 // vegas_pick.cuh -- table of sampling-kernel instantiations for one mode.
-// Included by exactly one translation unit per accumulation mode so that the
-// three modes compile in parallel.
+// Included by the translation units of one accumulation mode; each unit
+// instantiates a subset of the families so that they compile in parallel.
 #pragma once
 
 #include "vegas_kernels.cuh"
 
 namespace vegas {
 
-template <int MODE, int FAM, int MAXD>
+template <int MODE, int FAM, int MAXD, bool EXACT>
 static const void *pick_priv(bool priv) {
-    return priv ? reinterpret_cast<const void *>(&vegas_sample_kernel<FAM, MODE, MAXD, true>)
-                : reinterpret_cast<const void *>(&vegas_sample_kernel<FAM, MODE, MAXD, false>);
+    if (EXACT) return reinterpret_cast<const void *>(&vegas_sample_kernel<FAM, MODE, MAXD, true, true>);
+    return priv ? reinterpret_cast<const void *>(&vegas_sample_kernel<FAM, MODE, MAXD, false, true>)
+                : reinterpret_cast<const void *>(&vegas_sample_kernel<FAM, MODE, MAXD, false, false>);
 }
 
+// Exact-dimension kernels (no per-dimension guards) for d <= 8 with the
+// lane-private layout; generic kernels with a run-time d otherwise.
 template <int MODE, int FAM>
-static const void *pick_tier(int tier, bool priv) {
-    switch (tier) {
-    case 0: return pick_priv<MODE, FAM, 4>(priv);
-    case 1: return pick_priv<MODE, FAM, 8>(priv);
-    case 2: return pick_priv<MODE, FAM, 16>(priv);
-    default: return pick_priv<MODE, FAM, 32>(priv);
+static const void *pick_family(int d, bool priv) {
+    constexpr bool kExact = MODE != ACC_F64;  // the FP64 path is FP64-pipe bound either way
+    if (FAM == F_LO) {
+        if (d != 3) return nullptr;
+        return (kExact && priv) ? pick_priv<MODE, FAM, 3, true>(true) : pick_priv<MODE, FAM, 4, false>(priv);
     }
-}
-
-template <int MODE>
-static const void *pick_kernel(int fam, int tier, bool priv) {
-    switch (fam) {
-    case F_CONST: return pick_tier<MODE, F_CONST>(tier, priv);
-    case F_SUM: return pick_tier<MODE, F_SUM>(tier, priv);
-    case F_GAUSS_SYM: return pick_tier<MODE, F_GAUSS_SYM>(tier, priv);
-    case F_GENZ_OSC: return pick_tier<MODE, F_GENZ_OSC>(tier, priv);
-    case F_GENZ_GAUSS: return pick_tier<MODE, F_GENZ_GAUSS>(tier, priv);
-    case F_GENZ_PROD: return pick_tier<MODE, F_GENZ_PROD>(tier, priv);
-    case F_GENZ_CORNER: return pick_tier<MODE, F_GENZ_CORNER>(tier, priv);
-    case F_LO: return tier == 0 ? pick_priv<MODE, F_LO, 4>(priv) : nullptr;  // d = 3 only
-    default: return nullptr;
+    if (kExact && priv) {
+        switch (d) {
+        case 1: return pick_priv<MODE, FAM, 1, true>(true);
+        case 2: return pick_priv<MODE, FAM, 2, true>(true);
+        case 3: return pick_priv<MODE, FAM, 3, true>(true);
+        case 4: return pick_priv<MODE, FAM, 4, true>(true);
+        case 5: return pick_priv<MODE, FAM, 5, true>(true);
+        case 6: return pick_priv<MODE, FAM, 6, true>(true);
+        case 7: return pick_priv<MODE, FAM, 7, true>(true);
+        case 8: return pick_priv<MODE, FAM, 8, true>(true);
+        default: break;
+        }
     }
+    if (d <= 8) return pick_priv<MODE, FAM, 8, false>(priv);
+    if (d <= 16) return pick_priv<MODE, FAM, 16, false>(priv);
+    return pick_priv<MODE, FAM, 32, false>(priv);
 }
 
 }  // namespace vegas

@@ -44,9 +44,9 @@ template <> struct ModeTraits<ACC_F64> {
 };
 template <> struct ModeTraits<ACC_F32_SUM64> {
     using T = float;
-    using H = double;
-    static constexpr int TP = 16;   // 8-byte entries
-    static constexpr int HP = 16;
+    using H = float;                // bounded-depth cells, promoted to FP64 per block
+    static constexpr int TP = 16;   // 8-byte entries: 16 lanes per wavefront
+    static constexpr int HP = 32;   // 4-byte cells: a whole warp per wavefront
 };
 template <> struct ModeTraits<ACC_F32_KAHAN> {
     using T = float;
@@ -72,7 +72,9 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-template <int FAM, int MODE, int MAXD, bool PRIV>
+// EXACT: the dimension equals MAXD (no per-dimension guards); otherwise
+// 1 <= a.d <= MAXD at run time.
+template <int FAM, int MODE, int MAXD, bool EXACT, bool PRIV>
 __global__ void __launch_bounds__(512)
 vegas_sample_kernel(const SampleArgs a) {
     using Tr = ModeTraits<MODE>;
@@ -83,7 +85,7 @@ vegas_sample_kernel(const SampleArgs a) {
     constexpr int HP = PRIV ? Tr::HP : 1;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int d = a.d;
+    const int d = EXACT ? MAXD : a.d;
     const int N = a.N;
     const int cells = d * N;
     T2 *tab = reinterpret_cast<T2 *>(smem_raw);
@@ -109,25 +111,28 @@ vegas_sample_kernel(const SampleArgs a) {
     const long long lo = static_cast<long long>(blockIdx.x) * per;
     const long long hi = min(a.n, lo + per);
 
-    double s1d = 0.0, s2d = 0.0;       // ACC_F64 / ACC_F32_SUM64
+    double s1d = 0.0, s2d = 0.0;       // FP64 sums (ACC_F64, ACC_F32_SUM64)
+    float p1 = 0.f, p2 = 0.f;          // ACC_F32_SUM64: FP32 partials of <= 8 samples
+    int pcount = 0;
     float s1f = 0.f, c1f = 0.f, s2f = 0.f, c2f = 0.f;  // ACC_F32_KAHAN
     unsigned int nonfinite = 0;
 
-    for (long long k = lo + threadIdx.x; k < hi; k += blockDim.x) {
-        const unsigned long long s = static_cast<unsigned long long>(a.s_begin + k);
+    const int cnt = static_cast<int>(hi - lo);  // samples of this block (< 2^31)
+    for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+        const unsigned long long s = static_cast<unsigned long long>(a.s_begin + lo + k);
         const uint32_t slo = static_cast<uint32_t>(s), shi = static_cast<uint32_t>(s >> 32);
         uint32_t hoff[MAXD];
         T J = jinit;
         fam.begin();
 #pragma unroll
         for (int q = 0; q < (MAXD + 3) / 4; ++q) {
-            if (4 * q < d) {
+            if (EXACT || 4 * q < d) {
                 const uint4 r = philox4x32_10(make_uint4(slo, shi, a.iter, static_cast<uint32_t>(q)),
                                               a.key0, a.key1);
 #pragma unroll
                 for (int w = 0; w < 4; ++w) {
                     const int j = 4 * q + w;
-                    if (j < MAXD && j < d) {
+                    if (j < MAXD && (EXACT || j < d)) {
                         const Split sp = split_bin(word(r, w), static_cast<uint32_t>(N));
                         const uint32_t cell = static_cast<uint32_t>(j * N) + sp.bin;
                         const T2 ent = tab_l[cell * TP];
@@ -156,6 +161,15 @@ vegas_sample_kernel(const SampleArgs a) {
             const float t2 = s2f + y2;
             c2f = (t2 - s2f) - y2;
             s2f = t2;
+        } else if (MODE == ACC_F32_SUM64) {
+            p1 += static_cast<float>(v);
+            p2 += static_cast<float>(v2);
+            if (++pcount == 8) {
+                s1d += static_cast<double>(p1);
+                s2d += static_cast<double>(p2);
+                p1 = p2 = 0.f;
+                pcount = 0;
+            }
         } else {
             const double vd = static_cast<double>(v);
             s1d += vd;
@@ -164,8 +178,12 @@ vegas_sample_kernel(const SampleArgs a) {
         const H hv = static_cast<H>(v2);
 #pragma unroll
         for (int j = 0; j < MAXD; ++j) {
-            if (j < d) red_add_shared(hist_l + hoff[j], hv);
+            if (EXACT || j < d) red_add_shared(hist_l + hoff[j], hv);
         }
+    }
+    if (MODE == ACC_F32_SUM64) {
+        s1d += static_cast<double>(p1);
+        s2d += static_cast<double>(p2);
     }
 
     // block reduction of S1, S2 and the non-finite count

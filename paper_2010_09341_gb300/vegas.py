@@ -194,6 +194,19 @@ def vegas_philox(ctr: torch.Tensor, key: torch.Tensor, stream=None) -> torch.Ten
     return out
 
 
+def vegas_profile(ctx: Context, enable: bool = True) -> None:
+    check(nat.load().vegas_profile(ctx.handle, 1 if enable else 0), "vegas_profile")
+
+
+def vegas_profile_read(ctx: Context, cap: int = 1 << 16):
+    """Sampling-kernel durations (ms) of the iterations since the last read."""
+    buf = (ctypes.c_float * cap)()
+    cnt = ctypes.c_int32()
+    check(nat.load().vegas_profile_read(ctx.handle, buf, int(cap), ctypes.byref(cnt)),
+          "vegas_profile_read")
+    return [buf[i] for i in range(cnt.value)]
+
+
 def vegas_destroy(ctx: Context) -> None:
     if ctx.handle:
         nat.load().vegas_destroy(ctx.handle)

@@ -88,8 +88,12 @@ def test_trace_bins_bit_exact(family, d, N, prec):
             # FP32 per-sample error is relative to the integrand's scale: where
             # f is tiny (tails, zeros of cos, (1-x)^3 near x = 1) cancellation
             # makes its own relative error large.
+            # The LO toy's Breit-Wigner has d ln f / d ln shat ~ 37 on its
+            # shoulders, so FP32 rounding of shat (~1e-6 in a wide bin at
+            # small x) reaches a few 1e-5 in f: its per-sample bound is 2e-4.
             scale = np.mean(np.abs(vs))
-            ok = np.abs(ws - vs) <= 2e-5 * np.abs(vs) + 2e-6 * scale
+            rel = 2e-4 if family == "lo" else 2e-5
+            ok = np.abs(ws - vs) <= rel * np.abs(vs) + 2e-6 * scale
             if family == "lo":  # cut edges within FP32 rounding of a point
                 ok |= (vs == 0.0) != (ws == 0.0)
             assert np.all(ok), np.max(np.abs(ws - vs) / (np.abs(vs) + scale))
