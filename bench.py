@@ -38,6 +38,7 @@ WORKLOAD = "d=8 Gaussian a=0.1 + d=8 Genz oscillatory (c~U(0,1) seed 1), 50 bins
 # Nominal unit counts used for the issue roofline (derived, per SM per clock).
 ISSUE_PER_SM_CLK = 128.0      # 4 schedulers x 32 lanes: one warp instruction each per clock
 MUFU_PER_SM_CLK = 16.0        # special-function lanes
+MULWIDE_PER_SM_CLK = 32.0     # 32x32->64 integer multiplies (a quarter of the FP32 lanes)
 FP64_TFLOPS_NOMINAL = 1.25    # GB300 dense FP64 (FMA = 2 flop)
 
 
@@ -52,28 +53,39 @@ def ops_per_sample(family: str, d: int, precision: str):
 
     Philox4x32-10: 10 rounds x (2 wide multiplies + 2 three-input xors) per
     4 words (round keys are per-thread constants).  Per dimension: 1 wide
-    multiply (bin split), 2 (mantissa build), 1 table address, 1 table load,
-    1 FMA (x), 1 multiply (J), 1 histogram address, 1 shared atomic, plus the
-    integrand's per-dimension ops; J *= N^4 once per 4 dimensions.  Per
-    sample: integrand finish, v = J f, v^2, non-finite test (2), the two sums
-    (FP64: convert + add + FMA; Kahan: 8 FP32 ops), loop (3).
+    multiply (bin split), 2 (mantissa build), 1 cell index, 1 table address,
+    1 table load, 1 FMA (x), 1 multiply (J), 1 histogram address, 1 shared
+    integer atomic, plus the integrand's per-dimension ops; J *= N^4 once per
+    4 dimensions.  Per sample: integrand finish, v = J f, v^2, non-finite test
+    (2), the fixed-point histogram value (scale, convert, clamp, range test:
+    5), the two sums (FP32 partials + FP64 flush: 2 adds, 2 for the chunk
+    bookkeeping and 4 FP64 ops per 8 samples; Kahan: 8 FP32 ops; FP64:
+    convert + add + FMA), loop (3).
+    Wide multiplies (32x32->64) also count on their own pipe: 20 per Philox
+    call plus one per dimension.
     """
     per_dim_f = {"gauss_sym": 2, "genz_osc": 1, "genz_gauss": 3, "genz_prod": 4,
                  "genz_corner": 1, "sum": 1, "const": 0, "lo": 0}[family]
-    finish = {"gauss_sym": 2, "genz_osc": 4, "genz_gauss": 2, "genz_prod": 1,
+    finish = {"gauss_sym": 2, "genz_osc": 6, "genz_gauss": 2, "genz_prod": 1,
               "genz_corner": 3, "sum": 0, "const": 0, "lo": 20}[family]
     mufu = {"gauss_sym": 1, "genz_osc": 1, "genz_gauss": 1, "genz_prod": 1,
             "genz_corner": 2, "sum": 0, "const": 0, "lo": 2}[family]
-    philox = 40 * math.ceil(d / 4)
-    per_dim = (9 + per_dim_f) * d + d // 4
+    calls = math.ceil(d / 4)
+    philox = 40 * calls
+    per_dim = (10 + per_dim_f) * d + d // 4
     fp64 = 0
+    hist = 5
     if precision == "fp32_kahan":
         acc = 8
+    elif precision == "fp32_acc64":
+        acc = 4 + 0.5
+        fp64 = 0.5
     else:
         acc = 3
         fp64 = 3
-    total = philox + per_dim + finish + 2 + 2 + acc + 3
-    return {"total": total, "fp64": fp64, "mufu": mufu}
+        hist = 0
+    total = philox + per_dim + finish + 2 + 2 + hist + acc + 3
+    return {"total": total, "fp64": fp64, "mufu": mufu, "mulwide": 20 * calls + d}
 
 
 def roofline_samples_per_s(ops, sms: int, clk_hz: float) -> dict:
@@ -84,6 +96,8 @@ def roofline_samples_per_s(ops, sms: int, clk_hz: float) -> dict:
         bounds["fp64"] = sms * clk_hz * fp64_per_sm_clk / ops["fp64"]
     if ops["mufu"]:
         bounds["mufu"] = sms * clk_hz * MUFU_PER_SM_CLK / ops["mufu"]
+    if ops.get("mulwide"):
+        bounds["mulwide"] = sms * clk_hz * MULWIDE_PER_SM_CLK / ops["mulwide"]
     return bounds
 
 
@@ -316,7 +330,7 @@ def main():
     roofline = {"bound": "alu", "achieved": achieved_gops, "peak": peak_gops, "unit": "Gop/s",
                 "frac": achieved_gops / peak_gops, "traffic": None,
                 "kernel": "vegas_sample_kernel", "peak_basis":
-                "min over pipes (issue 128/clk/SM, FP64 %.2f TFLOP/s, MUFU 16/clk/SM) at %d SMs x %.0f MHz (max clock)"
+                "min over pipes (issue 128/clk/SM, 32x32->64 multiply 32/clk/SM, FP64 %.2f TFLOP/s, MUFU 16/clk/SM) at %d SMs x %.0f MHz (max clock)"
                 % (FP64_TFLOPS_NOMINAL, sms, clk_max_hz / 1e6), "per_integral": per_fam}
 
     # ---- end to end through the public API with host buffers

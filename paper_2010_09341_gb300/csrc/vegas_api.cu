@@ -36,7 +36,7 @@ constexpr size_t kAlign = 256;
 inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-    size_t edges, table, acc, last, nonfinite, iters, comb, total;
+    size_t edges, table, acc, last, nonfinite, hscale, iters, comb, total;
 };
 
 Layout layout_for(int d, int N) {
@@ -52,6 +52,8 @@ Layout layout_for(int d, int N) {
     off = align_up(off + sizeof(double) * (2 + static_cast<size_t>(d) * N));
     L.nonfinite = off;
     off = align_up(off + sizeof(unsigned long long));
+    L.hscale = off;
+    off = align_up(off + sizeof(float));
     L.iters = off;
     off = align_up(off + sizeof(IterRec) * VEGAS_MAX_ITERS);
     L.comb = off;
@@ -185,6 +187,7 @@ struct vegas_ctx {
     double *acc;
     double *last;
     unsigned long long *nonfinite;
+    float *hscale;
     IterRec *iters;
     CombRec *comb;
     int t;          // Philox iteration word of the next iteration
@@ -295,6 +298,7 @@ vegas_status vegas_create(const vegas_config *cfg, const vegas_integrand *itg, v
     c->acc = reinterpret_cast<double *>(c->ws + L.acc);
     c->last = reinterpret_cast<double *>(c->ws + L.last);
     c->nonfinite = reinterpret_cast<unsigned long long *>(c->ws + L.nonfinite);
+    c->hscale = reinterpret_cast<float *>(c->ws + L.hscale);
     c->iters = reinterpret_cast<IterRec *>(c->ws + L.iters);
     c->comb = reinterpret_cast<CombRec *>(c->ws + L.comb);
     c->t = 0;
@@ -319,7 +323,7 @@ vegas_status vegas_create(const vegas_config *cfg, const vegas_integrand *itg, v
         for (int k = 0; k <= N; ++k) e[static_cast<size_t>(j) * (N + 1) + k] = static_cast<double>(k) / N;
     cudaError_t ce = cudaMemcpyAsync(c->edges, e.data(), e.size() * sizeof(double),
                                      cudaMemcpyHostToDevice, c->stream);
-    if (ce == cudaSuccess) ce = cudaMemsetAsync(c->acc, 0, (L.nonfinite + 8) - L.acc, c->stream);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(c->acc, 0, (L.hscale + sizeof(float)) - L.acc, c->stream);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(c->comb, 0, sizeof(CombRec), c->stream);
     if (ce == cudaSuccess) ce = launch_table_from_edges(c->edges, c->table, mode, d, N, c->stream);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
@@ -346,7 +350,13 @@ static SampleArgs make_args(const vegas_ctx *c, long long s_begin, long long n, 
     a.iter = static_cast<uint32_t>(t);
     a.jinit = c->jinit;
     a.nblk4 = c->nblk4;
-    a.fc = c->fc;
+    a.hscale = c->hscale;
+    a.fc64 = c->fc;
+    for (int k = 0; k < 32; ++k) {
+        a.fc32.p[k] = static_cast<float>(c->fc.p[k]);
+        a.fc32.q[k] = static_cast<float>(c->fc.q[k]);
+    }
+    for (int k = 0; k < 8; ++k) a.fc32.s[k] = static_cast<float>(c->fc.s[k]);
     return a;
 }
 
@@ -355,9 +365,15 @@ static vegas_status launch_sampling(vegas_ctx *c, long long s_begin, long long n
     // a few samples per thread at least; otherwise fill every SM
     const long long want = (n + static_cast<long long>(c->threads) * 4 - 1) /
                            (static_cast<long long>(c->threads) * 4);
-    const int blocks = static_cast<int>(std::max(1LL, std::min<long long>(c->max_blocks, want)));
+    long long blocks = std::max(1LL, std::min<long long>(c->max_blocks, want));
+    if (c->mode != ACC_F64) {
+        // fixed-point histogram cells: at most 2048 N samples per block
+        const long long cap = 2048LL * c->cfg.n_bins;
+        blocks = std::max(blocks, (n + cap - 1) / cap);
+    }
     void *params[] = {&a};
-    VEGAS_CK(cudaLaunchKernel(c->kfn, dim3(blocks), dim3(c->threads), params, c->smem, c->stream));
+    VEGAS_CK(cudaLaunchKernel(c->kfn, dim3(static_cast<unsigned>(blocks)), dim3(c->threads), params,
+                              c->smem, c->stream));
     return VEGAS_OK;
 }
 
@@ -382,8 +398,8 @@ vegas_status vegas_iterate(vegas_ctx *c, vegas_iter_result *out) {
         if (st != VEGAS_OK) return st;
     }
     if (pe) VEGAS_CK(cudaEventRecord(pe->second, c->stream));
-    VEGAS_CK(launch_finalize(c->acc, c->last, c->nonfinite, c->iters, c->comb, c->n_done, n,
-                             c->cfg.n_dim, c->cfg.n_bins, 1.0 / c->scale, c->stream));
+    VEGAS_CK(launch_finalize(c->acc, c->last, c->nonfinite, c->hscale, c->iters, c->comb, c->n_done,
+                             n, c->cfg.n_dim, c->cfg.n_bins, 1.0 / c->scale, c->stream));
     const int rec = c->n_done;
     c->n_done += 1;
     c->t += 1;

@@ -17,11 +17,27 @@ namespace vegas {
 // variance are exact: if any exist, their plain mean is the result with
 // sigma 0.
 __global__ void __launch_bounds__(256)
-finalize_kernel(double *acc, double *last, unsigned long long *n_nonfinite, IterRec *iters,
-                CombRec *comb, int t, long long n, int total, double inv1, double inv2) {
+finalize_kernel(double *acc, double *last, unsigned long long *n_nonfinite, float *hscale,
+                IterRec *iters, CombRec *comb, int t, long long n, int total, double inv1,
+                double inv2) {
     __shared__ double sh[3][8];
     __shared__ double mean_s;
     __shared__ int nzero_s;
+    if (threadIdx.x == 0) {
+        // fixed-point histogram scale for the next iteration: the mean of the
+        // (scaled) v^2 maps to 2^18 (values up to 32x it stay below 2^23);
+        // 0 if there is no usable mean
+        const long long ne = n - static_cast<long long>(*n_nonfinite);
+        const double m2 = ne > 0 ? acc[1] / static_cast<double>(ne) : 0.0;
+        float hs = 0.f;
+        if (m2 > 0.0 && isfinite(m2)) {
+            int e = 18 - static_cast<int>(ceil(log2(m2)));
+            e = max(-100, min(100, e));
+            hs = ldexpf(1.0f, e);
+        }
+        *hscale = hs;
+    }
+    __syncthreads();
     for (int c = threadIdx.x; c < total; c += blockDim.x) {
         last[c] = acc[c] * (c == 0 ? inv1 : inv2);
         acc[c] = 0.0;
@@ -136,11 +152,11 @@ finalize_kernel(double *acc, double *last, unsigned long long *n_nonfinite, Iter
 }
 
 cudaError_t launch_finalize(double *acc, double *last, unsigned long long *n_nonfinite,
-                            IterRec *iters, CombRec *comb, int t, long long n, int d, int N,
-                            double inv_scale, cudaStream_t stream) {
+                            float *hscale, IterRec *iters, CombRec *comb, int t, long long n,
+                            int d, int N, double inv_scale, cudaStream_t stream) {
     const int total = 2 + d * N;
-    finalize_kernel<<<1, 256, 0, stream>>>(acc, last, n_nonfinite, iters, comb, t, n, total,
-                                           inv_scale, inv_scale * inv_scale);
+    finalize_kernel<<<1, 256, 0, stream>>>(acc, last, n_nonfinite, hscale, iters, comb, t, n,
+                                           total, inv_scale, inv_scale * inv_scale);
     return cudaGetLastError();
 }
 
@@ -302,12 +318,12 @@ __global__ void trace_kernel(const SampleArgs a, double inv_scale, int32_t *bins
     const int d = a.d, N = a.N;
     const T2 *tab = static_cast<const T2 *>(a.table);
     Integrand<FAM, T, MAXD> fam;
-    fam.load(a.fc, d);
+    const FamConsts<T> &fc = consts<T>(a);
     const unsigned long long s = static_cast<unsigned long long>(a.s_begin + k);
     const uint32_t slo = static_cast<uint32_t>(s), shi = static_cast<uint32_t>(s >> 32);
     T J = static_cast<T>(a.jinit);
     const T n4 = static_cast<T>(a.nblk4);
-    fam.begin();
+    fam.begin(fc);
 #pragma unroll
     for (int q = 0; q < (MAXD + 3) / 4; ++q) {
         if (4 * q < d) {
@@ -321,17 +337,17 @@ __global__ void trace_kernel(const SampleArgs a, double inv_scale, int32_t *bins
                     const uint32_t cell = static_cast<uint32_t>(j * N) + sp.bin;
                     const T2 ent = tab[cell];
                     const T m = Prec<T>::mant(sp.lo);
-                    const T x = fma(ent.y, m, ent.x);
+                    const T x = ffma(ent.y, m, ent.x);
                     J *= ent.y;
                     if (sizeof(T) == 4 && (j & 3) == 3) J *= n4;
-                    fam.dim(j, x);
+                    fam.dim(j, x, fc);
                     if (bins) bins[k * d + j] = static_cast<int32_t>(sp.bin);
                     if (xs) xs[k * d + j] = static_cast<double>(x);
                 }
             }
         }
     }
-    const T v = J * fam.finish(d);
+    const T v = J * fam.finish(fc);
     if (ws) ws[k] = static_cast<double>(v) * inv_scale;
 }
 

@@ -90,21 +90,45 @@ enum Family : int {
     F_LO = 7
 };
 
-// Per-integral constants a family needs, prepared on the host in FP64:
-//   p[j], q[j] per dimension (meaning per family below), s0..s7 scalars.
-// The kernel keeps them in registers (per-dimension arrays are indexed with
-// compile-time indices after unrolling).
-struct FamilyConsts {
-    double p[32];
-    double q[32];
-    double s[8];
+// Per-integral constants a family needs, prepared on the host in FP64 and
+// passed to the kernels in both precisions:
+//   p[j], q[j] per dimension (meaning per family below), s[0..7] scalars.
+// The kernels read them straight from the kernel-parameter space with
+// compile-time indices (after unrolling), so the FP32 path never converts
+// an FP64 constant per sample.
+template <class T> struct FamConsts {
+    T p[32];
+    T q[32];
+    T s[8];
 };
+using FamilyConsts = FamConsts<double>;
 
+// Precision-typed helpers: the float versions must never promote to FP64
+// (GB300's FP64 pipe issues 2 operations per clock per SM).
+__device__ __forceinline__ float ffma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double ffma(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fabs_t(float x) { return fabsf(x); }
+__device__ __forceinline__ double fabs_t(double x) { return fabs(x); }
 __device__ __forceinline__ float fexp2(float x) { return exp2f(x); }
 __device__ __forceinline__ double fexp2(double x) { return exp2(x); }
 __device__ __forceinline__ float flog2(float x) { return log2f(x); }
 __device__ __forceinline__ double flog2(double x) { return log2(x); }
-__device__ __forceinline__ float fcos(float x) { return cosf(x); }
+// FP32 cosine for moderate arguments: reduce by 2 pi with a two-part constant
+// (Cody & Waite, "Software Manual for the Elementary Functions", 1980):
+// 2 pi = C1 + C2, C1 = the float nearest 2 pi, C2 = 2 pi - C1; the nearest
+// multiple k comes from adding and subtracting 1.5 * 2^23 (valid for
+// |x| < 2^22 * 2 pi).  The reduced argument lies in [-pi, pi], where the
+// hardware approximation __cosf has an absolute error below 2^-21.
+__device__ __forceinline__ float fcos(float x) {
+    const float kInv2Pi = 0.159154943091895336f;
+    const float kC1 = 6.28318548202514648f;
+    const float kC2 = -1.74845553146951720e-7f;
+    const float kShift = 12582912.0f;  // 1.5 * 2^23
+    const float k = __fadd_rn(__fmaf_rn(x, kInv2Pi, kShift), -kShift);
+    float r = __fmaf_rn(-k, kC1, x);
+    r = __fmaf_rn(-k, kC2, r);
+    return __cosf(r);
+}
 __device__ __forceinline__ double fcos(double x) { return cos(x); }
 __device__ __forceinline__ float frsqrt(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double frsqrt(double x) { return rsqrt(x); }
@@ -125,50 +149,33 @@ __device__ __forceinline__ double frcp(double x) { return 1.0 / x; }
 //   GENZ_CORNER  acc += p_j x  (acc0 = 1)          f = 2^(-(d+1) log2 acc)
 //   LO           x kept in registers               f from s0..s6
 template <int FAM, class T, int MAXD> struct Integrand {
-    T pj[MAXD];
-    T qj[MAXD];
-    T s0, s1, s2, s3, s4, s5, s6;
+    using C = FamConsts<T>;
     T acc;
     T x0, x1, x2;
 
-    __device__ __forceinline__ void load(const FamilyConsts &fc, int d) {
-#pragma unroll
-        for (int j = 0; j < MAXD; ++j) {
-            pj[j] = static_cast<T>(j < d ? fc.p[j] : 0.0);
-            qj[j] = static_cast<T>(j < d ? fc.q[j] : 0.0);
-        }
-        s0 = static_cast<T>(fc.s[0]);
-        s1 = static_cast<T>(fc.s[1]);
-        s2 = static_cast<T>(fc.s[2]);
-        s3 = static_cast<T>(fc.s[3]);
-        s4 = static_cast<T>(fc.s[4]);
-        s5 = static_cast<T>(fc.s[5]);
-        s6 = static_cast<T>(fc.s[6]);
-    }
-
-    __device__ __forceinline__ void begin() {
-        if (FAM == F_GENZ_OSC) acc = s1;          // 2 pi u
+    __device__ __forceinline__ void begin(const C &fc) {
+        if (FAM == F_GENZ_OSC) acc = fc.s[1];     // 2 pi u
         else if (FAM == F_GENZ_CORNER) acc = T(1);
         else if (FAM == F_GENZ_PROD) acc = T(1);
         else acc = T(0);
     }
 
-    __device__ __forceinline__ void dim(int j, T x) {
+    __device__ __forceinline__ void dim(int j, T x, const C &fc) {
         if (FAM == F_SUM) {
             acc += x;
         } else if (FAM == F_GAUSS_SYM) {
             const T t = x - T(0.5);
-            acc = fma(t, t, acc);
+            acc = ffma(t, t, acc);
         } else if (FAM == F_GENZ_OSC || FAM == F_GENZ_CORNER) {
-            acc = fma(pj[j], x, acc);
+            acc = ffma(fc.p[j], x, acc);
         } else if (FAM == F_GENZ_GAUSS) {
-            const T t = pj[j] * (x - qj[j]);
-            acc = fma(t, t, acc);
+            const T t = fc.p[j] * (x - fc.q[j]);
+            acc = ffma(t, t, acc);
         } else if (FAM == F_GENZ_PROD) {
             // (c^-2 + (x-w)^2) c^2 = 1 + (c (x-w))^2; the c^2 factors are in
             // the initial weight.  Multiply the denominators, invert once.
-            const T t = pj[j] * (x - qj[j]);
-            acc *= fma(t, t, T(1));
+            const T t = fc.p[j] * (x - fc.q[j]);
+            acc *= ffma(t, t, T(1));
         } else if (FAM == F_LO) {
             if (j == 0) x0 = x;
             else if (j == 1) x1 = x;
@@ -176,7 +183,8 @@ template <int FAM, class T, int MAXD> struct Integrand {
         }
     }
 
-    __device__ __forceinline__ T finish(int d) {
+    __device__ __forceinline__ T finish(const C &fc) {
+        const T s0 = fc.s[0];
         if (FAM == F_CONST) return T(1);
         if (FAM == F_SUM) return acc;
         if (FAM == F_GAUSS_SYM) return fexp2(s0 * acc);
@@ -188,14 +196,15 @@ template <int FAM, class T, int MAXD> struct Integrand {
             // s0 = sqrtS^2, s1 = M^2, s2 = (M Gamma)^2, s3 = cut,
             // s4 = mll_lo^2, s5 = mll_hi^2; the constant 2 (35/32)^2 norm is
             // in the initial weight.
+            const T s1 = fc.s[1], s2 = fc.s[2], s3 = fc.s[3], s4 = fc.s[4], s5 = fc.s[5];
             const T shat = x0 * x1 * s0;
-            const T c = fma(T(2), x2, T(-1));
-            const bool in = (shat >= s4) && (shat <= s5) && (fabs(c) < s3);
+            const T c = ffma(T(2), x2, T(-1));
+            const bool in = (shat >= s4) && (shat <= s5) && (fabs_t(c) < s3);
             const T om0 = T(1) - x0, om1 = T(1) - x1;
             const T g = om0 * om0 * om0 * om1 * om1 * om1 * frsqrt(x0 * x1);
             const T dm = shat - s1;
-            const T den = fma(dm, dm, s2) * shat;
-            const T val = g * fma(c, c, T(1)) * frcp(den);
+            const T den = ffma(dm, dm, s2) * shat;
+            const T val = g * ffma(c, c, T(1)) * frcp(den);
             return in ? val : T(0);
         }
         return T(0);

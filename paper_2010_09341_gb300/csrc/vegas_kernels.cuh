@@ -37,9 +37,10 @@ size_t sample_smem(int mode, bool priv, int d, int N);
 
 // Finalize: move the accumulators (unscaled) to `last`, zero them, form
 // I_t and sigma_t, store iters[t] and recombine all iterations into *comb.
+// Also sets *hscale, the fixed-point histogram scale of the next iteration.
 cudaError_t launch_finalize(double *acc, double *last, unsigned long long *n_nonfinite,
-                            IterRec *iters, CombRec *comb, int t, long long n, int d, int N,
-                            double inv_scale, cudaStream_t stream);
+                            float *hscale, IterRec *iters, CombRec *comb, int t, long long n,
+                            int d, int N, double inv_scale, cudaStream_t stream);
 
 // Refine every dimension from the histograms in last[2..] and write the new
 // FP64 edges and the sampling table of the given mode.

@@ -72,6 +72,7 @@ def test_trace_bins_bit_exact(family, d, N, prec):
         bins, x, w = bins.cpu().numpy(), x.cpu().numpy(), w.cpu().numpy()
         ks = list(range(0, cnt, 7 if d > 8 else 3))
         vs = []
+        js = []
         for k in ks:
             ob, ox, J, f = O.sample(d, N, e, family, p, 5, 9, t, s0 + k)
             assert np.array_equal(bins[k], ob), (k, bins[k], ob)
@@ -80,7 +81,9 @@ def test_trace_bins_bit_exact(family, d, N, prec):
             else:
                 assert np.allclose(x[k], ox, rtol=0, atol=3e-7)
             vs.append(J * f)
+            js.append(abs(J))
         vs = np.array(vs)
+        js = np.array(js)
         ws = w[ks]
         if prec == "fp64":
             assert np.all(np.abs(ws - vs) <= 1e-13 * np.abs(vs) + 1e-300)
@@ -92,8 +95,11 @@ def test_trace_bins_bit_exact(family, d, N, prec):
             # shoulders, so FP32 rounding of shat (~1e-6 in a wide bin at
             # small x) reaches a few 1e-5 in f: its per-sample bound is 2e-4.
             scale = np.mean(np.abs(vs))
+            # The oscillatory family's FP32 cosine has an absolute error (its
+            # argument carries ~1e-6 of FP32 rounding), which J multiplies.
             rel = 2e-4 if family == "lo" else 2e-5
-            ok = np.abs(ws - vs) <= rel * np.abs(vs) + 2e-6 * scale
+            atol = 2e-6 * scale + (4e-6 * js if family == "genz_osc" else 0.0)
+            ok = np.abs(ws - vs) <= rel * np.abs(vs) + atol
             if family == "lo":  # cut edges within FP32 rounding of a point
                 ok |= (vs == 0.0) != (ws == 0.0)
             assert np.all(ok), np.max(np.abs(ws - vs) / (np.abs(vs) + scale))
@@ -124,16 +130,24 @@ def _compare_iteration(V, ctx, p, family, d, N, n, prec, e, t, seed=0, iid=0):
     return acc
 
 
+@pytest.mark.parametrize("warm", [False, True])
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("family,d,N,n", ITER_CASES)
-def test_iteration_parity_on_shared_grid(family, d, N, n, prec):
+def test_iteration_parity_on_shared_grid(family, d, N, n, prec, warm):
+    """warm: one iteration runs first, so the FP32 modes accumulate this one
+    in fixed-point histogram cells scaled from it (the first iteration of a
+    context uses FP32 cells)."""
     if family == "lo" and prec != "fp64":
         pytest.skip("LO cuts: FP32 points within rounding of a cut edge; covered below")
     V = native()
     ctx, p = _make(V, family, d, N, n, prec)
+    t = 0
+    if warm:
+        V.vegas_iterate(ctx)
+        t = 1
     e = random_grid(d, N, seed=1, spread=0.5)
     V.vegas_set_grid(ctx, e)
-    _compare_iteration(V, ctx, p, family, d, N, n, prec, e, 0)
+    _compare_iteration(V, ctx, p, family, d, N, n, prec, e, t)
 
 
 @pytest.mark.parametrize("prec", ["fp32_acc64", "fp32_kahan"])
@@ -269,15 +283,34 @@ def test_invalid_arguments_rejected():
 
 # -------------------------------------------------------- full-size checks
 @pytest.mark.parametrize("family", ["gauss_sym", "genz_osc"])
-@pytest.mark.parametrize("prec", ["fp32_acc64", "fp64"])
+@pytest.mark.parametrize("prec", ["fp32_acc64", "fp32_kahan", "fp64"])
 def test_full_size_d8_iteration(family, prec):
     """d = 8, 50 bins, 1e7 samples, the launch configuration the benchmark
-    times: the whole iteration against the oracle run on all host cores."""
-    import os
+    times (after a first iteration, as in the benchmark's steady state): the
+    whole iteration against the oracle run on all host cores."""
     V = native()
     d, N, n = 8, 50, 10_000_000
     p = params_for(family, d, seed=1) if family == "genz_osc" else params_for(family, d)
     ctx, _ = _make(V, family, d, N, n, prec, params=p)
-    e = random_grid(d, N, seed=2, spread=0.4)
-    V.vegas_set_grid(ctx, e)
-    _compare_iteration(V, ctx, p, family, d, N, n, prec, e, 0)
+    V.vegas_iterate(ctx)
+    V.vegas_refine(ctx)
+    e = V.vegas_get_grid(ctx)
+    _compare_iteration(V, ctx, p, family, d, N, n, prec, e, 1)
+
+
+def test_full_size_lo_iteration():
+    """d = 3 LO toy, 100 bins, 1e8 samples, FP32 with Kahan sums, after one
+    iteration (fixed-point histogram cells): estimate within 1e-4 (hard cuts,
+    see test_lo_fp32_parity), histograms within 1e-4 of their sum."""
+    V = native()
+    d, N, n = 3, 100, 100_000_000
+    ctx, p = _make(V, "lo", d, N, n, "fp32_kahan")
+    V.vegas_iterate(ctx)
+    V.vegas_refine(ctx)
+    e = V.vegas_get_grid(ctx)
+    I, _, _, _ = V.vegas_iterate(ctx)
+    _, _, h = V.vegas_get_sums(ctx)
+    acc = O.iterate(d, N, e, "lo", p, 0, 0, 1, n, threads=16)
+    Io = acc["S1"] / n
+    assert abs(I - Io) <= 1e-4 * abs(Io)
+    assert np.max(np.abs(h - acc["hist"])) <= 1e-4 * acc["hist"].sum()
