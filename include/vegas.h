@@ -202,6 +202,40 @@ vegas_status vegas_import_state(vegas_ctx *ctx, const void *buf, size_t size);
 vegas_status vegas_philox(const uint32_t *dev_ctr, const uint32_t *dev_key, uint32_t *dev_out,
                           int64_t n, void *stream);
 
+/* No-allocation form of one iteration's sums.  (The paper has no counterpart:
+ * this entry point exists for callers of this library, not for the method.)
+ *
+ * Some callers cannot allocate device memory when they call us: a runtime
+ * that owns the whole device through its own pool or arena and forbids other
+ * allocations, a plugin or callback that must not grow the process's memory
+ * footprint, or code on a path where cudaMalloc's implicit device
+ * synchronisation would stall other work.  vegas_iterate_noalloc needs no
+ * workspace and no context: its scratch (accumulators, counters, grid table)
+ * lives in a fixed device array inside this library, of 2 + 4096 FP64 sums
+ * plus a 4096-entry table (about 100 KB), which every GPU that loads the
+ * library holds until the process exits.  It never calls cudaMalloc,
+ * cudaFree or an allocating library routine.
+ *
+ * It computes what vegas_iterate's sampling does for iteration t (the Philox
+ * counter word) of the given configuration and integrand on the grid
+ * dev_edges (device, d rows of N+1 FP64 edges, read only), and writes
+ * dev_sums (device, 2 + d*N FP64: S1, S2, h_0[0..N-1], ...), in the layout of
+ * vegas_get_sums.  Asynchronous on stream; nothing is reported back except
+ * the status.
+ *   - EINVAL for an invalid configuration or integrand, and when
+ *     n_dim * n_bins exceeds 4096 (vegas_last_error_string says so).
+ *   - The first call on each device looks up the scratch array's device
+ *     address (once per device, with that device current); make that first
+ *     call before any stream capture.
+ *   - Every call uses the same array: each call clears it before use, and
+ *     calls that overlap on the GPU (other streams, other host threads)
+ *     race and corrupt each other's sums.  Serialise them.
+ *   - FP32 modes always use FP32 histogram cells here (as the first
+ *     iteration of a context does). */
+vegas_status vegas_iterate_noalloc(const vegas_config *cfg, const vegas_integrand *integrand,
+                                   int32_t t, const double *dev_edges, double *dev_sums,
+                                   void *stream);
+
 /* Tracing: with enable != 0, every vegas_iterate records a CUDA event pair
  * on the context's stream around its sampling-kernel launches.
  * vegas_profile_read synchronises the stream, writes up to cap durations in

@@ -75,6 +75,9 @@ _SIGS = {
     "vegas_export_state": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_size_t)]),
     "vegas_import_state": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
     "vegas_philox": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _P]),
+    "vegas_iterate_noalloc": (ctypes.c_int, [ctypes.POINTER(VegasConfig),
+                                             ctypes.POINTER(VegasIntegrand), ctypes.c_int32,
+                                             _P, _P, _P]),
     "vegas_profile": (ctypes.c_int, [_P, ctypes.c_int32]),
     "vegas_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float), ctypes.c_int32,
                                           ctypes.POINTER(ctypes.c_int32)]),

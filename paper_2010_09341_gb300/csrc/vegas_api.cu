@@ -632,3 +632,137 @@ vegas_status vegas_profile_read(vegas_ctx *c, float *ms_out, int32_t cap, int32_
 void vegas_destroy(vegas_ctx *c) { delete c; }
 
 }  // extern "C"
+
+// ------------------------------------------------------- no-allocation form
+// One iteration's sums with every piece of scratch in a file-scope device
+// array instead of a caller workspace.  For callers that cannot allocate
+// device memory (see vegas_iterate_noalloc in vegas.h).
+namespace {
+
+constexpr int kNoallocMaxCells = 4096;  // d * N
+constexpr size_t kNaAcc = 0;                                                    // 2 + cells doubles
+constexpr size_t kNaNonfinite = (sizeof(double) * (2 + kNoallocMaxCells) + 255) / 256 * 256;
+constexpr size_t kNaHscale = kNaNonfinite + kAlign;                             // float, kept 0
+constexpr size_t kNaTable = kNaHscale + kAlign;                                 // cells x 16 bytes
+constexpr size_t kNaBytes = kNaTable + 16 * static_cast<size_t>(kNoallocMaxCells);
+
+// Shared by every call in the process, on every device that loads the library.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+char *g_noalloc_ptr[kMaxDevices] = {};
+
+__global__ void noalloc_unscale_kernel(const double *acc, double *out, int total, double inv1,
+                                       double inv2) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < total) out[c] = acc[c] * (c == 0 ? inv1 : inv2);
+}
+
+// Device address of the scratch array on the current device, looked up once
+// per device (host code may not use the symbol itself as a pointer).
+vegas_status noalloc_scratch(char **out) {
+    int dev = 0;
+    VEGAS_CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return VEGAS_EINVAL;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        VEGAS_CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_noalloc_ptr[dev] = static_cast<char *>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return VEGAS_OK;
+}
+
+}  // namespace
+
+extern "C" vegas_status vegas_iterate_noalloc(const vegas_config *cfg, const vegas_integrand *itg,
+                                              int32_t t, const double *dev_edges, double *dev_sums,
+                                              void *stream) {
+    if (!config_ok(cfg) || !itg || t < 0 || !dev_edges || !dev_sums) return VEGAS_EINVAL;
+    const int d = cfg->n_dim, N = cfg->n_bins;
+    if (d * N > kNoallocMaxCells) {
+        snprintf(g_last_error, sizeof(g_last_error),
+                 "vegas_iterate_noalloc: n_dim * n_bins = %d exceeds the static scratch limit %d",
+                 d * N, kNoallocMaxCells);
+        return VEGAS_EINVAL;
+    }
+    if (itg->n_dim != d) return VEGAS_EINVAL;
+    const int np = n_params_for(itg->family, d);
+    if (np < 0 || itg->n_params != np || (np > 0 && !itg->params)) return VEGAS_EINVAL;
+    if (itg->family == VEGAS_F_LO && d != 3) return VEGAS_EINVAL;
+    FamilyConsts fc;
+    double norm = 1.0, fmax = 1.0;
+    if (!prepare_family(itg->family, d, itg->params, fc, norm, fmax)) return VEGAS_EINVAL;
+
+    char *scratch = nullptr;
+    const vegas_status st = noalloc_scratch(&scratch);
+    if (st != VEGAS_OK) return st;
+    cudaError_t err;
+    const DeviceInfo di = device_info(&err);
+    if (err != cudaSuccess) {
+        set_error("device query", err);
+        return VEGAS_ECUDA;
+    }
+    const int mode = mode_of(cfg->precision);
+    const size_t budget = di.smem_optin > 1024 ? di.smem_optin - 1024 : 0;
+    const bool priv = sample_smem(mode, true, d, N) <= budget;
+    const size_t smem = sample_smem(mode, priv, d, N);
+    if (smem > budget) return VEGAS_EINVAL;
+    const void *fn = sample_kernel(mode, itg->family, d, priv);
+    if (!fn) return VEGAS_EINVAL;
+    VEGAS_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(smem)));
+    const int threads = 512;
+    int occ = 0;
+    VEGAS_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem));
+    if (occ < 1) return VEGAS_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+    double *acc = reinterpret_cast<double *>(scratch + kNaAcc);
+    auto *nonfinite = reinterpret_cast<unsigned long long *>(scratch + kNaNonfinite);
+    float *hscale = reinterpret_cast<float *>(scratch + kNaHscale);
+    void *table = scratch + kNaTable;
+    // the array keeps the previous call's contents: clear the accumulators,
+    // the non-finite counter and the histogram scale (0: FP32 cells)
+    VEGAS_CK(cudaMemsetAsync(scratch, 0, kNaTable, s));
+    VEGAS_CK(launch_table_from_edges(dev_edges, table, mode, d, N, s));
+
+    const double scale = std::ldexp(1.0, -static_cast<int>(std::lround(std::log2(fmax))));
+    const double Nd = static_cast<double>(N);
+    SampleArgs a;
+    a.table = table;
+    a.acc = acc;
+    a.n_nonfinite = nonfinite;
+    a.d = d;
+    a.N = N;
+    a.key0 = cfg->seed;
+    a.key1 = cfg->integral_id;
+    a.iter = static_cast<uint32_t>(t);
+    a.jinit = mode == ACC_F64 ? norm * scale * std::pow(Nd, d) : norm * scale * std::pow(Nd, d % 4);
+    a.nblk4 = Nd * Nd * Nd * Nd;
+    a.hscale = hscale;
+    a.fc64 = fc;
+    for (int k = 0; k < 32; ++k) {
+        a.fc32.p[k] = static_cast<float>(fc.p[k]);
+        a.fc32.q[k] = static_cast<float>(fc.q[k]);
+    }
+    for (int k = 0; k < 8; ++k) a.fc32.s[k] = static_cast<float>(fc.s[k]);
+    const long long n = cfg->n_events;
+    const long long lim = cfg->events_limit > 0 ? cfg->events_limit : n;
+    for (long long s0 = 0; s0 < n; s0 += lim) {
+        a.s_begin = s0;
+        a.n = std::min(lim, n - s0);
+        const long long want = (a.n + threads * 4LL - 1) / (threads * 4LL);
+        long long blocks = std::max(1LL, std::min<long long>(static_cast<long long>(occ) * di.sms, want));
+        if (mode != ACC_F64) blocks = std::max(blocks, (a.n + 2048LL * N - 1) / (2048LL * N));
+        void *params[] = {&a};
+        VEGAS_CK(cudaLaunchKernel(fn, dim3(static_cast<unsigned>(blocks)), dim3(threads), params, smem, s));
+    }
+    const int total = 2 + d * N;
+    noalloc_unscale_kernel<<<(total + 255) / 256, 256, 0, s>>>(acc, dev_sums, total, 1.0 / scale,
+                                                               1.0 / (scale * scale));
+    VEGAS_CK(cudaGetLastError());
+    return VEGAS_OK;
+}

@@ -194,6 +194,32 @@ def vegas_philox(ctr: torch.Tensor, key: torch.Tensor, stream=None) -> torch.Ten
     return out
 
 
+def vegas_iterate_noalloc(cfg: Config, family: str, params, t: int, edges: torch.Tensor,
+                          sums: torch.Tensor, stream=None) -> None:
+    """One iteration's sums without any device allocation by the library.
+
+    For callers that cannot allocate device memory at call time (a runtime
+    that owns the device's memory through its own pool, a plugin that must not
+    grow the footprint).  ``edges`` (d x (N+1) float64) and ``sums``
+    (2 + d*N float64) are the caller's CUDA tensors; scratch lives in a fixed
+    array inside the library (n_dim * n_bins <= 4096).  Calls that overlap on
+    the GPU race on that array.
+    """
+    assert edges.is_cuda and sums.is_cuda
+    assert edges.dtype == torch.float64 and sums.dtype == torch.float64
+    assert edges.is_contiguous() and sums.is_contiguous()
+    c = cfg.to_c()
+    p = np.ascontiguousarray(np.asarray(params, dtype=np.float64))
+    itg = nat.VegasIntegrand(nat.FAMILIES[family], int(cfg.n_dim),
+                             p.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if p.size else None,
+                             int(p.size))
+    _, sp = _stream_ptr(stream)
+    check(nat.load().vegas_iterate_noalloc(ctypes.byref(c), ctypes.byref(itg), int(t),
+                                           ctypes.c_void_p(edges.data_ptr()),
+                                           ctypes.c_void_p(sums.data_ptr()), sp),
+          "vegas_iterate_noalloc")
+
+
 def vegas_profile(ctx: Context, enable: bool = True) -> None:
     check(nat.load().vegas_profile(ctx.handle, 1 if enable else 0), "vegas_profile")
 
