@@ -244,6 +244,64 @@ vegas_status vegas_iterate_noalloc(const vegas_config *cfg, const vegas_integran
 vegas_status vegas_profile(vegas_ctx *ctx, int32_t enable);
 vegas_status vegas_profile_read(vegas_ctx *ctx, float *ms_out, int32_t cap, int32_t *count);
 
+/* ------------------------------------------------------------------------
+ * Batched form: many integrals of uneven dimension, family and sample count
+ * advance one iteration each per step, in one persistent sampling launch plus
+ * a finalize and a refinement launch, replayed as one captured CUDA graph.
+ * (The paper distributes one integral's events over devices, Sec. 3.1-3.2;
+ * batching many integrals on one device is this library's serving form.)
+ *
+ * Sample s of a slot in iteration t draws the same Philox words as in a
+ * single-integral context with the same seed and integral_id, so each slot's
+ * iteration estimates equal its estimates alone up to summation order.  The
+ * combination across iterations uses running sums (inverse-variance weights,
+ * chi^2 from sum w I^2 - I sum w I).
+ *
+ * The workspace (caller-allocated, 256-byte aligned) holds the step plan,
+ * the per-slot state table and a pool from which each added integral takes
+ * vegas_batch_slot_bytes(cfg) bytes (grid, table, accumulators) until it is
+ * removed: admission is by free slots (EBUSY) and pool bytes (ENOMEM).
+ * Only FP32 precisions (VEGAS_FP32_KAHAN, VEGAS_FP32_ACC64).  A step is a
+ * captured CUDA graph, which the legacy NULL stream cannot hold: with
+ * stream == NULL the batch creates (and destroys) its own stream. */
+typedef struct vegas_batch vegas_batch;
+
+typedef struct {
+    int32_t slot;              /* slot id                                   */
+    int32_t t;                 /* Philox iteration word of the step's iteration */
+    vegas_iter_result it;      /* that iteration                            */
+    vegas_result_t comb;       /* combination of all its iterations so far;
+                                  comb.reserved = 6 if every weight was non-finite */
+} vegas_batch_result;
+
+size_t vegas_batch_workspace_bytes(int32_t max_slots, size_t pool_bytes);
+size_t vegas_batch_slot_bytes(const vegas_config *cfg);
+vegas_status vegas_batch_create(int32_t max_slots, int32_t precision, void *stream, void *dev_workspace,
+                                size_t ws_bytes, vegas_batch **out);
+/* Add an integral (uniform grid, iteration 0).  cfg->precision must be the
+ * batch's; cfg->n_events is its samples per iteration.  Synchronises the
+ * stream.  *slot receives its id. */
+vegas_status vegas_batch_add(vegas_batch *b, const vegas_config *cfg, const vegas_integrand *integrand,
+                             int32_t *slot);
+vegas_status vegas_batch_remove(vegas_batch *b, int32_t slot);
+/* One iteration of every slot (asynchronous; waits for the previous step). */
+vegas_status vegas_batch_step(vegas_batch *b);
+/* Wait for the last step and copy out up to cap results (one per slot run,
+ * largest sample count first); *count = number written. */
+vegas_status vegas_batch_wait(vegas_batch *b, vegas_batch_result *out, int32_t cap, int32_t *count);
+vegas_status vegas_batch_get_grid(vegas_batch *b, int32_t slot, double *edges_host);
+/* Samples per tile (multiple of 512): the unit blocks claim.  Autotune times
+ * the sampling kernel for each candidate on the current slots (results are
+ * discarded, slot state is unchanged), keeps the fastest and writes the
+ * average times (ms) to ms_out (may be NULL). */
+vegas_status vegas_batch_set_tile(vegas_batch *b, int32_t tile_samples);
+vegas_status vegas_batch_autotune(vegas_batch *b, const int32_t *candidates, int32_t n_candidates,
+                                  int32_t reps, float *ms_out, int32_t *best);
+vegas_status vegas_batch_info(vegas_batch *b, int32_t *n_active, size_t *pool_free, size_t *pool_largest,
+                              int32_t *tile_samples);
+void vegas_batch_destroy(vegas_batch *b);
+const char *vegas_batch_last_error(void);
+
 void vegas_destroy(vegas_ctx *ctx);
 const char *vegas_strerror(vegas_status st);
 const char *vegas_last_error_string(void);

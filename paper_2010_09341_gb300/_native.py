@@ -44,6 +44,11 @@ class VegasResult(ctypes.Structure):
                 ("reserved", ctypes.c_int32)]
 
 
+class VegasBatchResult(ctypes.Structure):
+    _fields_ = [("slot", ctypes.c_int32), ("t", ctypes.c_int32), ("it", VegasIterResult),
+                ("comb", VegasResult)]
+
+
 class VegasError(RuntimeError):
     def __init__(self, status, what=""):
         self.status = status
@@ -81,6 +86,25 @@ _SIGS = {
     "vegas_profile": (ctypes.c_int, [_P, ctypes.c_int32]),
     "vegas_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float), ctypes.c_int32,
                                           ctypes.POINTER(ctypes.c_int32)]),
+    "vegas_batch_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int32, ctypes.c_size_t]),
+    "vegas_batch_slot_bytes": (ctypes.c_size_t, [ctypes.POINTER(VegasConfig)]),
+    "vegas_batch_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _P, _P, ctypes.c_size_t,
+                                          ctypes.POINTER(_P)]),
+    "vegas_batch_add": (ctypes.c_int, [_P, ctypes.POINTER(VegasConfig), ctypes.POINTER(VegasIntegrand),
+                                       ctypes.POINTER(ctypes.c_int32)]),
+    "vegas_batch_remove": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "vegas_batch_step": (ctypes.c_int, [_P]),
+    "vegas_batch_wait": (ctypes.c_int, [_P, ctypes.POINTER(VegasBatchResult), ctypes.c_int32,
+                                        ctypes.POINTER(ctypes.c_int32)]),
+    "vegas_batch_get_grid": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
+    "vegas_batch_set_tile": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "vegas_batch_autotune": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
+                                            ctypes.c_int32, ctypes.POINTER(ctypes.c_float),
+                                            ctypes.POINTER(ctypes.c_int32)]),
+    "vegas_batch_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_size_t),
+                                        ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_int32)]),
+    "vegas_batch_destroy": (None, [_P]),
+    "vegas_batch_last_error": (ctypes.c_char_p, []),
     "vegas_destroy": (None, [_P]),
     "vegas_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "vegas_last_error_string": (ctypes.c_char_p, []),

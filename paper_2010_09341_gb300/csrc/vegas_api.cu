@@ -36,7 +36,7 @@ constexpr size_t kAlign = 256;
 inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-    size_t edges, table, acc, last, nonfinite, hscale, iters, comb, total;
+    size_t edges, table, acc, last, nonfinite, hscale, jmul, iters, comb, total;
 };
 
 Layout layout_for(int d, int N) {
@@ -54,6 +54,8 @@ Layout layout_for(int d, int N) {
     off = align_up(off + sizeof(unsigned long long));
     L.hscale = off;
     off = align_up(off + sizeof(float));
+    L.jmul = off;
+    off = align_up(off + sizeof(double));
     L.iters = off;
     off = align_up(off + sizeof(IterRec) * VEGAS_MAX_ITERS);
     L.comb = off;
@@ -188,6 +190,7 @@ struct vegas_ctx {
     double *last;
     unsigned long long *nonfinite;
     float *hscale;
+    double *jmul;
     IterRec *iters;
     CombRec *comb;
     int t;          // Philox iteration word of the next iteration
@@ -299,6 +302,7 @@ vegas_status vegas_create(const vegas_config *cfg, const vegas_integrand *itg, v
     c->last = reinterpret_cast<double *>(c->ws + L.last);
     c->nonfinite = reinterpret_cast<unsigned long long *>(c->ws + L.nonfinite);
     c->hscale = reinterpret_cast<float *>(c->ws + L.hscale);
+    c->jmul = reinterpret_cast<double *>(c->ws + L.jmul);
     c->iters = reinterpret_cast<IterRec *>(c->ws + L.iters);
     c->comb = reinterpret_cast<CombRec *>(c->ws + L.comb);
     c->t = 0;
@@ -324,6 +328,8 @@ vegas_status vegas_create(const vegas_config *cfg, const vegas_integrand *itg, v
     cudaError_t ce = cudaMemcpyAsync(c->edges, e.data(), e.size() * sizeof(double),
                                      cudaMemcpyHostToDevice, c->stream);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(c->acc, 0, (L.hscale + sizeof(float)) - L.acc, c->stream);
+    static const double kOne = 1.0;
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(c->jmul, &kOne, sizeof(double), cudaMemcpyHostToDevice, c->stream);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(c->comb, 0, sizeof(CombRec), c->stream);
     if (ce == cudaSuccess) ce = launch_table_from_edges(c->edges, c->table, mode, d, N, c->stream);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
@@ -350,6 +356,7 @@ static SampleArgs make_args(const vegas_ctx *c, long long s_begin, long long n, 
     a.iter = static_cast<uint32_t>(t);
     a.jinit = c->jinit;
     a.nblk4 = c->nblk4;
+    a.jmul = c->jmul;
     a.hscale = c->hscale;
     a.fc64 = c->fc;
     for (int k = 0; k < 32; ++k) {
@@ -398,8 +405,9 @@ vegas_status vegas_iterate(vegas_ctx *c, vegas_iter_result *out) {
         if (st != VEGAS_OK) return st;
     }
     if (pe) VEGAS_CK(cudaEventRecord(pe->second, c->stream));
-    VEGAS_CK(launch_finalize(c->acc, c->last, c->nonfinite, c->hscale, c->iters, c->comb, c->n_done,
-                             n, c->cfg.n_dim, c->cfg.n_bins, 1.0 / c->scale, c->stream));
+    VEGAS_CK(launch_finalize(c->acc, c->last, c->nonfinite, c->hscale, c->jmul, c->iters, c->comb,
+                             c->n_done, n, c->cfg.n_dim, c->cfg.n_bins, 1.0 / c->scale, c->jinit,
+                             c->stream));
     const int rec = c->n_done;
     c->n_done += 1;
     c->t += 1;
@@ -526,6 +534,9 @@ struct BlobHeader {
     int32_t n_params;
     int32_t t;
     int32_t n_done;
+    float hscale;       // fixed-point histogram scale of the next iteration
+    int32_t pad;
+    double jmul;        // rescale of v of the next iteration
 };
 constexpr uint32_t kMagic = 0x56454741u;  // "VEGA"
 }  // namespace
@@ -544,8 +555,11 @@ vegas_status vegas_export_state(vegas_ctx *c, void *buf, size_t *size) {
     char *p = static_cast<char *>(buf);
     BlobHeader h;
     memset(&h, 0, sizeof(h));
+    VEGAS_CK(cudaMemcpyAsync(&h.hscale, c->hscale, sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    VEGAS_CK(cudaMemcpyAsync(&h.jmul, c->jmul, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    VEGAS_CK(cudaStreamSynchronize(c->stream));
     h.magic = kMagic;
-    h.version = 1;
+    h.version = 2;
     h.cfg = c->cfg;
     h.family = c->family;
     h.n_params = static_cast<int32_t>(c->params.size());
@@ -573,7 +587,7 @@ vegas_status vegas_import_state(vegas_ctx *c, const void *buf, size_t size) {
     BlobHeader h;
     memcpy(&h, p, sizeof(h));
     p += sizeof(h);
-    if (h.magic != kMagic || h.version != 1) return VEGAS_EINVAL;
+    if (h.magic != kMagic || h.version != 2) return VEGAS_EINVAL;
     const vegas_config &a = h.cfg, &b = c->cfg;
     if (a.n_dim != b.n_dim || a.n_bins != b.n_bins || a.n_events != b.n_events ||
         a.seed != b.seed || a.integral_id != b.integral_id || a.precision != b.precision ||
@@ -595,6 +609,8 @@ vegas_status vegas_import_state(vegas_ctx *c, const void *buf, size_t size) {
                                  c->stream));
     p += sizeof(IterRec) * h.n_done;
     VEGAS_CK(cudaMemcpyAsync(c->comb, p, sizeof(CombRec), cudaMemcpyHostToDevice, c->stream));
+    VEGAS_CK(cudaMemcpyAsync(c->hscale, &h.hscale, sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    VEGAS_CK(cudaMemcpyAsync(c->jmul, &h.jmul, sizeof(double), cudaMemcpyHostToDevice, c->stream));
     VEGAS_CK(launch_table_from_edges(c->edges, c->table, c->mode, d, N, c->stream));
     VEGAS_CK(cudaStreamSynchronize(c->stream));
     c->t = h.t;
@@ -632,6 +648,14 @@ vegas_status vegas_profile_read(vegas_ctx *c, float *ms_out, int32_t cap, int32_
 void vegas_destroy(vegas_ctx *c) { delete c; }
 
 }  // extern "C"
+
+// Family constants and parameter counts for the batched form (vegas_batch.cu).
+namespace vegas {
+bool host_prepare_family(int family, int d, const double *p, FamilyConsts &fc, double &norm, double &fmax) {
+    return prepare_family(family, d, p, fc, norm, fmax);
+}
+int host_n_params(int family, int d) { return n_params_for(family, d); }
+}  // namespace vegas
 
 // ------------------------------------------------------- no-allocation form
 // One iteration's sums with every piece of scratch in a file-scope device
@@ -742,6 +766,7 @@ extern "C" vegas_status vegas_iterate_noalloc(const vegas_config *cfg, const veg
     a.iter = static_cast<uint32_t>(t);
     a.jinit = mode == ACC_F64 ? norm * scale * std::pow(Nd, d) : norm * scale * std::pow(Nd, d % 4);
     a.nblk4 = Nd * Nd * Nd * Nd;
+    a.jmul = nullptr;
     a.hscale = hscale;
     a.fc64 = fc;
     for (int k = 0; k < 32; ++k) {

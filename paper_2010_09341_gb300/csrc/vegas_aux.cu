@@ -7,6 +7,7 @@
 // squared deviations), and they touch O(d N) values, so their cost is
 // launch latency, not arithmetic.
 #include "vegas_kernels.cuh"
+#include "vegas_refine.cuh"
 
 namespace vegas {
 
@@ -18,26 +19,27 @@ namespace vegas {
 // sigma 0.
 __global__ void __launch_bounds__(256)
 finalize_kernel(double *acc, double *last, unsigned long long *n_nonfinite, float *hscale,
-                IterRec *iters, CombRec *comb, int t, long long n, int total, double inv1,
-                double inv2) {
+                double *jmul, IterRec *iters, CombRec *comb, int t, long long n, int total,
+                double inv_scale0, double jinit0) {
     __shared__ double sh[3][8];
     __shared__ double mean_s;
     __shared__ int nzero_s;
+    __shared__ double inv_s;
     if (threadIdx.x == 0) {
-        // fixed-point histogram scale for the next iteration: the mean of the
-        // (scaled) v^2 maps to 2^18 (values up to 32x it stay below 2^23);
-        // 0 if there is no usable mean
+        // v was accumulated scaled by scale0 * jmul; the next iteration's
+        // rescale and fixed-point histogram scale come from this one's mean v^2
+        const double jm = *jmul;
+        inv_s = inv_scale0 / jm;
         const long long ne = n - static_cast<long long>(*n_nonfinite);
         const double m2 = ne > 0 ? acc[1] / static_cast<double>(ne) : 0.0;
-        float hs = 0.f;
-        if (m2 > 0.0 && isfinite(m2)) {
-            int e = 18 - static_cast<int>(ceil(log2(m2)));
-            e = max(-100, min(100, e));
-            hs = ldexpf(1.0f, e);
-        }
+        double ratio;
+        float hs;
+        next_scales(m2, jinit0 * jm, &ratio, &hs);
         *hscale = hs;
+        *jmul = jm * ratio;
     }
     __syncthreads();
+    const double inv1 = inv_s, inv2 = inv_s * inv_s;
     for (int c = threadIdx.x; c < total; c += blockDim.x) {
         last[c] = acc[c] * (c == 0 ? inv1 : inv2);
         acc[c] = 0.0;
@@ -152,135 +154,25 @@ finalize_kernel(double *acc, double *last, unsigned long long *n_nonfinite, floa
 }
 
 cudaError_t launch_finalize(double *acc, double *last, unsigned long long *n_nonfinite,
-                            float *hscale, IterRec *iters, CombRec *comb, int t, long long n,
-                            int d, int N, double inv_scale, cudaStream_t stream) {
+                            float *hscale, double *jmul, IterRec *iters, CombRec *comb, int t,
+                            long long n, int d, int N, double inv_scale0, double jinit0,
+                            cudaStream_t stream) {
     const int total = 2 + d * N;
-    finalize_kernel<<<1, 256, 0, stream>>>(acc, last, n_nonfinite, hscale, iters, comb, t, n,
-                                           total, inv_scale, inv_scale * inv_scale);
+    finalize_kernel<<<1, 256, 0, stream>>>(acc, last, n_nonfinite, hscale, jmul, iters, comb, t, n,
+                                           total, inv_scale0, jinit0);
     return cudaGetLastError();
 }
 
 // --------------------------------------------------------------- refine
-// Grid refinement of one dimension per block (Lepage 1980):
-//   smooth   d_0 = (h_0+h_1)/2, d_k = (h_{k-1}+h_k+h_{k+1})/3, d_{N-1} = (h_{N-2}+h_{N-1})/2
-//   normalise d_k /= sum d
-//   compress rho_k = ((1 - d_k)/ln(1/d_k))^alpha   (0 at d = 0, 1 at d = 1)
-//   rebin    new edge k (1..N-1) where the running rho sum reaches k sum(rho)/N,
-//            interpolated linearly inside the old bin; zero-weight bins are
-//            skipped and an edge on an old edge takes the lower bin.
-// A dimension whose weights sum to zero keeps its grid.
-template <class T2, class T>
-__device__ __forceinline__ void write_entry(void *table, int idx, double e, double w) {
-    reinterpret_cast<T2 *>(table)[idx] = T2{static_cast<T>(e - w), static_cast<T>(w)};
-}
-
-__device__ __forceinline__ void store_table(void *table, int mode, int idx, double e, double w) {
-    if (mode == ACC_F64) write_entry<double2, double>(table, idx, e, w);
-    else write_entry<float2, float>(table, idx, e, w);
-}
-
-constexpr int kRefineThreads = 128;
-
 __global__ void __launch_bounds__(kRefineThreads)
 refine_kernel(const double *last, double *edges, void *table, int mode, int N, double alpha,
               int smooth) {
     extern __shared__ double rs[];
-    double *eo = rs;            // old edges, N+1
-    double *rho = rs + (N + 1); // compressed weights, N
-    double *cum = rho + N;      // inclusive running sum, N
-    __shared__ double red[kRefineThreads / 32];
-    __shared__ double total_s;
     const int j = blockIdx.x;
-    const double *h = last + 2 + static_cast<size_t>(j) * N;
-    double *e = edges + static_cast<size_t>(j) * (N + 1);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int k = tid; k <= N; k += blockDim.x) eo[k] = e[k];
-
-    // smoothing, kept in rho[] for now
-    double part = 0.0;
-    for (int k = tid; k < N; k += blockDim.x) {
-        double v;
-        if (!smooth) v = h[k];
-        else if (k == 0) v = (h[0] + h[1]) / 2.0;
-        else if (k == N - 1) v = (h[N - 2] + h[N - 1]) / 2.0;
-        else v = (h[k - 1] + h[k] + h[k + 1]) / 3.0;
-        rho[k] = v;
-        part += v;
-    }
-    part = warp_sum(part);
-    if (lane == 0) red[warp] = part;
-    __syncthreads();
-    if (tid == 0) {
-        double s = 0.0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += red[k];
-        total_s = s;
-    }
-    __syncthreads();
-    const double total = total_s;
-    if (!(total > 0.0) || !isfinite(total)) return;  // keep the grid (table unchanged)
-
-    // normalise and compress
-    for (int k = tid; k < N; k += blockDim.x) {
-        const double dk = rho[k] / total;
-        double r;
-        if (dk <= 0.0) r = 0.0;
-        else if (dk >= 1.0) r = 1.0;
-        else r = pow((1.0 - dk) / log(1.0 / dk), alpha);
-        rho[k] = r;
-    }
-    __syncthreads();
-
-    // inclusive scan of rho: each thread a contiguous chunk, then chunk offsets
-    const int chunk = (N + blockDim.x - 1) / blockDim.x;
-    const int k0 = tid * chunk, k1 = min(N, k0 + chunk);
-    double run = 0.0;
-    for (int k = k0; k < k1; ++k) {
-        run += rho[k];
-        cum[k] = run;
-    }
-    double incl = run;  // warp inclusive scan of chunk totals
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const double y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    if (lane == 31) red[warp] = incl;
-    __syncthreads();
-    double off = incl - run;
-    for (int w = 0; w < warp; ++w) off += red[w];
-    for (int k = k0; k < k1; ++k) cum[k] += off;
-    __syncthreads();
-    const double rsum = cum[N - 1];
-    if (!(rsum > 0.0)) return;
-    const double delta = rsum / static_cast<double>(N);
-
-    // rebin: new edge k is in the first old bin whose inclusive sum reaches k delta
-    for (int k = tid; k <= N; k += blockDim.x) {
-        double ek;
-        if (k == 0) ek = 0.0;
-        else if (k == N) ek = 1.0;
-        else {
-            const double target = static_cast<double>(k) * delta;
-            int lo = 0, hi = N - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (cum[mid] >= target) hi = mid;
-                else lo = mid + 1;
-            }
-            const int b = lo;
-            const double before = b > 0 ? cum[b - 1] : 0.0;
-            double frac = rho[b] > 0.0 ? (target - before) / rho[b] : 1.0;
-            frac = fmin(fmax(frac, 0.0), 1.0);
-            ek = eo[b] + frac * (eo[b + 1] - eo[b]);
-        }
-        rs[3 * N + 1 + k] = ek;  // new edges after cum[]
-    }
-    __syncthreads();
-    const double *en = rs + 3 * N + 1;
-    for (int k = tid; k <= N; k += blockDim.x) e[k] = en[k];
-    for (int k = tid; k < N; k += blockDim.x) {
-        store_table(table, mode, j * N + k, en[k], en[k + 1] - en[k]);
-    }
+    const size_t entry = mode == ACC_F64 ? sizeof(double2) : sizeof(float2);
+    refine_block(last + 2 + static_cast<size_t>(j) * N, edges + static_cast<size_t>(j) * (N + 1),
+                 static_cast<char *>(table) + entry * static_cast<size_t>(j) * N, mode, N, alpha,
+                 smooth, rs);
 }
 
 cudaError_t launch_refine(const double *last, double *edges, void *table, int mode, int d, int N,
@@ -321,7 +213,8 @@ __global__ void trace_kernel(const SampleArgs a, double inv_scale, int32_t *bins
     const FamConsts<T> &fc = consts<T>(a);
     const unsigned long long s = static_cast<unsigned long long>(a.s_begin + k);
     const uint32_t slo = static_cast<uint32_t>(s), shi = static_cast<uint32_t>(s >> 32);
-    T J = static_cast<T>(a.jinit);
+    const double jm = a.jmul ? *a.jmul : 1.0;
+    T J = static_cast<T>(a.jinit * jm);
     const T n4 = static_cast<T>(a.nblk4);
     fam.begin(fc);
 #pragma unroll
@@ -348,7 +241,7 @@ __global__ void trace_kernel(const SampleArgs a, double inv_scale, int32_t *bins
         }
     }
     const T v = J * fam.finish(fc);
-    if (ws) ws[k] = static_cast<double>(v) * inv_scale;
+    if (ws) ws[k] = static_cast<double>(v) * (inv_scale / jm);
 }
 
 template <int MODE, int FAM>

@@ -38,9 +38,11 @@ size_t sample_smem(int mode, bool priv, int d, int N);
 // Finalize: move the accumulators (unscaled) to `last`, zero them, form
 // I_t and sigma_t, store iters[t] and recombine all iterations into *comb.
 // Also sets *hscale, the fixed-point histogram scale of the next iteration.
+// Also rescales v for the next iteration (*jmul) -- see next_scales.
 cudaError_t launch_finalize(double *acc, double *last, unsigned long long *n_nonfinite,
-                            float *hscale, IterRec *iters, CombRec *comb, int t, long long n,
-                            int d, int N, double inv_scale, cudaStream_t stream);
+                            float *hscale, double *jmul, IterRec *iters, CombRec *comb, int t,
+                            long long n, int d, int N, double inv_scale0, double jinit0,
+                            cudaStream_t stream);
 
 // Refine every dimension from the histograms in last[2..] and write the new
 // FP64 edges and the sampling table of the given mode.

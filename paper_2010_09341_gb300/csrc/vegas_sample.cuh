@@ -30,7 +30,8 @@ struct SampleArgs {
     int d, N;
     uint32_t key0, key1;      // Philox key (seed, integral id)
     uint32_t iter;            // Philox counter word 2
-    double jinit;             // initial weight C (includes N^d and scale)
+    double jinit;             // initial weight C (includes N^d and the initial scale of v)
+    const double *jmul;       // device: power-of-two rescale of v set by the last finalize (null: 1)
     double nblk4;             // N^4 (FP32 path multiplies it in every 4 dims)
     const float *hscale;      // FP32 modes: fixed-point scale of v^2 (0: float cells)
     FamConsts<double> fc64;   // integrand constants, FP64 path
@@ -100,6 +101,28 @@ __host__ __device__ constexpr size_t sample_smem_bytes(int d, int N) {
 __device__ __forceinline__ void red_add_shared(float *p, float v) { atomicAdd(p, v); }
 __device__ __forceinline__ void red_add_shared(double *p, double v) { atomicAdd(p, v); }
 
+// Scales for the next iteration from m2, the mean of this iteration's scaled
+// v^2 (0 if none): a power of two `ratio` that brings the mean of v^2 near 1
+// (FP32 keeps its full precision for v and v^2 whatever the size of the
+// integral), limited so that the initial weight jinit * jmul * ratio stays
+// within 2^-100..2^100, and the fixed-point histogram scale that maps the
+// rescaled mean to 2^18.
+__device__ __forceinline__ void next_scales(double m2, double jinit_eff, double *ratio, float *hs) {
+    double r = 1.0;
+    float h = 0.f;
+    if (m2 > 0.0 && isfinite(m2)) {
+        int e = -static_cast<int>(rint(0.5 * log2(m2)));
+        const int ej = static_cast<int>(rint(log2(fabs(jinit_eff) > 0.0 ? fabs(jinit_eff) : 1.0)));
+        e = max(-100 - ej, min(100 - ej, e));
+        r = ldexp(1.0, e);
+        int eh = 18 - static_cast<int>(ceil(log2(m2 * r * r)));
+        eh = max(-100, min(100, eh));
+        h = ldexpf(1.0f, eh);
+    }
+    *ratio = r;
+    *hs = h;
+}
+
 // Warp-level FP64 sum.
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -107,59 +130,79 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// EXACT: the dimension equals MAXD (no per-dimension guards); otherwise
-// 1 <= a.d <= MAXD at run time.
-template <int FAM, int MODE, int MAXD, bool EXACT, bool PRIV>
-__global__ void __launch_bounds__(512)
-vegas_sample_kernel(const SampleArgs a) {
+// Shared-memory working set of one block for one integral: the table (TP
+// copies per cell), the coarse histogram cells (HP copies per cell) and, in
+// the FP32 modes, one fine cell per (dimension, bin).
+template <int MODE, bool PRIV> struct BlockState {
     using Tr = ModeTraits<MODE>;
     using T = typename Tr::T;
     using T2 = typename Prec<T>::T2;
     using H = typename Tr::H;
-    constexpr int TP = PRIV ? Tr::TP : 1;
-    constexpr int HP = PRIV ? Tr::HP : 1;
+    static constexpr int TP = PRIV ? Tr::TP : 1;
+    static constexpr int HP = PRIV ? Tr::HP : 1;
+    T2 *tab;
+    H *hist;
+    uint32_t *fine;
+    int cells;
 
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int d = EXACT ? MAXD : a.d;
-    const int N = a.N;
-    const int cells = d * N;
-    T2 *tab = reinterpret_cast<T2 *>(smem_raw);
-    H *hist = reinterpret_cast<H *>(smem_raw + static_cast<size_t>(cells) * TP * sizeof(T2));
-    uint32_t *fine = reinterpret_cast<uint32_t *>(hist + static_cast<size_t>(cells) * HP);  // FP32 modes
+    __device__ __forceinline__ void carve(unsigned char *raw, int ncells) {
+        cells = ncells;
+        tab = reinterpret_cast<T2 *>(raw);
+        hist = reinterpret_cast<H *>(raw + static_cast<size_t>(cells) * TP * sizeof(T2));
+        fine = reinterpret_cast<uint32_t *>(hist + static_cast<size_t>(cells) * HP);
+    }
+    // Every thread of the block calls this; the caller synchronises after it.
+    __device__ __forceinline__ void stage(const void *gtable) {
+        const T2 *g = static_cast<const T2 *>(gtable);
+        for (int k = threadIdx.x; k < cells * TP; k += blockDim.x) tab[k] = g[k / TP];
+        for (int k = threadIdx.x; k < cells * HP; k += blockDim.x) hist[k] = H(0);
+        if (MODE != ACC_F64)
+            for (int k = threadIdx.x; k < cells; k += blockDim.x) fine[k] = 0u;
+    }
+};
 
-    // stage the grid table (TP copies per cell) and zero the histogram
-    const float hs = (MODE != ACC_F64) ? *a.hscale : 0.f;
-    const bool fixed = hs > 0.f;
-    const T2 *gtab = static_cast<const T2 *>(a.table);
-    for (int k = threadIdx.x; k < cells * TP; k += blockDim.x) tab[k] = gtab[k / TP];
-    for (int k = threadIdx.x; k < cells * HP; k += blockDim.x) hist[k] = H(0);
-    if (MODE != ACC_F64)
-        for (int k = threadIdx.x; k < cells; k += blockDim.x) fine[k] = 0u;
-    __syncthreads();
-
-    const int lane = threadIdx.x & 31;
-    const T2 *tab_l = tab + (lane % TP);
-    H *hist_l = hist + (lane % HP);
-
-    Integrand<FAM, T, MAXD> fam;
-    const FamConsts<T> &fc = consts<T>(a);
-    const T jinit = static_cast<T>(a.jinit);
-    const T n4 = static_cast<T>(a.nblk4);
-
-    // contiguous sample range of this block
-    const long long per = (a.n + gridDim.x - 1) / gridDim.x;
-    const long long lo = static_cast<long long>(blockIdx.x) * per;
-    const long long hi = min(a.n, lo + per);
-
-    double s1d = 0.0, s2d = 0.0;       // FP64 sums (ACC_F64, ACC_F32_SUM64)
+// Per-thread running sums of v and v^2 and the non-finite count.
+template <int MODE> struct ThreadSums {
+    double s1d = 0.0, s2d = 0.0;                     // ACC_F64, ACC_F32_SUM64
     float s1f = 0.f, c1f = 0.f, s2f = 0.f, c2f = 0.f;  // ACC_F32_KAHAN
     unsigned int nonfinite = 0;
+};
 
-    // Each thread takes every blockDim-th sample of the block's range, in
-    // chunks of kChunk; ACC_F32_SUM64 adds a chunk's FP32 partial sums into
-    // the FP64 sums once per chunk.
+// Scalars of one integral's iteration that the sampling loop needs.
+template <class T> struct RangeParams {
+    int d, N;
+    uint32_t key0, key1, iter;
+    T jinit, n4;
+    float hs;        // fixed-point scale of v^2 (FP32 modes); 0: FP32 cells
+    double *acc;     // FP64 accumulators [2 + d N] (values beyond the fixed range)
+};
+
+// The block samples [s0, s0 + cnt) of one integral: thread t takes
+// s0 + t + u * blockDim, in chunks of kChunk samples (ACC_F32_SUM64 adds a
+// chunk's FP32 partial sums into the FP64 sums once per chunk).
+// EXACT: the dimension equals MAXD (no per-dimension guards); otherwise
+// 1 <= rp.d <= MAXD at run time.
+template <int FAM, int MODE, int MAXD, bool EXACT, bool PRIV>
+__device__ __forceinline__ void sample_range(const BlockState<MODE, PRIV> &bs,
+                                             const RangeParams<typename ModeTraits<MODE>::T> &rp,
+                                             const FamConsts<typename ModeTraits<MODE>::T> &fc,
+                                             ThreadSums<MODE> &ts, unsigned long long s0, int cnt) {
+    using BS = BlockState<MODE, PRIV>;
+    using T = typename BS::T;
+    using T2 = typename BS::T2;
+    using H = typename BS::H;
+    constexpr int TP = BS::TP;
+    constexpr int HP = BS::HP;
+    const int d = EXACT ? MAXD : rp.d;
+    const int N = rp.N;
+    const int lane = threadIdx.x & 31;
+    const T2 *tab_l = bs.tab + (lane % TP);
+    H *hist_l = bs.hist + (lane % HP);
+    const float hs = rp.hs;
+    const bool fixed = hs > 0.f;
+    Integrand<FAM, T, MAXD> fam;
+
     constexpr int kChunk = 8;
-    const int cnt = static_cast<int>(hi - lo);  // samples of this block (< 2^31)
     const int stride = blockDim.x;
     for (int k0 = threadIdx.x; k0 < cnt; k0 += kChunk * stride) {
         float p1 = 0.f, p2 = 0.f;
@@ -167,16 +210,16 @@ vegas_sample_kernel(const SampleArgs a) {
         for (int u = 0; u < kChunk; ++u) {
             const int k = k0 + u * stride;
             if (k >= cnt) break;
-            const unsigned long long s = static_cast<unsigned long long>(a.s_begin + lo + k);
+            const unsigned long long s = s0 + static_cast<unsigned long long>(k);
             const uint32_t slo = static_cast<uint32_t>(s), shi = static_cast<uint32_t>(s >> 32);
             uint32_t cellj[MAXD];
-            T J = jinit;
+            T J = rp.jinit;
             fam.begin(fc);
 #pragma unroll
             for (int q = 0; q < (MAXD + 3) / 4; ++q) {
                 if (EXACT || 4 * q < d) {
-                    const uint4 r = philox4x32_10(make_uint4(slo, shi, a.iter, static_cast<uint32_t>(q)),
-                                                  a.key0, a.key1);
+                    const uint4 r = philox4x32_10(make_uint4(slo, shi, rp.iter, static_cast<uint32_t>(q)),
+                                                  rp.key0, rp.key1);
 #pragma unroll
                     for (int w = 0; w < 4; ++w) {
                         const int j = 4 * q + w;
@@ -187,7 +230,7 @@ vegas_sample_kernel(const SampleArgs a) {
                             const T m = Prec<T>::mant(sp.lo);
                             const T x = ffma(ent.y, m, ent.x);
                             J *= ent.y;
-                            if (sizeof(T) == 4 && (j & 3) == 3) J *= n4;
+                            if (sizeof(T) == 4 && (j & 3) == 3) J *= rp.n4;
                             cellj[j] = cell;
                             fam.dim(j, x, fc);
                         }
@@ -197,25 +240,25 @@ vegas_sample_kernel(const SampleArgs a) {
             T v = J * fam.finish(fc);
             if (!isfinite(v)) {
                 v = T(0);
-                ++nonfinite;
+                ++ts.nonfinite;
             }
             const T v2 = v * v;
             if (MODE == ACC_F32_KAHAN) {
-                const float y1 = static_cast<float>(v) - c1f;
-                const float t1 = s1f + y1;
-                c1f = (t1 - s1f) - y1;
-                s1f = t1;
-                const float y2 = static_cast<float>(v2) - c2f;
-                const float t2 = s2f + y2;
-                c2f = (t2 - s2f) - y2;
-                s2f = t2;
+                const float y1 = static_cast<float>(v) - ts.c1f;
+                const float t1 = ts.s1f + y1;
+                ts.c1f = (t1 - ts.s1f) - y1;
+                ts.s1f = t1;
+                const float y2 = static_cast<float>(v2) - ts.c2f;
+                const float t2 = ts.s2f + y2;
+                ts.c2f = (t2 - ts.s2f) - y2;
+                ts.s2f = t2;
             } else if (MODE == ACC_F32_SUM64) {
                 p1 += static_cast<float>(v);
                 p2 += static_cast<float>(v2);
             } else {
                 const double vd = static_cast<double>(v);
-                s1d += vd;
-                s2d = __fma_rn(vd, vd, s2d);
+                ts.s1d += vd;
+                ts.s2d = __fma_rn(vd, vd, ts.s2d);
             }
             if (MODE == ACC_F64) {
 #pragma unroll
@@ -233,7 +276,7 @@ vegas_sample_kernel(const SampleArgs a) {
                     const float t = __fmaf_rn(qf, is_fine ? kFineScale : 1.0f, 8388608.0f);
                     uint32_t q = __float_as_uint(t) - 0x4B000000u;
                     q = max(q, 1u);
-                    unsigned int *base = is_fine ? fine : reinterpret_cast<unsigned int *>(hist_l);
+                    unsigned int *base = is_fine ? bs.fine : reinterpret_cast<unsigned int *>(hist_l);
                     const uint32_t step = is_fine ? 1u : static_cast<uint32_t>(HP);
 #pragma unroll
                     for (int j = 0; j < MAXD; ++j) {
@@ -242,7 +285,7 @@ vegas_sample_kernel(const SampleArgs a) {
                 } else {
 #pragma unroll
                     for (int j = 0; j < MAXD; ++j) {
-                        if (EXACT || j < d) atomicAdd(a.acc + 2 + cellj[j], static_cast<double>(v2));
+                        if (EXACT || j < d) atomicAdd(rp.acc + 2 + cellj[j], static_cast<double>(v2));
                     }
                 }
             } else {
@@ -254,26 +297,40 @@ vegas_sample_kernel(const SampleArgs a) {
             }
         }
         if (MODE == ACC_F32_SUM64) {
-            s1d += static_cast<double>(p1);
-            s2d += static_cast<double>(p2);
+            ts.s1d += static_cast<double>(p1);
+            ts.s2d += static_cast<double>(p2);
         }
     }
+}
 
-    // block reduction of S1, S2 and the non-finite count
+// Adds the block's sums to the integral's FP64 accumulators: S1, S2 and the
+// non-finite count by a block reduction, each histogram cell by one warp
+// (FP32 cells summed as a warp tree, 5 levels, then promoted once).  Starts
+// with a barrier (every thread's samples are in) and ends with one (the
+// shared cells may be reused).  Resets ts.
+template <int MODE, bool PRIV>
+__device__ __forceinline__ void flush_block(const BlockState<MODE, PRIV> &bs, ThreadSums<MODE> &ts,
+                                            float hs, double *acc, unsigned long long *n_nonfinite) {
+    using BS = BlockState<MODE, PRIV>;
+    using H = typename BS::H;
+    constexpr int HP = BS::HP;
+    __shared__ double red1[32], red2[32];
+    __shared__ unsigned int rednf[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
     double b1, b2;
     if (MODE == ACC_F32_KAHAN) {
-        b1 = static_cast<double>(s1f) - static_cast<double>(c1f);
-        b2 = static_cast<double>(s2f) - static_cast<double>(c2f);
+        b1 = static_cast<double>(ts.s1f) - static_cast<double>(ts.c1f);
+        b2 = static_cast<double>(ts.s2f) - static_cast<double>(ts.c2f);
     } else {
-        b1 = s1d;
-        b2 = s2d;
+        b1 = ts.s1d;
+        b2 = ts.s2d;
     }
     b1 = warp_sum(b1);
     b2 = warp_sum(b2);
-    unsigned int nf = __reduce_add_sync(0xFFFFFFFFu, nonfinite);
-    __shared__ double red1[16], red2[16];
-    __shared__ unsigned int rednf[16];
-    const int warp = threadIdx.x >> 5;
+    const unsigned int nf = __reduce_add_sync(0xFFFFFFFFu, ts.nonfinite);
+    ts = ThreadSums<MODE>();
+    __syncthreads();
     if (lane == 0) {
         red1[warp] = b1;
         red2[warp] = b2;
@@ -281,36 +338,70 @@ vegas_sample_kernel(const SampleArgs a) {
     }
     __syncthreads();
     if (warp == 0) {
-        const int nw = blockDim.x >> 5;
-        double x1 = lane < nw ? red1[lane] : 0.0;
-        double x2 = lane < nw ? red2[lane] : 0.0;
-        unsigned int xn = lane < nw ? rednf[lane] : 0u;
+        double x1 = lane < nwarps ? red1[lane] : 0.0;
+        double x2 = lane < nwarps ? red2[lane] : 0.0;
+        unsigned int xn = lane < nwarps ? rednf[lane] : 0u;
         x1 = warp_sum(x1);
         x2 = warp_sum(x2);
         xn = __reduce_add_sync(0xFFFFFFFFu, xn);
         if (lane == 0) {
-            atomicAdd(a.acc + 0, x1);
-            atomicAdd(a.acc + 1, x2);
-            if (xn) atomicAdd(a.n_nonfinite, static_cast<unsigned long long>(xn));
+            atomicAdd(acc + 0, x1);
+            atomicAdd(acc + 1, x2);
+            if (xn) atomicAdd(n_nonfinite, static_cast<unsigned long long>(xn));
         }
     }
-    // histogram flush: one warp per cell, lanes over the HP copies.  FP32
-    // cells are summed as a warp tree in FP32 (5 levels) and promoted once.
-    const int nwarps = blockDim.x >> 5;
+    const bool fixed = hs > 0.f;
     const float inv_hs = fixed ? 1.0f / hs : 0.f;
-    for (int c = warp; c < cells; c += nwarps) {
+    for (int c = warp; c < bs.cells; c += nwarps) {
         H h = H(0);
         for (int k = lane; k < HP; k += 32) {
             if (MODE != ACC_F64 && fixed)
-                h += static_cast<H>(static_cast<float>(reinterpret_cast<const unsigned int *>(hist)[c * HP + k]) * inv_hs);
+                h += static_cast<H>(static_cast<float>(reinterpret_cast<const unsigned int *>(bs.hist)[c * HP + k]) * inv_hs);
             else
-                h += hist[c * HP + k];
+                h += bs.hist[c * HP + k];
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(0xFFFFFFFFu, h, o);
-        if (MODE != ACC_F64 && fixed && lane == 0) h += static_cast<H>(static_cast<float>(fine[c]) * (inv_hs * kFineInv));
-        if (lane == 0 && h != H(0)) atomicAdd(a.acc + 2 + c, static_cast<double>(h));
+        if (MODE != ACC_F64 && fixed && lane == 0)
+            h += static_cast<H>(static_cast<float>(bs.fine[c]) * (inv_hs * kFineInv));
+        if (lane == 0 && h != H(0)) atomicAdd(acc + 2 + c, static_cast<double>(h));
     }
+    __syncthreads();
+}
+
+// One integral, samples [a.s_begin, a.s_begin + a.n): each block takes a
+// contiguous range of them.
+template <int FAM, int MODE, int MAXD, bool EXACT, bool PRIV>
+__global__ void __launch_bounds__(512)
+vegas_sample_kernel(const SampleArgs a) {
+    using BS = BlockState<MODE, PRIV>;
+    using T = typename BS::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int d = EXACT ? MAXD : a.d;
+    BS bs;
+    bs.carve(smem_raw, d * a.N);
+    bs.stage(a.table);
+    RangeParams<T> rp;
+    rp.d = d;
+    rp.N = a.N;
+    rp.key0 = a.key0;
+    rp.key1 = a.key1;
+    rp.iter = a.iter;
+    rp.jinit = static_cast<T>(a.jinit * (a.jmul ? *a.jmul : 1.0));
+    rp.n4 = static_cast<T>(a.nblk4);
+    rp.hs = (MODE != ACC_F64) ? *a.hscale : 0.f;
+    rp.acc = a.acc;
+    __syncthreads();
+
+    const long long per = (a.n + gridDim.x - 1) / gridDim.x;
+    const long long lo = static_cast<long long>(blockIdx.x) * per;
+    const long long hi = min(a.n, lo + per);
+    ThreadSums<MODE> ts;
+    if (hi > lo)
+        sample_range<FAM, MODE, MAXD, EXACT, PRIV>(bs, rp, consts<T>(a), ts,
+                                                   static_cast<unsigned long long>(a.s_begin + lo),
+                                                   static_cast<int>(hi - lo));
+    flush_block<MODE, PRIV>(bs, ts, rp.hs, a.acc, a.n_nonfinite);
 }
 
 }  // namespace vegas

@@ -262,3 +262,118 @@ class Integrator:
         if self.ctx is None:
             raise RuntimeError("compile() an integrand first")
         return vegas_run(self.ctx, n_iter)
+
+
+class Batch:
+    """The batched form of the C ABI (vegas_batch_*): many integrals, one
+    iteration of each per step, replayed as one CUDA graph.
+
+    ``pool_bytes`` of device memory hold the added integrals' grids and
+    accumulators (``vegas_batch_slot_bytes`` each); ``max_slots`` bounds their
+    number.  Workspace from PyTorch.
+    """
+
+    def __init__(self, max_slots: int, pool_bytes: int, precision: str = "fp32_kahan",
+                 stream=None, workspace=None):
+        lib = nat.load()
+        nbytes = lib.vegas_batch_workspace_bytes(int(max_slots), ctypes.c_size_t(int(pool_bytes)))
+        if nbytes == 0:
+            raise nat.VegasError(nat.VEGAS_EINVAL, "vegas_batch_workspace_bytes")
+        if workspace is None:
+            workspace = torch.empty(int(nbytes), dtype=torch.uint8, device="cuda")
+        self.workspace = workspace
+        self.precision = precision
+        # default: the library's own stream (graphs cannot use the legacy stream)
+        self.stream = stream
+        sp = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+        torch.cuda.synchronize()  # the workspace allocation is complete
+        h = ctypes.c_void_p()
+        check(lib.vegas_batch_create(int(max_slots), nat.PRECISIONS[precision], sp,
+                                     ctypes.c_void_p(workspace.data_ptr()),
+                                     ctypes.c_size_t(workspace.numel()), ctypes.byref(h)),
+              "vegas_batch_create")
+        self.handle = h
+        self.max_slots = int(max_slots)
+        self._buf = (nat.VegasBatchResult * self.max_slots)()
+        self.cfgs = {}
+
+    @staticmethod
+    def slot_bytes(cfg: Config) -> int:
+        c = cfg.to_c()
+        return int(nat.load().vegas_batch_slot_bytes(ctypes.byref(c)))
+
+    def add(self, cfg: Config, family: str, params=()) -> int:
+        """Admit an integral; raises VegasError with status EBUSY / ENOMEM when full."""
+        c = cfg.to_c()
+        p = np.ascontiguousarray(np.asarray(params, dtype=np.float64))
+        itg = nat.VegasIntegrand(nat.FAMILIES[family], int(cfg.n_dim),
+                                 p.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if p.size else None,
+                                 int(p.size))
+        slot = ctypes.c_int32()
+        check(nat.load().vegas_batch_add(self.handle, ctypes.byref(c), ctypes.byref(itg),
+                                         ctypes.byref(slot)), "vegas_batch_add")
+        self.cfgs[int(slot.value)] = cfg
+        return int(slot.value)
+
+    def remove(self, slot: int) -> None:
+        check(nat.load().vegas_batch_remove(self.handle, int(slot)), "vegas_batch_remove")
+        self.cfgs.pop(int(slot), None)
+
+    def step(self) -> None:
+        check(nat.load().vegas_batch_step(self.handle), "vegas_batch_step")
+
+    def wait(self):
+        """Results of the last step: {slot: dict(t, I_t, sigma_t, n, n_nonfinite, I, sigma, chi2_dof, n_iter)}."""
+        cnt = ctypes.c_int32()
+        check(nat.load().vegas_batch_wait(self.handle, self._buf, self.max_slots, ctypes.byref(cnt)),
+              "vegas_batch_wait")
+        out = {}
+        for k in range(cnt.value):
+            r = self._buf[k]
+            out[int(r.slot)] = {"t": r.t, "I_t": r.it.I, "sigma_t": r.it.sigma, "n": r.it.n,
+                                "n_nonfinite": r.it.n_nonfinite, "I": r.comb.I,
+                                "sigma": r.comb.sigma, "chi2_dof": r.comb.chi2_dof,
+                                "n_iter": r.comb.n_iter}
+        return out
+
+    def grid(self, slot: int) -> np.ndarray:
+        cfg = self.cfgs[int(slot)]
+        e = np.zeros((cfg.n_dim, cfg.n_bins + 1), dtype=np.float64)
+        check(nat.load().vegas_batch_get_grid(self.handle, int(slot),
+                                              e.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+              "vegas_batch_get_grid")
+        return e
+
+    def set_tile(self, tile_samples: int) -> None:
+        check(nat.load().vegas_batch_set_tile(self.handle, int(tile_samples)), "vegas_batch_set_tile")
+
+    def autotune(self, candidates, reps: int = 3):
+        """Time the sampling kernel per candidate tile size; keep the fastest."""
+        cand = (ctypes.c_int32 * len(candidates))(*[int(c) for c in candidates])
+        ms = (ctypes.c_float * len(candidates))()
+        best = ctypes.c_int32()
+        check(nat.load().vegas_batch_autotune(self.handle, cand, len(candidates), int(reps), ms,
+                                              ctypes.byref(best)), "vegas_batch_autotune")
+        return int(best.value), [float(x) for x in ms]
+
+    def info(self):
+        n = ctypes.c_int32()
+        free = ctypes.c_size_t()
+        largest = ctypes.c_size_t()
+        tile = ctypes.c_int32()
+        check(nat.load().vegas_batch_info(self.handle, ctypes.byref(n), ctypes.byref(free),
+                                          ctypes.byref(largest), ctypes.byref(tile)),
+              "vegas_batch_info")
+        return {"n_active": n.value, "pool_free": free.value, "pool_largest": largest.value,
+                "tile_samples": tile.value}
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            nat.load().vegas_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -314,3 +314,18 @@ def test_full_size_lo_iteration():
     Io = acc["S1"] / n
     assert abs(I - Io) <= 1e-4 * abs(Io)
     assert np.max(np.abs(h - acc["hist"])) <= 1e-4 * acc["hist"].sum()
+
+
+@pytest.mark.parametrize("prec", ["fp32_acc64", "fp32_kahan"])
+def test_fp32_tiny_integral_corner_d16(prec):
+    """Genz corner peak in d = 16 has an integral near 1e-20 while f reaches 1:
+    the FP32 paths rescale v by powers of two each iteration so that v^2 stays
+    in FP32's normal range.  The result must agree with the closed form."""
+    V = native()
+    d, N, n = 16, 50, 1_000_000
+    p = params_for("genz_corner", d, seed=5)
+    ctx, _ = _make(V, "genz_corner", d, N, n, prec, params=p)
+    r = V.vegas_run(ctx, 8)
+    exact = CF.genz_corner_laplace(p)
+    assert abs(r["I"] - exact) < 4 * r["sigma"], (r["I"], exact, r["sigma"])
+    assert r["sigma"] < 0.05 * exact
