@@ -178,6 +178,10 @@ vegas_status vegas_set_grid(vegas_ctx *ctx, const double *edges_host);
  * [S1, S2, h_0[0..N-1], ..., h_{d-1}[0..N-1]].  Synchronises the stream. */
 vegas_status vegas_get_sums(vegas_ctx *ctx, double *sums_host);
 
+/* Samples per iteration from the next vegas_iterate on (>= 2).  The sample
+ * indices of an iteration are always 0..n_events-1. */
+vegas_status vegas_set_events(vegas_ctx *ctx, int64_t n_events);
+
 /* Iteration counter t (the Philox counter word 2 of the next iteration). */
 vegas_status vegas_get_iteration(vegas_ctx *ctx, int32_t *t);
 vegas_status vegas_set_iteration(vegas_ctx *ctx, int32_t t);
@@ -290,6 +294,8 @@ vegas_status vegas_batch_step(vegas_batch *b);
  * largest sample count first); *count = number written. */
 vegas_status vegas_batch_wait(vegas_batch *b, vegas_batch_result *out, int32_t cap, int32_t *count);
 vegas_status vegas_batch_get_grid(vegas_batch *b, int32_t slot, double *edges_host);
+/* Samples per iteration of a slot from the next step on (>= 2).  Synchronises. */
+vegas_status vegas_batch_set_events(vegas_batch *b, int32_t slot, int64_t n_events);
 /* Samples per tile (multiple of 512): the unit blocks claim.  Autotune times
  * the sampling kernel for each candidate on the current slots (results are
  * discarded, slot state is unchanged), keeps the fastest and writes the

@@ -74,6 +74,7 @@ _SIGS = {
     "vegas_get_grid": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
     "vegas_set_grid": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
     "vegas_get_sums": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
+    "vegas_set_events": (ctypes.c_int, [_P, ctypes.c_int64]),
     "vegas_get_iteration": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),
     "vegas_set_iteration": (ctypes.c_int, [_P, ctypes.c_int32]),
     "vegas_trace": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, _P, _P, _P]),
@@ -97,6 +98,7 @@ _SIGS = {
     "vegas_batch_wait": (ctypes.c_int, [_P, ctypes.POINTER(VegasBatchResult), ctypes.c_int32,
                                         ctypes.POINTER(ctypes.c_int32)]),
     "vegas_batch_get_grid": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
+    "vegas_batch_set_events": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int64]),
     "vegas_batch_set_tile": (ctypes.c_int, [_P, ctypes.c_int32]),
     "vegas_batch_autotune": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
                                             ctypes.c_int32, ctypes.POINTER(ctypes.c_float),

@@ -503,6 +503,12 @@ vegas_status vegas_get_sums(vegas_ctx *c, double *sums_host) {
     return VEGAS_OK;
 }
 
+vegas_status vegas_set_events(vegas_ctx *c, int64_t n_events) {
+    if (!c || n_events < 2) return VEGAS_EINVAL;
+    c->cfg.n_events = n_events;
+    return VEGAS_OK;
+}
+
 vegas_status vegas_get_iteration(vegas_ctx *c, int32_t *t) {
     if (!c || !t) return VEGAS_EINVAL;
     *t = c->t;

@@ -688,6 +688,19 @@ vegas_status vegas_batch_get_grid(vegas_batch *b, int32_t slot, double *edges_ho
     return VEGAS_OK;
 }
 
+vegas_status vegas_batch_set_events(vegas_batch *b, int32_t slot, int64_t n_events) {
+    if (!b || slot < 0 || slot >= b->max_slots || !b->slots[slot].used || n_events < 2) return VEGAS_EINVAL;
+    if (n_events == b->slots[slot].n) return VEGAS_OK;
+    vegas_status st = batch_sync(b);
+    if (st != VEGAS_OK) return st;
+    SlotDev *dsd = reinterpret_cast<SlotDev *>(b->ws + b->L.slots) + slot;
+    // the host value must outlive the asynchronous copy: keep it in the slot
+    b->slots[slot].n = n_events;
+    VB_CK(cudaMemcpyAsync(&dsd->n, &b->slots[slot].n, sizeof(long long), cudaMemcpyHostToDevice, b->stream));
+    VB_CK(cudaStreamSynchronize(b->stream));
+    return VEGAS_OK;
+}
+
 vegas_status vegas_batch_set_tile(vegas_batch *b, int32_t tile_samples) {
     if (!b || tile_samples < 512 || tile_samples > (1 << 26) || tile_samples % 512) return VEGAS_EINVAL;
     b->tile_samples = tile_samples;

@@ -1,0 +1,235 @@
+"""Continuous-batching server of VEGAS integrations over the batched C ABI.
+
+Requests (integrand family, dimension, parameters, relative-error target,
+sample budget) arrive over time.  Every loop turn the server
+
+  1. admits arrived requests while a slot and pool memory are free
+     (``vegas_batch_add`` refuses with EBUSY / ENOMEM otherwise; refused
+     requests wait in arrival order),
+  2. runs one batched step -- one VEGAS iteration of every admitted
+     integral in one graph launch -- so new work overlaps the old on the GPU,
+  3. retires every integral whose combined estimate reached its target
+     (sigma / |I| <= target after at least ``min_iters`` iterations) or whose
+     budget is spent, and records its latency (arrival to retirement).
+
+Samples per iteration: ``n_first`` for the first ``warm_iters`` iterations
+(grid adaptation), then what the target needs from the current estimate,
+n = total_needed / remaining_iterations, rounded up to a power of two and
+kept within [n_first, n_max] and the budget.
+
+The paper's own distribution of one integration over devices (Sec. 3.1,
+3.2) is not a server; this module is the serving form of the method.
+"""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import vegas as V
+from ._native import VEGAS_EBUSY, VEGAS_ENOMEM, VegasError
+
+
+@dataclass
+class Request:
+    family: str
+    d: int
+    params: np.ndarray
+    target_rel: float
+    budget: int = 10 ** 9
+    arrival: float = 0.0
+    seed: int = 0
+    integral_id: int = 0
+    n_bins: int = 50
+    alpha: float = 1.5
+    # filled by the server
+    admitted: float = -1.0
+    done: float = -1.0
+    result: dict = field(default_factory=dict)
+    converged: bool = False
+
+
+def _pow2_ceil(x: float) -> int:
+    return 1 << max(0, int(math.ceil(math.log2(max(1.0, x)))))
+
+
+class Server:
+    def __init__(self, max_slots: int = 1024, pool_bytes: int = 512 << 20,
+                 precision: str = "fp32_kahan", n_first: int = 1 << 17, n_max: int = 1 << 24,
+                 warm_iters: int = 2, min_iters: int = 3, iters_to_target: int = 4,
+                 adaptive: bool = True, tile_samples: int | None = None):
+        self.batch = V.Batch(max_slots=max_slots, pool_bytes=pool_bytes, precision=precision)
+        if tile_samples:
+            self.batch.set_tile(tile_samples)
+        self.precision = precision
+        self.n_first = int(n_first)
+        self.n_max = int(n_max)
+        self.warm_iters = warm_iters
+        self.min_iters = min_iters
+        self.iters_to_target = iters_to_target
+        self.adaptive = adaptive
+        self.active = {}      # slot -> [Request, samples used, n per iteration]
+        self.queue = []       # arrived, not yet admitted (arrival order)
+        self.steps = 0
+        self.samples = 0
+
+    def _admit(self, now: float) -> None:
+        while self.queue:
+            r = self.queue[0]
+            n0 = min(self.n_first, max(2, r.budget))
+            cfg = V.Config(n_dim=r.d, n_events=n0, n_bins=r.n_bins, alpha=r.alpha, seed=r.seed,
+                           integral_id=r.integral_id, precision=self.precision)
+            try:
+                slot = self.batch.add(cfg, r.family, r.params)
+            except VegasError as e:
+                if e.status in (VEGAS_EBUSY, VEGAS_ENOMEM):
+                    return  # full: wait for retirements
+                raise
+            r.admitted = now
+            self.active[slot] = [r, 0, n0]
+            self.queue.pop(0)
+
+    def _next_n(self, r: Request, used: int, res: dict) -> int:
+        """Samples for the next iteration of one integral."""
+        m = res["n_iter"]
+        left = r.budget - used
+        if not self.adaptive or m < self.warm_iters or res["sigma"] <= 0 or res["I"] == 0:
+            return max(2, min(self.n_first, left))
+        rel = res["sigma"] / abs(res["I"])
+        need_total = used * (rel / r.target_rel) ** 2
+        more = max(0.0, need_total - used)
+        n = _pow2_ceil(more / self.iters_to_target)
+        return int(max(2, min(max(self.n_first, n), self.n_max, left)))
+
+    def step(self, now_fn) -> list:
+        """One batched iteration of all active integrals; returns retired requests."""
+        if not self.active:
+            return []
+        self.batch.step()
+        res = self.batch.wait()
+        self.steps += 1
+        now = now_fn()
+        retired = []
+        for slot, rec in list(self.active.items()):
+            r, used, n = rec
+            out = res[slot]
+            used += out["n"] + out["n_nonfinite"]
+            self.samples += n
+            rec[1] = used
+            conv = (out["n_iter"] >= self.min_iters and out["sigma"] <= r.target_rel * abs(out["I"])
+                    and out["I"] != 0)
+            if conv or used >= r.budget:
+                r.done = now
+                r.converged = bool(conv)
+                r.result = dict(out)
+                r.result["samples"] = used
+                self.batch.remove(slot)
+                del self.active[slot]
+                retired.append(r)
+                continue
+            nn = self._next_n(r, used, out)
+            if nn != n:
+                self.batch.set_events(slot, nn)
+                rec[2] = nn
+        return retired
+
+    def run(self, requests, time_limit: float = 60.0, realtime: bool = True):
+        """Serve ``requests`` (sorted by arrival time, seconds from start).
+
+        With ``realtime`` the arrivals follow the wall clock; otherwise every
+        request is queued at start.  Returns summary statistics.
+        """
+        pending = sorted(requests, key=lambda q: q.arrival)
+        t0 = time.perf_counter()
+        clock = (lambda: time.perf_counter() - t0)
+        done = []
+        i = 0
+        while True:
+            now = clock()
+            while i < len(pending) and (not realtime or pending[i].arrival <= now):
+                self.queue.append(pending[i])
+                i += 1
+            self._admit(now)
+            if not self.active:
+                if i >= len(pending) and not self.queue:
+                    break
+                if realtime and i < len(pending):
+                    time.sleep(max(0.0, min(0.01, pending[i].arrival - clock())))
+                continue
+            done.extend(self.step(clock))
+            if clock() > time_limit:
+                break
+        wall = clock()
+        return summarize(done, wall, self.steps, self.samples, len(requests))
+
+
+def summarize(done, wall: float, steps: int, samples: int, n_requests: int) -> dict:
+    lat = np.array([r.done - r.arrival for r in done]) if done else np.zeros(0)
+    conv = sum(1 for r in done if r.converged)
+    return {
+        "requests": n_requests, "completed": len(done), "converged": conv,
+        "wall_s": wall, "integrals_per_s": len(done) / wall if wall > 0 else 0.0,
+        "p50_ms": float(np.percentile(lat, 50) * 1e3) if lat.size else None,
+        "p99_ms": float(np.percentile(lat, 99) * 1e3) if lat.size else None,
+        "steps": steps, "samples": samples,
+        "samples_per_s": samples / wall if wall > 0 else 0.0,
+    }
+
+
+def serve_single_fp64(requests, n_first: int = 1 << 17, n_max: int = 1 << 24, warm_iters: int = 2,
+                      min_iters: int = 3, iters_to_target: int = 4, time_limit: float = 60.0):
+    """The plain FP64 single-integral form: one context per request, one at a
+    time, the same sample schedule and stopping rule as the server."""
+    t0 = time.perf_counter()
+    done = []
+    samples = 0
+    steps = 0
+    helper = Server.__new__(Server)
+    helper.n_first, helper.n_max = n_first, n_max
+    helper.warm_iters, helper.iters_to_target, helper.adaptive = warm_iters, iters_to_target, True
+    for r in sorted(requests, key=lambda q: q.arrival):
+        now = time.perf_counter() - t0
+        if now < r.arrival:
+            time.sleep(r.arrival - now)
+        n = min(n_first, max(2, r.budget))
+        cfg = V.Config(n_dim=r.d, n_events=n, n_bins=r.n_bins, alpha=r.alpha, seed=r.seed,
+                       integral_id=r.integral_id, precision="fp64")
+        ctx = V.vegas_create(cfg, r.family, r.params)
+        used = 0
+        while True:
+            I_t, s_t, n_ok, n_nf = V.vegas_iterate(ctx)
+            steps += 1
+            samples += n
+            used += n
+            res = V.vegas_result(ctx)
+            conv = res["n_iter"] >= min_iters and res["sigma"] <= r.target_rel * abs(res["I"]) and res["I"] != 0
+            if conv or used >= r.budget:
+                r.converged = bool(conv)
+                r.result = dict(res)
+                r.result["samples"] = used
+                break
+            V.vegas_refine(ctx)
+            nn = helper._next_n(r, used, res)
+            if nn != n:
+                V.vegas_set_events(ctx, nn)
+                n = nn
+        V.vegas_destroy(ctx)
+        r.done = time.perf_counter() - t0
+        done.append(r)
+        if r.done > time_limit:
+            break
+    return summarize(done, time.perf_counter() - t0, steps, samples, len(requests))
+
+
+def requests_from(integrals, budget: int | None = None, target: float | None = None):
+    """Requests from workload ``Integral`` records (see workloads.request_stream)."""
+    out = []
+    for it in integrals:
+        out.append(Request(family=it.family, d=it.d, params=np.asarray(it.params, dtype=np.float64),
+                           target_rel=target if target is not None else it.target_rel,
+                           budget=budget if budget is not None else (it.budget or 10 ** 9),
+                           arrival=it.arrival, seed=it.seed, integral_id=it.integral_id,
+                           n_bins=it.n_bins, alpha=it.alpha))
+    return out

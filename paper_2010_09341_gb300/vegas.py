@@ -144,6 +144,11 @@ def vegas_get_sums(ctx: Context):
     return s[0], s[1], s[2:].reshape(d, N)
 
 
+def vegas_set_events(ctx: Context, n_events: int) -> None:
+    check(nat.load().vegas_set_events(ctx.handle, int(n_events)), "vegas_set_events")
+    ctx.cfg.n_events = int(n_events)
+
+
 def vegas_get_iteration(ctx: Context) -> int:
     t = ctypes.c_int32()
     check(nat.load().vegas_get_iteration(ctx.handle, ctypes.byref(t)), "vegas_get_iteration")
@@ -343,6 +348,11 @@ class Batch:
                                               e.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
               "vegas_batch_get_grid")
         return e
+
+    def set_events(self, slot: int, n_events: int) -> None:
+        check(nat.load().vegas_batch_set_events(self.handle, int(slot), int(n_events)),
+              "vegas_batch_set_events")
+        self.cfgs[int(slot)].n_events = int(n_events)
 
     def set_tile(self, tile_samples: int) -> None:
         check(nat.load().vegas_batch_set_tile(self.handle, int(tile_samples)), "vegas_batch_set_tile")
