@@ -222,6 +222,104 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------ other workloads
+def _time_single(V, torch, family, params, d, N, n, prec, iters, warm=2, iid=0):
+    """samples/s of `iters` iterations (sample + finalize + refine) of one
+    integral, after `warm` untimed ones; device time with CUDA events."""
+    cfg = V.Config(n_dim=d, n_events=n, n_bins=N, alpha=ALPHA, seed=0, integral_id=iid,
+                   precision=prec)
+    ctx = V.vegas_create(cfg, family, params)
+    for _ in range(warm):
+        V.vegas_iterate(ctx, sync=False)
+        V.vegas_refine(ctx)
+    V.vegas_profile(ctx, True)
+    s = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(s)
+    for _ in range(iters):
+        V.vegas_iterate(ctx, sync=False)
+        V.vegas_refine(ctx)
+    b.record(s)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    kms = V.vegas_profile_read(ctx)
+    res = V.vegas_result(ctx)
+    V.vegas_destroy(ctx)
+    return {"samples_per_s": n * iters / (ms / 1e3), "ms_per_iter": ms / iters,
+            "kernel_ms": sum(kms) / max(1, len(kms)), "I": res["I"], "sigma": res["sigma"]}
+
+
+def _time_batched(V, torch, steps=8, warm=2):
+    """The uneven 512-integral mix: one step = one iteration of every integral."""
+    from paper_2010_09341_gb300 import workloads as W
+    mix = W.batch_mix(512, seed=2)
+    b = V.Batch(max_slots=512, pool_bytes=256 << 20, precision="fp32_kahan")
+    for it in mix:
+        b.add(V.Config(n_dim=it.d, n_events=it.n_events, n_bins=it.n_bins, alpha=ALPHA, seed=0,
+                       integral_id=it.integral_id, precision="fp32_kahan"), it.family, it.params)
+    for _ in range(warm):
+        b.step()
+        b.wait()
+    best, ms = b.autotune([4096, 8192, 16384, 32768, 65536], reps=2)
+    b.step()
+    b.wait()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        b.step()
+        b.wait()
+    dt = time.perf_counter() - t0
+    n_total = sum(it.n_events for it in mix)
+    b.close()
+    return {"workload": "512 integrals, d ~ U{2..16}, Genz gauss/prod/corner, c ~ U(0.5,5), "
+                        "n ~ logU(1e4,1e7) per iteration, 50 bins, FP32 Kahan, seed 2",
+            "samples_per_step": n_total, "steps": steps, "ms_per_step": 1e3 * dt / steps,
+            "samples_per_s": n_total * steps / dt,
+            "integral_iterations_per_s": 512 * steps / dt,
+            "tile_samples": best, "autotune_ms": dict(zip(["4096", "8192", "16384", "32768", "65536"], ms)),
+            "timing": "wall clock per step incl. graph launch and result download"}
+
+
+def _serving(V, rate, n_requests, target, budget, fp64_sample=0):
+    from paper_2010_09341_gb300 import serve as S
+    from paper_2010_09341_gb300 import workloads as W
+    stream = W.request_stream(rate=rate, n_requests=n_requests, seed=3)
+    reqs = S.requests_from(stream, budget=budget, target=target)
+    srv = S.Server(max_slots=1024, pool_bytes=512 << 20)
+    st = srv.run(reqs, realtime=True, time_limit=120)
+    srv.batch.close()
+    out = {"rate_per_s": rate, "target_rel": target, "budget": budget, **st}
+    if fp64_sample:
+        sub = S.requests_from(stream[:fp64_sample], budget=budget, target=target)
+        for r in sub:
+            r.arrival = 0.0
+        st64 = S.serve_single_fp64(sub, time_limit=120)
+        out["fp64_single"] = {"requests": fp64_sample, **st64}
+        out["batched_fp32_vs_fp64_single_integrals_per_s"] = (
+            st["integrals_per_s"] / st64["integrals_per_s"] if st64["integrals_per_s"] else None)
+    return out
+
+
+def _traffic_from_profile():
+    """DRAM bytes per sampling-kernel launch from the committed ncu summary,
+    if the kernel sources still hash to what was profiled; else None."""
+    import hashlib
+    import re
+    prof = os.path.join(ROOT, "profiles", "sample_kernel_d8_gauss.md")
+    src = os.path.join(ROOT, "paper_2010_09341_gb300", "csrc")
+    try:
+        txt = open(prof).read()
+        h = hashlib.sha256()
+        for f in ("vegas_device.cuh", "vegas_sample.cuh"):
+            h.update(open(os.path.join(src, f), "rb").read())
+        want = re.search(r"kernel_source_sha256:\s*([0-9a-f]{64})", txt).group(1)
+        if want != h.hexdigest():
+            return None
+        return float(re.search(r"traffic_bytes_per_launch:\s*([0-9.]+)", txt).group(1))
+    except (OSError, AttributeError):
+        return None
+
+
 # ----------------------------------------------------------------- GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -233,6 +331,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the other workloads")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -328,7 +427,7 @@ def main():
     achieved_gops = ach_ops / (kern_total_ms / 1e3) / 1e9
     peak_gops = ach_ops / roof_s / 1e9
     roofline = {"bound": "alu", "achieved": achieved_gops, "peak": peak_gops, "unit": "Gop/s",
-                "frac": achieved_gops / peak_gops, "traffic": None,
+                "frac": achieved_gops / peak_gops, "traffic": _traffic_from_profile(),
                 "kernel": "vegas_sample_kernel", "peak_basis":
                 "min over pipes (issue 128/clk/SM, 32x32->64 multiply 32/clk/SM, FP64 %.2f TFLOP/s, MUFU 16/clk/SM) at %d SMs x %.0f MHz (max clock)"
                 % (FP64_TFLOPS_NOMINAL, sms, clk_max_hz / 1e6), "per_integral": per_fam}
@@ -359,6 +458,24 @@ def main():
                "steps": args.e2e_steps,
                "path": "per integral: vegas_set_grid(host) + vegas_iterate(result to host) + vegas_refine + vegas_get_grid(host)"}
 
+    # ---- the other workloads (rank 0 only)
+    extra = None
+    if rank == 0 and not args.no_extra:
+        from paper_2010_09341_gb300 import workloads as W
+        extra = {}
+        extra["config1_fp64_d4_gauss"] = _time_single(
+            V, torch, "gauss_sym", W.gauss_sym_params(0.1), 4, 50, 100_000, "fp64", 5)
+        for fam, p in _integrals():
+            extra["config2_fp64_path_" + fam] = _time_single(V, torch, fam, p, D, NBINS, NEVENTS,
+                                                             "fp64", 3)
+            extra["config2_fp32_kahan_" + fam] = _time_single(V, torch, fam, p, D, NBINS, NEVENTS,
+                                                              "fp32_kahan", 10)
+        extra["config3_lo_fp32_kahan"] = _time_single(V, torch, "lo", W.lo_params(), 3, 100,
+                                                      100_000_000, "fp32_kahan", 10)
+        extra["config4_batched"] = _time_batched(V, torch)
+        extra["config5_serving_1e-4"] = _serving(V, rate=1000.0, n_requests=1000, target=1e-4,
+                                                 budget=10 ** 9, fp64_sample=40)
+
     # ---- CPU baseline: the oracle on this host's cores (rank 0, N = 1)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -379,7 +496,7 @@ def main():
                        "step": "one iteration (sample + finalize + refine) of both integrals",
                        "l2": "flushed between steps (256 MiB write outside the step events); the kernel reads no HBM inputs",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "extra": extra,
             "gpu_launches": args.steps * 3 * len(ctxs),
             "clocks": clk,
         }
