@@ -157,6 +157,27 @@ vegas_status vegas_create(const vegas_config *cfg, const vegas_integrand *integr
  * fills *out.  ENONFINITE (with *out filled) if no sample had a finite weight. */
 vegas_status vegas_iterate(vegas_ctx *ctx, vegas_iter_result *out);
 
+/* Sharded iteration: one integral's samples split over several devices or
+ * processes (the paper's multi-device use of one integration, Sec. 3.1 and
+ * Sec. 3.2: each iteration's partial results are combined before the grid is
+ * refined).  Every shard holds a context with the same configuration and
+ * grid; per iteration:
+ *   vegas_sample_shard(ctx, s_begin, count)  samples its range of the
+ *       iteration's n_events samples into the context's accumulators;
+ *   the caller sums the accumulators of all shards in place on every shard
+ *       (vegas_accumulators gives them: 2 + d*N FP64 values in the
+ *       context's current scale, identical on every shard, plus one
+ *       64-bit non-finite count), e.g. with an all-reduce;
+ *   vegas_finalize(ctx, out) forms the iteration result for all n_events
+ *       samples and advances the iteration (as vegas_iterate does after its
+ *       sampling); then vegas_refine gives every shard the same grid.
+ * Sample indices are global, so the union of the shards is exactly the
+ * single-context iteration.  Asynchronous unless out != NULL. */
+vegas_status vegas_sample_shard(vegas_ctx *ctx, int64_t s_begin, int64_t count);
+vegas_status vegas_accumulators(vegas_ctx *ctx, double **dev_sums, int64_t *n_sums,
+                                unsigned long long **dev_nonfinite);
+vegas_status vegas_finalize(vegas_ctx *ctx, vegas_iter_result *out);
+
 /* Refine the grid from the last iteration's histograms (asynchronous). */
 vegas_status vegas_refine(vegas_ctx *ctx);
 

@@ -67,6 +67,10 @@ _SIGS = {
     "vegas_create": (ctypes.c_int, [ctypes.POINTER(VegasConfig), ctypes.POINTER(VegasIntegrand),
                                     _P, _P, ctypes.c_size_t, ctypes.POINTER(_P)]),
     "vegas_iterate": (ctypes.c_int, [_P, ctypes.POINTER(VegasIterResult)]),
+    "vegas_sample_shard": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int64]),
+    "vegas_accumulators": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_int64),
+                                          ctypes.POINTER(_P)]),
+    "vegas_finalize": (ctypes.c_int, [_P, ctypes.POINTER(VegasIterResult)]),
     "vegas_refine": (ctypes.c_int, [_P]),
     "vegas_result": (ctypes.c_int, [_P, ctypes.POINTER(VegasResult)]),
     "vegas_run": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(VegasIterResult),

@@ -384,11 +384,10 @@ static vegas_status launch_sampling(vegas_ctx *c, long long s_begin, long long n
     return VEGAS_OK;
 }
 
-vegas_status vegas_iterate(vegas_ctx *c, vegas_iter_result *out) {
-    if (!c) return VEGAS_EINVAL;
-    if (c->n_done >= VEGAS_MAX_ITERS) return VEGAS_EINVAL;
-    const long long n = c->cfg.n_events;
-    const long long lim = c->cfg.events_limit > 0 ? c->cfg.events_limit : n;
+// Sampling of samples [s_begin, s_begin + count) of the next iteration into
+// the accumulators (split into launches of at most events_limit samples).
+static vegas_status sample_samples(vegas_ctx *c, long long s_begin, long long count) {
+    const long long lim = c->cfg.events_limit > 0 ? c->cfg.events_limit : count;
     std::pair<cudaEvent_t, cudaEvent_t> *pe = nullptr;
     if (c->profiling) {
         if (c->ev_used == c->ev.size()) {
@@ -400,11 +399,18 @@ vegas_status vegas_iterate(vegas_ctx *c, vegas_iter_result *out) {
         pe = &c->ev[c->ev_used++];
         VEGAS_CK(cudaEventRecord(pe->first, c->stream));
     }
-    for (long long s0 = 0; s0 < n; s0 += lim) {
-        const vegas_status st = launch_sampling(c, s0, std::min(lim, n - s0));
+    for (long long s0 = 0; s0 < count; s0 += lim) {
+        const vegas_status st = launch_sampling(c, s_begin + s0, std::min(lim, count - s0));
         if (st != VEGAS_OK) return st;
     }
     if (pe) VEGAS_CK(cudaEventRecord(pe->second, c->stream));
+    return VEGAS_OK;
+}
+
+// Iteration result from the accumulators (n_events samples in all) and the
+// step to the next iteration.
+static vegas_status finalize_iteration(vegas_ctx *c, vegas_iter_result *out) {
+    const long long n = c->cfg.n_events;
     VEGAS_CK(launch_finalize(c->acc, c->last, c->nonfinite, c->hscale, c->jmul, c->iters, c->comb,
                              c->n_done, n, c->cfg.n_dim, c->cfg.n_bins, 1.0 / c->scale, c->jinit,
                              c->stream));
@@ -420,6 +426,36 @@ vegas_status vegas_iterate(vegas_ctx *c, vegas_iter_result *out) {
     out->n = r.n;
     out->n_nonfinite = r.n_nonfinite;
     return r.n <= 0 ? VEGAS_ENONFINITE : VEGAS_OK;
+}
+
+vegas_status vegas_iterate(vegas_ctx *c, vegas_iter_result *out) {
+    if (!c) return VEGAS_EINVAL;
+    if (c->n_done >= VEGAS_MAX_ITERS) return VEGAS_EINVAL;
+    const vegas_status st = sample_samples(c, 0, c->cfg.n_events);
+    if (st != VEGAS_OK) return st;
+    return finalize_iteration(c, out);
+}
+
+vegas_status vegas_sample_shard(vegas_ctx *c, int64_t s_begin, int64_t count) {
+    if (!c || s_begin < 0 || count < 0 || s_begin + count > c->cfg.n_events) return VEGAS_EINVAL;
+    if (c->n_done >= VEGAS_MAX_ITERS) return VEGAS_EINVAL;
+    if (count == 0) return VEGAS_OK;
+    return sample_samples(c, s_begin, count);
+}
+
+vegas_status vegas_accumulators(vegas_ctx *c, double **dev_sums, int64_t *n_sums,
+                                unsigned long long **dev_nonfinite) {
+    if (!c) return VEGAS_EINVAL;
+    if (dev_sums) *dev_sums = c->acc;
+    if (n_sums) *n_sums = 2 + static_cast<int64_t>(c->cfg.n_dim) * c->cfg.n_bins;
+    if (dev_nonfinite) *dev_nonfinite = c->nonfinite;
+    return VEGAS_OK;
+}
+
+vegas_status vegas_finalize(vegas_ctx *c, vegas_iter_result *out) {
+    if (!c) return VEGAS_EINVAL;
+    if (c->n_done >= VEGAS_MAX_ITERS) return VEGAS_EINVAL;
+    return finalize_iteration(c, out);
 }
 
 vegas_status vegas_refine(vegas_ctx *c) {

@@ -102,6 +102,38 @@ def vegas_iterate(ctx: Context, sync: bool = True):
     return r.I, r.sigma, r.n, r.n_nonfinite
 
 
+def vegas_sample_shard(ctx: Context, s_begin: int, count: int) -> None:
+    check(nat.load().vegas_sample_shard(ctx.handle, int(s_begin), int(count)), "vegas_sample_shard")
+
+
+def vegas_accumulators(ctx: Context):
+    """(sums, nonfinite): CUDA tensor views of the context's FP64 accumulators
+    (2 + d*N values) and its int64 non-finite count, inside the workspace."""
+    sp = ctypes.c_void_p()
+    cnt = ctypes.c_int64()
+    nfp = ctypes.c_void_p()
+    check(nat.load().vegas_accumulators(ctx.handle, ctypes.byref(sp), ctypes.byref(cnt),
+                                        ctypes.byref(nfp)), "vegas_accumulators")
+    base = ctx.workspace.data_ptr()
+    off = sp.value - base
+    sums = ctx.workspace[off: off + 8 * cnt.value].view(torch.float64)
+    off2 = nfp.value - base
+    nonfinite = ctx.workspace[off2: off2 + 8].view(torch.int64)
+    return sums, nonfinite
+
+
+def vegas_finalize(ctx: Context, sync: bool = True):
+    lib = nat.load()
+    if not sync:
+        check(lib.vegas_finalize(ctx.handle, None), "vegas_finalize")
+        return None
+    r = nat.VegasIterResult()
+    st = lib.vegas_finalize(ctx.handle, ctypes.byref(r))
+    if st not in (nat.VEGAS_OK, nat.VEGAS_ENONFINITE):
+        check(st, "vegas_finalize")
+    return r.I, r.sigma, r.n, r.n_nonfinite
+
+
 def vegas_refine(ctx: Context):
     check(nat.load().vegas_refine(ctx.handle), "vegas_refine")
 

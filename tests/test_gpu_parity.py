@@ -329,3 +329,35 @@ def test_fp32_tiny_integral_corner_d16(prec):
     exact = CF.genz_corner_laplace(p)
     assert abs(r["I"] - exact) < 4 * r["sigma"], (r["I"], exact, r["sigma"])
     assert r["sigma"] < 0.05 * exact
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_kahan"])
+def test_two_shards_equal_one_context(prec):
+    """Two contexts on one GPU take the two halves of every iteration; their
+    accumulators are summed (as an all-reduce would) and both finalize and
+    refine: the results equal a single context's, and the shards' grids stay
+    identical."""
+    V = native()
+    import torch
+    d, N, n = 6, 40, 300_001
+    p = params_for("genz_prod", d)
+    ref, _ = _make(V, "genz_prod", d, N, n, prec, params=p)
+    sh = [_make(V, "genz_prod", d, N, n, prec, params=p)[0] for _ in range(2)]
+    tol = TOL[prec]
+    for t in range(3):
+        Ir = V.vegas_iterate(ref)[0]
+        half = n // 2
+        V.vegas_sample_shard(sh[0], 0, half)
+        V.vegas_sample_shard(sh[1], half, n - half)
+        (a, na), (b, nb) = V.vegas_accumulators(sh[0]), V.vegas_accumulators(sh[1])
+        tot, ntot = a + b, na + nb
+        for s_, n_ in ((a, na), (b, nb)):
+            s_.copy_(tot)
+            n_.copy_(ntot)
+        I0 = V.vegas_finalize(sh[0])[0]
+        I1 = V.vegas_finalize(sh[1])[0]
+        assert I0 == I1
+        assert abs(I0 - Ir) <= tol * abs(Ir)
+        for c in (ref, sh[0], sh[1]):
+            V.vegas_refine(c)
+        assert np.array_equal(V.vegas_get_grid(sh[0]), V.vegas_get_grid(sh[1]))
