@@ -353,3 +353,17 @@ def test_brute_force_d2(family):
     assert abs(q - exact) < 1e-9 * abs(exact)
     r = O.integrate(2, 50, family, p, 50000, 5)
     _check(r, q)
+
+
+def test_oracle_reproduces_golden_fixture_bitwise():
+    """tests/golden/config1_oracle.json was written by tests/golden/make_golden.py
+    (oracle only); the oracle must reproduce it exactly on this machine."""
+    import hashlib
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "config1_oracle.json")
+    g = json.load(open(path))
+    r = O.integrate(4, 50, "gauss_sym", [0.1], 100_000, 5, alpha=1.5, seed=0)
+    assert [[float(I).hex(), float(s).hex()] for I, s in r["iters"]] == g["iters"]
+    assert float(r["I"]).hex() == g["I"] and float(r["sigma"]).hex() == g["sigma"]
+    assert hashlib.sha256(r["edges"].astype("<f8").tobytes()).hexdigest() == g["edges_sha256"]
