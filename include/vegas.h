@@ -98,7 +98,7 @@ typedef enum {
 
 #define VEGAS_MAX_DIM 32
 #define VEGAS_MAX_BINS 1024
-#define VEGAS_MAX_ITERS 4096
+#define VEGAS_MAX_ITERS 4096  /* per-iteration records kept (a ring); iterations are unbounded */
 
 typedef struct {
     int32_t family;         /* vegas_family                                   */
@@ -185,8 +185,8 @@ vegas_status vegas_refine(vegas_ctx *ctx);
 vegas_status vegas_result(vegas_ctx *ctx, vegas_result_t *out);
 
 /* run_integration of Sec. 3.1: n_iter rounds of iterate + refine (no refine
- * after the last), then vegas_result.  iters (may be NULL) receives n_iter
- * per-iteration results. */
+ * after the last), then vegas_result.  iters (may be NULL; then n_iter <=
+ * VEGAS_MAX_ITERS) receives n_iter per-iteration results. */
 vegas_status vegas_run(vegas_ctx *ctx, int32_t n_iter, vegas_iter_result *iters,
                        vegas_result_t *out);
 

@@ -36,7 +36,7 @@ constexpr size_t kAlign = 256;
 inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-    size_t edges, table, acc, last, nonfinite, hscale, jmul, iters, comb, total;
+    size_t edges, table, acc, last, nonfinite, hscale, jmul, iters, comb, cstate, total;
 };
 
 Layout layout_for(int d, int N) {
@@ -57,9 +57,11 @@ Layout layout_for(int d, int N) {
     L.jmul = off;
     off = align_up(off + sizeof(double));
     L.iters = off;
-    off = align_up(off + sizeof(IterRec) * VEGAS_MAX_ITERS);
+    off = align_up(off + sizeof(IterRec) * kIterRing);
     L.comb = off;
     off = align_up(off + sizeof(CombRec));
+    L.cstate = off;
+    off = align_up(off + sizeof(CombState));
     L.total = off;
     return L;
 }
@@ -193,6 +195,7 @@ struct vegas_ctx {
     double *jmul;
     IterRec *iters;
     CombRec *comb;
+    CombState *cstate;
     int t;          // Philox iteration word of the next iteration
     int n_done;     // iterations recorded in iters[]
     FamilyConsts fc;
@@ -305,6 +308,7 @@ vegas_status vegas_create(const vegas_config *cfg, const vegas_integrand *itg, v
     c->jmul = reinterpret_cast<double *>(c->ws + L.jmul);
     c->iters = reinterpret_cast<IterRec *>(c->ws + L.iters);
     c->comb = reinterpret_cast<CombRec *>(c->ws + L.comb);
+    c->cstate = reinterpret_cast<CombState *>(c->ws + L.cstate);
     c->t = 0;
     c->n_done = 0;
     c->fc = fc;
@@ -330,7 +334,7 @@ vegas_status vegas_create(const vegas_config *cfg, const vegas_integrand *itg, v
     if (ce == cudaSuccess) ce = cudaMemsetAsync(c->acc, 0, (L.hscale + sizeof(float)) - L.acc, c->stream);
     static const double kOne = 1.0;
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(c->jmul, &kOne, sizeof(double), cudaMemcpyHostToDevice, c->stream);
-    if (ce == cudaSuccess) ce = cudaMemsetAsync(c->comb, 0, sizeof(CombRec), c->stream);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(c->comb, 0, (L.cstate + sizeof(CombState)) - L.comb, c->stream);
     if (ce == cudaSuccess) ce = launch_table_from_edges(c->edges, c->table, mode, d, N, c->stream);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
     if (ce != cudaSuccess) {
@@ -411,15 +415,15 @@ static vegas_status sample_samples(vegas_ctx *c, long long s_begin, long long co
 // step to the next iteration.
 static vegas_status finalize_iteration(vegas_ctx *c, vegas_iter_result *out) {
     const long long n = c->cfg.n_events;
-    VEGAS_CK(launch_finalize(c->acc, c->last, c->nonfinite, c->hscale, c->jmul, c->iters, c->comb,
-                             c->n_done, n, c->cfg.n_dim, c->cfg.n_bins, 1.0 / c->scale, c->jinit,
-                             c->stream));
+    VEGAS_CK(launch_finalize(c->acc, c->last, c->nonfinite, c->hscale, c->jmul, c->iters, c->cstate,
+                             c->comb, c->n_done, n, c->cfg.n_dim, c->cfg.n_bins, 1.0 / c->scale,
+                             c->jinit, c->stream));
     const int rec = c->n_done;
     c->n_done += 1;
     c->t += 1;
     if (!out) return VEGAS_OK;
     IterRec r;
-    VEGAS_CK(cudaMemcpyAsync(&r, c->iters + rec, sizeof(r), cudaMemcpyDeviceToHost, c->stream));
+    VEGAS_CK(cudaMemcpyAsync(&r, c->iters + rec % kIterRing, sizeof(r), cudaMemcpyDeviceToHost, c->stream));
     VEGAS_CK(cudaStreamSynchronize(c->stream));
     out->I = r.I;
     out->sigma = r.sigma;
@@ -430,7 +434,6 @@ static vegas_status finalize_iteration(vegas_ctx *c, vegas_iter_result *out) {
 
 vegas_status vegas_iterate(vegas_ctx *c, vegas_iter_result *out) {
     if (!c) return VEGAS_EINVAL;
-    if (c->n_done >= VEGAS_MAX_ITERS) return VEGAS_EINVAL;
     const vegas_status st = sample_samples(c, 0, c->cfg.n_events);
     if (st != VEGAS_OK) return st;
     return finalize_iteration(c, out);
@@ -438,7 +441,6 @@ vegas_status vegas_iterate(vegas_ctx *c, vegas_iter_result *out) {
 
 vegas_status vegas_sample_shard(vegas_ctx *c, int64_t s_begin, int64_t count) {
     if (!c || s_begin < 0 || count < 0 || s_begin + count > c->cfg.n_events) return VEGAS_EINVAL;
-    if (c->n_done >= VEGAS_MAX_ITERS) return VEGAS_EINVAL;
     if (count == 0) return VEGAS_OK;
     return sample_samples(c, s_begin, count);
 }
@@ -454,7 +456,6 @@ vegas_status vegas_accumulators(vegas_ctx *c, double **dev_sums, int64_t *n_sums
 
 vegas_status vegas_finalize(vegas_ctx *c, vegas_iter_result *out) {
     if (!c) return VEGAS_EINVAL;
-    if (c->n_done >= VEGAS_MAX_ITERS) return VEGAS_EINVAL;
     return finalize_iteration(c, out);
 }
 
@@ -479,9 +480,23 @@ vegas_status vegas_result(vegas_ctx *c, vegas_result_t *out) {
     return VEGAS_OK;
 }
 
+// Copy count iteration records, starting at record index first, out of the ring.
+static vegas_status read_records(vegas_ctx *c, int first, int count, IterRec *dst) {
+    int done = 0;
+    while (done < count) {
+        const int pos = (first + done) % kIterRing;
+        const int len = std::min(count - done, kIterRing - pos);
+        VEGAS_CK(cudaMemcpyAsync(dst + done, c->iters + pos, sizeof(IterRec) * len, cudaMemcpyDeviceToHost,
+                                 c->stream));
+        done += len;
+    }
+    VEGAS_CK(cudaStreamSynchronize(c->stream));
+    return VEGAS_OK;
+}
+
 vegas_status vegas_run(vegas_ctx *c, int32_t n_iter, vegas_iter_result *iters, vegas_result_t *out) {
     if (!c || n_iter < 1 || !out) return VEGAS_EINVAL;
-    if (c->n_done + n_iter > VEGAS_MAX_ITERS) return VEGAS_EINVAL;
+    if (iters && n_iter > kIterRing) return VEGAS_EINVAL;
     const int first = c->n_done;
     for (int k = 0; k < n_iter; ++k) {
         vegas_status st = vegas_iterate(c, nullptr);
@@ -493,9 +508,8 @@ vegas_status vegas_run(vegas_ctx *c, int32_t n_iter, vegas_iter_result *iters, v
     }
     if (iters) {
         std::vector<IterRec> rs(n_iter);
-        VEGAS_CK(cudaMemcpyAsync(rs.data(), c->iters + first, sizeof(IterRec) * n_iter,
-                                 cudaMemcpyDeviceToHost, c->stream));
-        VEGAS_CK(cudaStreamSynchronize(c->stream));
+        const vegas_status st = read_records(c, first, n_iter, rs.data());
+        if (st != VEGAS_OK) return st;
         for (int k = 0; k < n_iter; ++k) {
             iters[k].I = rs[k].I;
             iters[k].sigma = rs[k].sigma;
@@ -587,8 +601,9 @@ vegas_status vegas_export_state(vegas_ctx *c, void *buf, size_t *size) {
     if (!c || !size) return VEGAS_EINVAL;
     const int d = c->cfg.n_dim, N = c->cfg.n_bins;
     const size_t ne = static_cast<size_t>(d) * (N + 1);
+    const int nrec = std::min(c->n_done, kIterRing);
     const size_t need = sizeof(BlobHeader) + sizeof(double) * c->params.size() +
-                        sizeof(double) * ne + sizeof(IterRec) * c->n_done + sizeof(CombRec);
+                        sizeof(double) * ne + sizeof(IterRec) * nrec + sizeof(CombRec) + sizeof(CombState);
     if (!buf) {
         *size = need;
         return VEGAS_OK;
@@ -601,7 +616,7 @@ vegas_status vegas_export_state(vegas_ctx *c, void *buf, size_t *size) {
     VEGAS_CK(cudaMemcpyAsync(&h.jmul, c->jmul, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     VEGAS_CK(cudaStreamSynchronize(c->stream));
     h.magic = kMagic;
-    h.version = 2;
+    h.version = 3;
     h.cfg = c->cfg;
     h.family = c->family;
     h.n_params = static_cast<int32_t>(c->params.size());
@@ -613,11 +628,14 @@ vegas_status vegas_export_state(vegas_ctx *c, void *buf, size_t *size) {
     p += sizeof(double) * c->params.size();
     VEGAS_CK(cudaMemcpyAsync(p, c->edges, sizeof(double) * ne, cudaMemcpyDeviceToHost, c->stream));
     p += sizeof(double) * ne;
-    if (c->n_done > 0)
-        VEGAS_CK(cudaMemcpyAsync(p, c->iters, sizeof(IterRec) * c->n_done, cudaMemcpyDeviceToHost,
-                                 c->stream));
-    p += sizeof(IterRec) * c->n_done;
+    if (nrec > 0) {
+        const vegas_status st = read_records(c, c->n_done - nrec, nrec, reinterpret_cast<IterRec *>(p));
+        if (st != VEGAS_OK) return st;
+    }
+    p += sizeof(IterRec) * nrec;
     VEGAS_CK(cudaMemcpyAsync(p, c->comb, sizeof(CombRec), cudaMemcpyDeviceToHost, c->stream));
+    p += sizeof(CombRec);
+    VEGAS_CK(cudaMemcpyAsync(p, c->cstate, sizeof(CombState), cudaMemcpyDeviceToHost, c->stream));
     VEGAS_CK(cudaStreamSynchronize(c->stream));
     *size = need;
     return VEGAS_OK;
@@ -629,28 +647,33 @@ vegas_status vegas_import_state(vegas_ctx *c, const void *buf, size_t size) {
     BlobHeader h;
     memcpy(&h, p, sizeof(h));
     p += sizeof(h);
-    if (h.magic != kMagic || h.version != 2) return VEGAS_EINVAL;
+    if (h.magic != kMagic || h.version != 3) return VEGAS_EINVAL;
     const vegas_config &a = h.cfg, &b = c->cfg;
     if (a.n_dim != b.n_dim || a.n_bins != b.n_bins || a.n_events != b.n_events ||
         a.seed != b.seed || a.integral_id != b.integral_id || a.precision != b.precision ||
         a.alpha != b.alpha || a.smooth != b.smooth || h.family != c->family ||
         h.n_params != static_cast<int32_t>(c->params.size()))
         return VEGAS_EINVAL;
-    if (h.n_done < 0 || h.n_done > VEGAS_MAX_ITERS || h.t < 0) return VEGAS_EINVAL;
+    if (h.n_done < 0 || h.t < 0) return VEGAS_EINVAL;
+    const int nrec = std::min(h.n_done, kIterRing);
     const int d = b.n_dim, N = b.n_bins;
     const size_t ne = static_cast<size_t>(d) * (N + 1);
     const size_t need = sizeof(BlobHeader) + sizeof(double) * h.n_params + sizeof(double) * ne +
-                        sizeof(IterRec) * h.n_done + sizeof(CombRec);
+                        sizeof(IterRec) * nrec + sizeof(CombRec) + sizeof(CombState);
     if (size < need) return VEGAS_EINVAL;
     if (memcmp(p, c->params.data(), sizeof(double) * h.n_params) != 0) return VEGAS_EINVAL;
     p += sizeof(double) * h.n_params;
     VEGAS_CK(cudaMemcpyAsync(c->edges, p, sizeof(double) * ne, cudaMemcpyHostToDevice, c->stream));
     p += sizeof(double) * ne;
-    if (h.n_done > 0)
-        VEGAS_CK(cudaMemcpyAsync(c->iters, p, sizeof(IterRec) * h.n_done, cudaMemcpyHostToDevice,
-                                 c->stream));
-    p += sizeof(IterRec) * h.n_done;
+    for (int k = 0; k < nrec; ++k) {
+        const int pos = (h.n_done - nrec + k) % kIterRing;
+        VEGAS_CK(cudaMemcpyAsync(c->iters + pos, p + sizeof(IterRec) * k, sizeof(IterRec),
+                                 cudaMemcpyHostToDevice, c->stream));
+    }
+    p += sizeof(IterRec) * nrec;
     VEGAS_CK(cudaMemcpyAsync(c->comb, p, sizeof(CombRec), cudaMemcpyHostToDevice, c->stream));
+    p += sizeof(CombRec);
+    VEGAS_CK(cudaMemcpyAsync(c->cstate, p, sizeof(CombState), cudaMemcpyHostToDevice, c->stream));
     VEGAS_CK(cudaMemcpyAsync(c->hscale, &h.hscale, sizeof(float), cudaMemcpyHostToDevice, c->stream));
     VEGAS_CK(cudaMemcpyAsync(c->jmul, &h.jmul, sizeof(double), cudaMemcpyHostToDevice, c->stream));
     VEGAS_CK(launch_table_from_edges(c->edges, c->table, c->mode, d, N, c->stream));

@@ -13,17 +13,17 @@ namespace vegas {
 
 // ------------------------------------------------------------- finalize
 // Iteration estimate (Lepage 1978): I = S1/n, sigma^2 = (S2/n - I^2)/(n-1).
-// Combination over iterations: inverse-variance weighted mean, its sigma and
-// chi^2/dof = sum (I_j - I)^2 / sigma_j^2 / (m - 1).  Iterations with zero
-// variance are exact: if any exist, their plain mean is the result with
-// sigma 0.
+// Combination over iterations, kept as running FP64 sums of w = 1/sigma^2,
+// w I and w I^2 over the iterations with a finite weight:
+//   I = sum w I / sum w,  sigma = (sum w)^-1/2,
+//   chi^2/dof = (sum w I^2 - I sum w I) / (m - 1)   (clamped at 0).
+// Iterations with zero variance are exact: if any exist, their plain mean is
+// the result with sigma 0.  One block; O(d N) work, whatever the number of
+// iterations so far.
 __global__ void __launch_bounds__(256)
 finalize_kernel(double *acc, double *last, unsigned long long *n_nonfinite, float *hscale,
-                double *jmul, IterRec *iters, CombRec *comb, int t, long long n, int total,
-                double inv_scale0, double jinit0) {
-    __shared__ double sh[3][8];
-    __shared__ double mean_s;
-    __shared__ int nzero_s;
+                double *jmul, IterRec *iters, CombState *cs, CombRec *comb, int rec, long long n,
+                int total, double inv_scale0, double jinit0) {
     __shared__ double inv_s;
     if (threadIdx.x == 0) {
         // v was accumulated scaled by scale0 * jmul; the next iteration's
@@ -54,112 +54,57 @@ finalize_kernel(double *acc, double *last, unsigned long long *n_nonfinite, floa
         r.n_nonfinite = nf;
         if (ne >= 2) {
             const double I = last[0] / static_cast<double>(ne);
-            double var = (last[1] / static_cast<double>(ne) - I * I) / static_cast<double>(ne - 1);
+            const double var = (last[1] / static_cast<double>(ne) - I * I) / static_cast<double>(ne - 1);
             r.I = I;
             r.sigma = var > 0.0 ? sqrt(var) : 0.0;
-        } else if (ne == 1) {
-            r.I = last[0];
-            r.sigma = 0.0;
         } else {
-            r.I = 0.0;
+            r.I = ne == 1 ? last[0] : 0.0;
             r.sigma = 0.0;
         }
-        iters[t] = r;
-    }
-    __syncthreads();
-    // combination over iters[0..t] (includes the record just written)
-    const int m = t + 1;
-    double wsum = 0.0, wisum = 0.0, zsum = 0.0;
-    int nzero = 0;
-    for (int j = threadIdx.x; j < m; j += blockDim.x) {
-        const IterRec r = iters[j];
-        if (r.n <= 0) continue;  // an all-non-finite iteration carries no information
-        if (r.sigma == 0.0) {
-            ++nzero;
-            zsum += r.I;
-        } else {
-            const double w = 1.0 / (r.sigma * r.sigma);
-            wsum += w;
-            wisum += w * r.I;
+        iters[rec % kIterRing] = r;
+        CombState st = *cs;
+        st.n_done += 1;
+        if (ne > 0) {
+            st.m += 1;
+            if (r.sigma == 0.0) {
+                st.nzero += 1;
+                st.zsum += r.I;
+            } else {
+                const double w = 1.0 / (r.sigma * r.sigma);
+                st.wsum += w;
+                st.wisum += w * r.I;
+                st.wi2sum += w * r.I * r.I;
+            }
         }
-    }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    wsum = warp_sum(wsum);
-    wisum = warp_sum(wisum);
-    zsum = warp_sum(zsum);
-    nzero = __reduce_add_sync(0xFFFFFFFFu, nzero);
-    __shared__ int nz_w[8];
-    if (lane == 0) {
-        sh[0][warp] = wsum;
-        sh[1][warp] = wisum;
-        sh[2][warp] = zsum;
-        nz_w[warp] = nzero;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double a = 0, b = 0, z = 0;
-        int nz = 0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
-            a += sh[0][k];
-            b += sh[1][k];
-            z += sh[2][k];
-            nz += nz_w[k];
-        }
-        nzero_s = nz;
-        if (nz > 0) mean_s = z / nz;
-        else mean_s = a > 0.0 ? b / a : 0.0;
-        sh[0][0] = a;
-    }
-    __syncthreads();
-    const double mean = mean_s;
-    double chi = 0.0;
-    int used = 0;
-    if (nzero_s == 0) {
-        for (int j = threadIdx.x; j < m; j += blockDim.x) {
-            const IterRec r = iters[j];
-            if (r.n <= 0) continue;
-            const double dv = (r.I - mean) / r.sigma;
-            chi += dv * dv;
-            ++used;
-        }
-    }
-    chi = warp_sum(chi);
-    used = __reduce_add_sync(0xFFFFFFFFu, used);
-    __syncthreads();
-    if (lane == 0) {
-        sh[1][warp] = chi;
-        nz_w[warp] = used;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double c = 0.0;
-        int u = 0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
-            c += sh[1][k];
-            u += nz_w[k];
-        }
+        *cs = st;
         CombRec out;
-        out.n_iter = m;
-        out.I = mean;
-        if (nzero_s > 0) {
+        out.n_iter = st.n_done;
+        out.status = ne <= 0 ? 6 : 0;
+        if (st.nzero > 0) {
+            out.I = st.zsum / st.nzero;
             out.sigma = 0.0;
             out.chi2_dof = 0.0;
+        } else if (st.wsum > 0.0) {
+            out.I = st.wisum / st.wsum;
+            out.sigma = 1.0 / sqrt(st.wsum);
+            const double chi = st.wi2sum - out.I * st.wisum;
+            out.chi2_dof = st.m > 1 ? fmax(chi, 0.0) / static_cast<double>(st.m - 1) : 0.0;
         } else {
-            out.sigma = sh[0][0] > 0.0 ? 1.0 / sqrt(sh[0][0]) : 0.0;
-            out.chi2_dof = u > 1 ? c / static_cast<double>(u - 1) : 0.0;
+            out.I = 0.0;
+            out.sigma = 0.0;
+            out.chi2_dof = 0.0;
         }
-        out.status = iters[t].n <= 0 ? 6 : 0;
         *comb = out;
     }
 }
 
 cudaError_t launch_finalize(double *acc, double *last, unsigned long long *n_nonfinite,
-                            float *hscale, double *jmul, IterRec *iters, CombRec *comb, int t,
-                            long long n, int d, int N, double inv_scale0, double jinit0,
-                            cudaStream_t stream) {
+                            float *hscale, double *jmul, IterRec *iters, CombState *cs,
+                            CombRec *comb, int rec, long long n, int d, int N, double inv_scale0,
+                            double jinit0, cudaStream_t stream) {
     const int total = 2 + d * N;
-    finalize_kernel<<<1, 256, 0, stream>>>(acc, last, n_nonfinite, hscale, jmul, iters, comb, t, n,
-                                           total, inv_scale0, jinit0);
+    finalize_kernel<<<1, 256, 0, stream>>>(acc, last, n_nonfinite, hscale, jmul, iters, cs, comb,
+                                           rec, n, total, inv_scale0, jinit0);
     return cudaGetLastError();
 }
 

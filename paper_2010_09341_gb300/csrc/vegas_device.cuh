@@ -57,9 +57,10 @@ __device__ __forceinline__ Split split_bin(uint32_t r, uint32_t N) {
     return Split{static_cast<uint32_t>(t >> 32), static_cast<uint32_t>(t)};
 }
 
-// FP32: m = 1 + (lo >> 9) 2^-23, exact.
+// FP32: m = 1 + (lo >> 9) 2^-23, exact.  One funnel shift of the 64-bit
+// pair (0x7F : lo) right by 9 gives (lo >> 9) | (0x7F << 23), the bits of m.
 __device__ __forceinline__ float unit_mantissa_f32(uint32_t lo) {
-    return __uint_as_float(0x3F800000u | (lo >> 9));
+    return __uint_as_float(__funnelshift_r(lo, 0x7Fu, 9));
 }
 
 // FP64: m = 1 + lo 2^-32, exact (all 32 bits fit in the 52-bit mantissa).
@@ -109,7 +110,13 @@ __device__ __forceinline__ float ffma(float a, float b, float c) { return __fmaf
 __device__ __forceinline__ double ffma(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ float fabs_t(float x) { return fabsf(x); }
 __device__ __forceinline__ double fabs_t(double x) { return fabs(x); }
-__device__ __forceinline__ float fexp2(float x) { return exp2f(x); }
+// 2^x for the FP32 path: the hardware approximation (relative error about
+// 2^-22), results below the normal range flushed to zero.
+__device__ __forceinline__ float fexp2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 __device__ __forceinline__ double fexp2(double x) { return exp2(x); }
 __device__ __forceinline__ float flog2(float x) { return log2f(x); }
 __device__ __forceinline__ double flog2(double x) { return log2(x); }

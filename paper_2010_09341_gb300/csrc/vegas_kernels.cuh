@@ -18,6 +18,18 @@ struct IterRec {
     long long n_nonfinite;
 };
 
+// Running sums of the combination (finalize kernel).
+struct CombState {
+    double wsum, wisum, wi2sum, zsum;
+    int m;        // iterations with a finite weight
+    int nzero;    // of which with zero variance
+    int n_done;   // all iterations finalized
+    int pad;
+};
+
+// Iteration records are kept in a ring of this many entries.
+constexpr int kIterRing = 4096;
+
 // Running combination over all iterations so far (finalize kernel).
 struct CombRec {
     double I;
@@ -40,9 +52,9 @@ size_t sample_smem(int mode, bool priv, int d, int N);
 // Also sets *hscale, the fixed-point histogram scale of the next iteration.
 // Also rescales v for the next iteration (*jmul) -- see next_scales.
 cudaError_t launch_finalize(double *acc, double *last, unsigned long long *n_nonfinite,
-                            float *hscale, double *jmul, IterRec *iters, CombRec *comb, int t,
-                            long long n, int d, int N, double inv_scale0, double jinit0,
-                            cudaStream_t stream);
+                            float *hscale, double *jmul, IterRec *iters, CombState *cs,
+                            CombRec *comb, int rec, long long n, int d, int N, double inv_scale0,
+                            double jinit0, cudaStream_t stream);
 
 // Refine every dimension from the histograms in last[2..] and write the new
 // FP64 edges and the sampling table of the given mode.

@@ -70,7 +70,16 @@ __device__ __forceinline__ void refine_block(const double *h, double *e, void *t
         double r;
         if (dk <= 0.0) r = 0.0;
         else if (dk >= 1.0) r = 1.0;
-        else r = pow((1.0 - dk) / log(1.0 / dk), alpha);
+        else {
+            const double g = (1.0 - dk) / log(1.0 / dk);
+            // g^alpha; the usual exponents without a general power
+            if (alpha == 1.5) r = g * sqrt(g);
+            else if (alpha == 1.0) r = g;
+            else if (alpha == 0.5) r = sqrt(g);
+            else if (alpha == 2.0) r = g * g;
+            else if (alpha == 0.0) r = 1.0;
+            else r = pow(g, alpha);
+        }
         rho[k] = r;
     }
     __syncthreads();

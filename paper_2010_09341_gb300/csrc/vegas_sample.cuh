@@ -206,7 +206,8 @@ __device__ __forceinline__ void sample_range(const BlockState<MODE, PRIV> &bs,
     const int stride = blockDim.x;
     for (int k0 = threadIdx.x; k0 < cnt; k0 += kChunk * stride) {
         float p1 = 0.f, p2 = 0.f;
-#pragma unroll 1
+        // two samples in flight: their Philox and table-load chains interleave
+#pragma unroll 2
         for (int u = 0; u < kChunk; ++u) {
             const int k = k0 + u * stride;
             if (k >= cnt) break;
