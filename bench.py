@@ -230,16 +230,14 @@ def _time_single(V, torch, family, params, d, N, n, prec, iters, warm=2, iid=0):
                    precision=prec)
     ctx = V.vegas_create(cfg, family, params)
     for _ in range(warm):
-        V.vegas_iterate(ctx, sync=False)
-        V.vegas_refine(ctx)
+        V.vegas_step(ctx, sync=False)
     V.vegas_profile(ctx, True)
     s = torch.cuda.current_stream()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     a.record(s)
     for _ in range(iters):
-        V.vegas_iterate(ctx, sync=False)
-        V.vegas_refine(ctx)
+        V.vegas_step(ctx, sync=False)
     b.record(s)
     torch.cuda.synchronize()
     ms = a.elapsed_time(b)
@@ -365,8 +363,7 @@ def main():
 
     def step():
         for c in ctxs:
-            V.vegas_iterate(c, sync=False)
-            V.vegas_refine(c)
+            V.vegas_step(c, sync=False)  # iterate + refine
 
     for _ in range(args.warmup):
         step()
@@ -493,11 +490,11 @@ def main():
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "samples_per_step": samples_per_step,
                        "bins": NBINS, "dims": D, "precision": PRECISION,
-                       "step": "one iteration (sample + finalize + refine) of both integrals",
+                       "step": "one iteration (sample, then finalize + refine in one launch) of both integrals",
                        "l2": "flushed between steps (256 MiB write outside the step events); the kernel reads no HBM inputs",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "extra": extra,
-            "gpu_launches": args.steps * 3 * len(ctxs),
+            "gpu_launches": args.steps * 2 * len(ctxs),
             "clocks": clk,
         }
         print(json.dumps(out))

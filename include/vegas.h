@@ -178,6 +178,11 @@ vegas_status vegas_accumulators(vegas_ctx *ctx, double **dev_sums, int64_t *n_su
                                 unsigned long long **dev_nonfinite);
 vegas_status vegas_finalize(vegas_ctx *ctx, vegas_iter_result *out);
 
+/* vegas_iterate followed by vegas_refine, with the iteration result and the
+ * refinement in one launch (what run_integration does for every iteration
+ * but the last).  Same results as the two calls. */
+vegas_status vegas_step(vegas_ctx *ctx, vegas_iter_result *out);
+
 /* Refine the grid from the last iteration's histograms (asynchronous). */
 vegas_status vegas_refine(vegas_ctx *ctx);
 

@@ -71,6 +71,7 @@ _SIGS = {
     "vegas_accumulators": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_int64),
                                           ctypes.POINTER(_P)]),
     "vegas_finalize": (ctypes.c_int, [_P, ctypes.POINTER(VegasIterResult)]),
+    "vegas_step": (ctypes.c_int, [_P, ctypes.POINTER(VegasIterResult)]),
     "vegas_refine": (ctypes.c_int, [_P]),
     "vegas_result": (ctypes.c_int, [_P, ctypes.POINTER(VegasResult)]),
     "vegas_run": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(VegasIterResult),

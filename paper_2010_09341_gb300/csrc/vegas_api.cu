@@ -55,7 +55,7 @@ Layout layout_for(int d, int N) {
     L.hscale = off;
     off = align_up(off + sizeof(float));
     L.jmul = off;
-    off = align_up(off + sizeof(double));
+    off = align_up(off + 2 * sizeof(double));  // double-buffered by record parity
     L.iters = off;
     off = align_up(off + sizeof(IterRec) * kIterRing);
     L.comb = off;
@@ -332,8 +332,8 @@ vegas_status vegas_create(const vegas_config *cfg, const vegas_integrand *itg, v
     cudaError_t ce = cudaMemcpyAsync(c->edges, e.data(), e.size() * sizeof(double),
                                      cudaMemcpyHostToDevice, c->stream);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(c->acc, 0, (L.hscale + sizeof(float)) - L.acc, c->stream);
-    static const double kOne = 1.0;
-    if (ce == cudaSuccess) ce = cudaMemcpyAsync(c->jmul, &kOne, sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    static const double kOnes[2] = {1.0, 1.0};
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(c->jmul, kOnes, sizeof(kOnes), cudaMemcpyHostToDevice, c->stream);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(c->comb, 0, (L.cstate + sizeof(CombState)) - L.comb, c->stream);
     if (ce == cudaSuccess) ce = launch_table_from_edges(c->edges, c->table, mode, d, N, c->stream);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
@@ -360,7 +360,7 @@ static SampleArgs make_args(const vegas_ctx *c, long long s_begin, long long n, 
     a.iter = static_cast<uint32_t>(t);
     a.jinit = c->jinit;
     a.nblk4 = c->nblk4;
-    a.jmul = c->jmul;
+    a.jmul = c->jmul + (c->n_done & 1);
     a.hscale = c->hscale;
     a.fc64 = c->fc;
     for (int k = 0; k < 32; ++k) {
@@ -413,11 +413,26 @@ static vegas_status sample_samples(vegas_ctx *c, long long s_begin, long long co
 
 // Iteration result from the accumulators (n_events samples in all) and the
 // step to the next iteration.
-static vegas_status finalize_iteration(vegas_ctx *c, vegas_iter_result *out) {
-    const long long n = c->cfg.n_events;
-    VEGAS_CK(launch_finalize(c->acc, c->last, c->nonfinite, c->hscale, c->jmul, c->iters, c->cstate,
-                             c->comb, c->n_done, n, c->cfg.n_dim, c->cfg.n_bins, 1.0 / c->scale,
-                             c->jinit, c->stream));
+static FinalizeArgs finalize_args(vegas_ctx *c) {
+    FinalizeArgs f;
+    f.acc = c->acc;
+    f.last = c->last;
+    f.n_nonfinite = c->nonfinite;
+    f.hscale = c->hscale;
+    f.jmul2 = c->jmul;
+    f.iters = c->iters;
+    f.cs = c->cstate;
+    f.comb = c->comb;
+    f.rec = c->n_done;
+    f.total = 2 + c->cfg.n_dim * c->cfg.n_bins;
+    f.n = c->cfg.n_events;
+    f.inv_scale0 = 1.0 / c->scale;
+    f.jinit0 = c->jinit;
+    return f;
+}
+
+// Advance the counters after a finalize; copy the record out if asked.
+static vegas_status after_finalize(vegas_ctx *c, vegas_iter_result *out) {
     const int rec = c->n_done;
     c->n_done += 1;
     c->t += 1;
@@ -432,11 +447,27 @@ static vegas_status finalize_iteration(vegas_ctx *c, vegas_iter_result *out) {
     return r.n <= 0 ? VEGAS_ENONFINITE : VEGAS_OK;
 }
 
+// Iteration result from the accumulators (n_events samples in all) and the
+// step to the next iteration.
+static vegas_status finalize_iteration(vegas_ctx *c, vegas_iter_result *out) {
+    VEGAS_CK(launch_finalize(finalize_args(c), c->stream));
+    return after_finalize(c, out);
+}
+
 vegas_status vegas_iterate(vegas_ctx *c, vegas_iter_result *out) {
     if (!c) return VEGAS_EINVAL;
     const vegas_status st = sample_samples(c, 0, c->cfg.n_events);
     if (st != VEGAS_OK) return st;
     return finalize_iteration(c, out);
+}
+
+vegas_status vegas_step(vegas_ctx *c, vegas_iter_result *out) {
+    if (!c) return VEGAS_EINVAL;
+    const vegas_status st = sample_samples(c, 0, c->cfg.n_events);
+    if (st != VEGAS_OK) return st;
+    VEGAS_CK(launch_finalize_refine(finalize_args(c), c->edges, c->table, c->mode, c->cfg.n_dim,
+                                    c->cfg.n_bins, c->cfg.alpha, c->cfg.smooth, c->stream));
+    return after_finalize(c, out);
 }
 
 vegas_status vegas_sample_shard(vegas_ctx *c, int64_t s_begin, int64_t count) {
@@ -499,12 +530,8 @@ vegas_status vegas_run(vegas_ctx *c, int32_t n_iter, vegas_iter_result *iters, v
     if (iters && n_iter > kIterRing) return VEGAS_EINVAL;
     const int first = c->n_done;
     for (int k = 0; k < n_iter; ++k) {
-        vegas_status st = vegas_iterate(c, nullptr);
+        const vegas_status st = k + 1 < n_iter ? vegas_step(c, nullptr) : vegas_iterate(c, nullptr);
         if (st != VEGAS_OK) return st;
-        if (k + 1 < n_iter) {
-            st = vegas_refine(c);
-            if (st != VEGAS_OK) return st;
-        }
     }
     if (iters) {
         std::vector<IterRec> rs(n_iter);
@@ -613,7 +640,8 @@ vegas_status vegas_export_state(vegas_ctx *c, void *buf, size_t *size) {
     BlobHeader h;
     memset(&h, 0, sizeof(h));
     VEGAS_CK(cudaMemcpyAsync(&h.hscale, c->hscale, sizeof(float), cudaMemcpyDeviceToHost, c->stream));
-    VEGAS_CK(cudaMemcpyAsync(&h.jmul, c->jmul, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    VEGAS_CK(cudaMemcpyAsync(&h.jmul, c->jmul + (c->n_done & 1), sizeof(double), cudaMemcpyDeviceToHost,
+                             c->stream));
     VEGAS_CK(cudaStreamSynchronize(c->stream));
     h.magic = kMagic;
     h.version = 3;
@@ -675,7 +703,8 @@ vegas_status vegas_import_state(vegas_ctx *c, const void *buf, size_t size) {
     p += sizeof(CombRec);
     VEGAS_CK(cudaMemcpyAsync(c->cstate, p, sizeof(CombState), cudaMemcpyHostToDevice, c->stream));
     VEGAS_CK(cudaMemcpyAsync(c->hscale, &h.hscale, sizeof(float), cudaMemcpyHostToDevice, c->stream));
-    VEGAS_CK(cudaMemcpyAsync(c->jmul, &h.jmul, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    VEGAS_CK(cudaMemcpyAsync(c->jmul + (h.n_done & 1), &h.jmul, sizeof(double), cudaMemcpyHostToDevice,
+                             c->stream));
     VEGAS_CK(launch_table_from_edges(c->edges, c->table, c->mode, d, N, c->stream));
     VEGAS_CK(cudaStreamSynchronize(c->stream));
     c->t = h.t;

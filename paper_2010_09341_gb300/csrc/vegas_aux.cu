@@ -18,93 +18,96 @@ namespace vegas {
 //   I = sum w I / sum w,  sigma = (sum w)^-1/2,
 //   chi^2/dof = (sum w I^2 - I sum w I) / (m - 1)   (clamped at 0).
 // Iterations with zero variance are exact: if any exist, their plain mean is
-// the result with sigma 0.  One block; O(d N) work, whatever the number of
-// iterations so far.
-__global__ void __launch_bounds__(256)
-finalize_kernel(double *acc, double *last, unsigned long long *n_nonfinite, float *hscale,
-                double *jmul, IterRec *iters, CombState *cs, CombRec *comb, int rec, long long n,
-                int total, double inv_scale0, double jinit0) {
-    __shared__ double inv_s;
-    if (threadIdx.x == 0) {
-        // v was accumulated scaled by scale0 * jmul; the next iteration's
-        // rescale and fixed-point histogram scale come from this one's mean v^2
-        const double jm = *jmul;
-        inv_s = inv_scale0 / jm;
-        const long long ne = n - static_cast<long long>(*n_nonfinite);
-        const double m2 = ne > 0 ? acc[1] / static_cast<double>(ne) : 0.0;
-        double ratio;
-        float hs;
-        next_scales(m2, jinit0 * jm, &ratio, &hs);
-        *hscale = hs;
-        *jmul = jm * ratio;
+// the result with sigma 0.  O(1) whatever the number of iterations so far.
+//
+// The v-rescale is double-buffered by record parity: iteration `rec` was
+// sampled with jmul[rec & 1] and the next one uses jmul[(rec + 1) & 1], so
+// blocks that still read the current value never race with the update.
+__device__ void finalize_stats(const FinalizeArgs &f) {
+    // thread 0 only: S1, S2, the counters, the scales and the combination
+    const double jm = f.jmul2[f.rec & 1];
+    const double inv1 = f.inv_scale0 / jm;
+    const long long nf = static_cast<long long>(*f.n_nonfinite);
+    *f.n_nonfinite = 0ull;
+    const long long ne = f.n - nf;
+    const double S1 = f.acc[0] * inv1, S2 = f.acc[1] * inv1 * inv1;
+    const double m2 = ne > 0 ? f.acc[1] / static_cast<double>(ne) : 0.0;
+    f.last[0] = S1;
+    f.last[1] = S2;
+    f.acc[0] = 0.0;
+    f.acc[1] = 0.0;
+    double ratio;
+    float hs;
+    next_scales(m2, f.jinit0 * jm, &ratio, &hs);
+    *f.hscale = hs;
+    f.jmul2[(f.rec + 1) & 1] = jm * ratio;
+    IterRec r;
+    r.n = ne;
+    r.n_nonfinite = nf;
+    if (ne >= 2) {
+        const double rn = 1.0 / static_cast<double>(ne);
+        const double I = S1 * rn;
+        const double var = (S2 * rn - I * I) / static_cast<double>(ne - 1);
+        r.I = I;
+        r.sigma = var > 0.0 ? sqrt(var) : 0.0;
+    } else {
+        r.I = ne == 1 ? S1 : 0.0;
+        r.sigma = 0.0;
     }
-    __syncthreads();
-    const double inv1 = inv_s, inv2 = inv_s * inv_s;
-    for (int c = threadIdx.x; c < total; c += blockDim.x) {
-        last[c] = acc[c] * (c == 0 ? inv1 : inv2);
-        acc[c] = 0.0;
+    f.iters[f.rec % kIterRing] = r;
+    CombState st = *f.cs;
+    st.n_done += 1;
+    if (ne > 0) {
+        st.m += 1;
+        if (r.sigma == 0.0) {
+            st.nzero += 1;
+            st.zsum += r.I;
+        } else {
+            const double w = 1.0 / (r.sigma * r.sigma);
+            st.wsum += w;
+            st.wisum += w * r.I;
+            st.wi2sum += w * r.I * r.I;
+        }
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const long long nf = static_cast<long long>(*n_nonfinite);
-        *n_nonfinite = 0ull;
-        const long long ne = n - nf;
-        IterRec r;
-        r.n = ne;
-        r.n_nonfinite = nf;
-        if (ne >= 2) {
-            const double I = last[0] / static_cast<double>(ne);
-            const double var = (last[1] / static_cast<double>(ne) - I * I) / static_cast<double>(ne - 1);
-            r.I = I;
-            r.sigma = var > 0.0 ? sqrt(var) : 0.0;
-        } else {
-            r.I = ne == 1 ? last[0] : 0.0;
-            r.sigma = 0.0;
-        }
-        iters[rec % kIterRing] = r;
-        CombState st = *cs;
-        st.n_done += 1;
-        if (ne > 0) {
-            st.m += 1;
-            if (r.sigma == 0.0) {
-                st.nzero += 1;
-                st.zsum += r.I;
-            } else {
-                const double w = 1.0 / (r.sigma * r.sigma);
-                st.wsum += w;
-                st.wisum += w * r.I;
-                st.wi2sum += w * r.I * r.I;
-            }
-        }
-        *cs = st;
-        CombRec out;
-        out.n_iter = st.n_done;
-        out.status = ne <= 0 ? 6 : 0;
-        if (st.nzero > 0) {
-            out.I = st.zsum / st.nzero;
-            out.sigma = 0.0;
-            out.chi2_dof = 0.0;
-        } else if (st.wsum > 0.0) {
-            out.I = st.wisum / st.wsum;
-            out.sigma = 1.0 / sqrt(st.wsum);
-            const double chi = st.wi2sum - out.I * st.wisum;
-            out.chi2_dof = st.m > 1 ? fmax(chi, 0.0) / static_cast<double>(st.m - 1) : 0.0;
-        } else {
-            out.I = 0.0;
-            out.sigma = 0.0;
-            out.chi2_dof = 0.0;
-        }
-        *comb = out;
+    *f.cs = st;
+    CombRec out;
+    out.n_iter = st.n_done;
+    out.status = ne <= 0 ? 6 : 0;
+    if (st.nzero > 0) {
+        out.I = st.zsum / st.nzero;
+        out.sigma = 0.0;
+        out.chi2_dof = 0.0;
+    } else if (st.wsum > 0.0) {
+        out.I = st.wisum / st.wsum;
+        out.sigma = 1.0 / sqrt(st.wsum);
+        const double chi = st.wi2sum - out.I * st.wisum;
+        out.chi2_dof = st.m > 1 ? fmax(chi, 0.0) / static_cast<double>(st.m - 1) : 0.0;
+    } else {
+        out.I = 0.0;
+        out.sigma = 0.0;
+        out.chi2_dof = 0.0;
+    }
+    *f.comb = out;
+}
+
+// Histogram rows of one iteration: last = acc * inv^2, acc = 0, for the
+// values [begin, end) of the accumulator row (every thread of the block).
+__device__ __forceinline__ void move_rows(const FinalizeArgs &f, int begin, int end) {
+    const double inv = f.inv_scale0 / f.jmul2[f.rec & 1];
+    const double inv2 = inv * inv;
+    for (int c = begin + threadIdx.x; c < end; c += blockDim.x) {
+        f.last[c] = f.acc[c] * inv2;
+        f.acc[c] = 0.0;
     }
 }
 
-cudaError_t launch_finalize(double *acc, double *last, unsigned long long *n_nonfinite,
-                            float *hscale, double *jmul, IterRec *iters, CombState *cs,
-                            CombRec *comb, int rec, long long n, int d, int N, double inv_scale0,
-                            double jinit0, cudaStream_t stream) {
-    const int total = 2 + d * N;
-    finalize_kernel<<<1, 256, 0, stream>>>(acc, last, n_nonfinite, hscale, jmul, iters, cs, comb,
-                                           rec, n, total, inv_scale0, jinit0);
+__global__ void __launch_bounds__(256) finalize_kernel(const FinalizeArgs f) {
+    if (threadIdx.x == 0) finalize_stats(f);
+    move_rows(f, 2, f.total);
+}
+
+cudaError_t launch_finalize(const FinalizeArgs &f, cudaStream_t stream) {
+    finalize_kernel<<<1, 256, 0, stream>>>(f);
     return cudaGetLastError();
 }
 
@@ -118,6 +121,35 @@ refine_kernel(const double *last, double *edges, void *table, int mode, int N, d
     refine_block(last + 2 + static_cast<size_t>(j) * N, edges + static_cast<size_t>(j) * (N + 1),
                  static_cast<char *>(table) + entry * static_cast<size_t>(j) * N, mode, N, alpha,
                  smooth, rs);
+}
+
+// Finalize and refinement of one iteration in one launch (d + 1 blocks):
+// block j < d refines dimension j from its accumulator row (refinement only
+// normalises the histogram, so the row's scale does not matter) and then
+// moves the row to `last`; block d forms the iteration result.
+__global__ void __launch_bounds__(kRefineThreads)
+finalize_refine_kernel(const FinalizeArgs f, double *edges, void *table, int mode, int d, int N,
+                       double alpha, int smooth) {
+    extern __shared__ double rs[];
+    const int j = blockIdx.x;
+    if (j == d) {
+        if (threadIdx.x == 0) finalize_stats(f);
+        return;
+    }
+    const size_t entry = mode == ACC_F64 ? sizeof(double2) : sizeof(float2);
+    refine_block(f.acc + 2 + static_cast<size_t>(j) * N, edges + static_cast<size_t>(j) * (N + 1),
+                 static_cast<char *>(table) + entry * static_cast<size_t>(j) * N, mode, N, alpha,
+                 smooth, rs);
+    __syncthreads();
+    move_rows(f, 2 + j * N, 2 + (j + 1) * N);
+}
+
+cudaError_t launch_finalize_refine(const FinalizeArgs &f, double *edges, void *table, int mode,
+                                   int d, int N, double alpha, int smooth, cudaStream_t stream) {
+    const size_t smem = static_cast<size_t>(4 * N + 2) * sizeof(double);
+    finalize_refine_kernel<<<d + 1, kRefineThreads, smem, stream>>>(f, edges, table, mode, d, N, alpha,
+                                                                    smooth);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_refine(const double *last, double *edges, void *table, int mode, int d, int N,

@@ -48,13 +48,25 @@ inline int tier_of(int d) { return d <= 4 ? 0 : (d <= 8 ? 1 : (d <= 16 ? 2 : 3))
 size_t sample_smem(int mode, bool priv, int d, int N);
 
 // Finalize: move the accumulators (unscaled) to `last`, zero them, form
-// I_t and sigma_t, store iters[t] and recombine all iterations into *comb.
-// Also sets *hscale, the fixed-point histogram scale of the next iteration.
-// Also rescales v for the next iteration (*jmul) -- see next_scales.
-cudaError_t launch_finalize(double *acc, double *last, unsigned long long *n_nonfinite,
-                            float *hscale, double *jmul, IterRec *iters, CombState *cs,
-                            CombRec *comb, int rec, long long n, int d, int N, double inv_scale0,
-                            double jinit0, cudaStream_t stream);
+// I_t and sigma_t, store the record, update the combination and the scales
+// of the next iteration (fixed-point histogram scale, v-rescale).
+struct FinalizeArgs {
+    double *acc, *last;
+    unsigned long long *n_nonfinite;
+    float *hscale;
+    double *jmul2;        // two slots, selected by record parity
+    IterRec *iters;
+    CombState *cs;
+    CombRec *comb;
+    int rec;              // record index of this iteration
+    int total;            // 2 + d N
+    long long n;          // samples of the iteration
+    double inv_scale0, jinit0;
+};
+cudaError_t launch_finalize(const FinalizeArgs &f, cudaStream_t stream);
+// Finalize and refinement in one launch (vegas_step).
+cudaError_t launch_finalize_refine(const FinalizeArgs &f, double *edges, void *table, int mode,
+                                   int d, int N, double alpha, int smooth, cudaStream_t stream);
 
 // Refine every dimension from the histograms in last[2..] and write the new
 // FP64 edges and the sampling table of the given mode.

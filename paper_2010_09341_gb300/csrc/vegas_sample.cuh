@@ -101,6 +101,10 @@ __host__ __device__ constexpr size_t sample_smem_bytes(int d, int N) {
 __device__ __forceinline__ void red_add_shared(float *p, float v) { atomicAdd(p, v); }
 __device__ __forceinline__ void red_add_shared(double *p, double v) { atomicAdd(p, v); }
 
+__device__ __forceinline__ int binary_exponent(double x) {  // floor(log2 x) for x > 0 normal
+    return static_cast<int>((__double_as_longlong(x) >> 52) & 0x7FF) - 1023;
+}
+
 // Scales for the next iteration from m2, the mean of this iteration's scaled
 // v^2 (0 if none): a power of two `ratio` that brings the mean of v^2 near 1
 // (FP32 keeps its full precision for v and v^2 whatever the size of the
@@ -108,16 +112,23 @@ __device__ __forceinline__ void red_add_shared(double *p, double v) { atomicAdd(
 // within 2^-100..2^100, and the fixed-point histogram scale that maps the
 // rescaled mean to 2^18.
 __device__ __forceinline__ void next_scales(double m2, double jinit_eff, double *ratio, float *hs) {
+    // exponents from the bits, not from FP64 log2 (a long chain on this GPU's FP64 pipe)
     double r = 1.0;
     float h = 0.f;
     if (m2 > 0.0 && isfinite(m2)) {
-        int e = -static_cast<int>(rint(0.5 * log2(m2)));
-        const int ej = static_cast<int>(rint(log2(fabs(jinit_eff) > 0.0 ? fabs(jinit_eff) : 1.0)));
+        const int ex = binary_exponent(m2);                  // m2 in [2^ex, 2^(ex+1))
+        int e = -(ex >> 1);                                  // m2 r^2 in [1, 4)
+        const double aj = fabs(jinit_eff);
+        const int ej = (aj > 0.0 && isfinite(aj)) ? binary_exponent(aj) : 0;
         e = max(-100 - ej, min(100 - ej, e));
-        r = ldexp(1.0, e);
-        int eh = 18 - static_cast<int>(ceil(log2(m2 * r * r)));
+        e = max(-1000, min(1000, e));
+        r = __longlong_as_double(static_cast<long long>(e + 1023) << 52);
+        const double y = m2 * r * r;                         // exact (power-of-two factors)
+        const long long yb = __double_as_longlong(y);
+        const int cl = binary_exponent(y) + ((yb & 0xFFFFFFFFFFFFFLL) != 0 ? 1 : 0);  // ceil(log2 y)
+        int eh = 18 - cl;
         eh = max(-100, min(100, eh));
-        h = ldexpf(1.0f, eh);
+        h = __int_as_float((eh + 127) << 23);
     }
     *ratio = r;
     *hs = h;

@@ -102,6 +102,19 @@ def vegas_iterate(ctx: Context, sync: bool = True):
     return r.I, r.sigma, r.n, r.n_nonfinite
 
 
+def vegas_step(ctx: Context, sync: bool = True):
+    """vegas_iterate + vegas_refine in fewer launches; with sync returns the iteration."""
+    lib = nat.load()
+    if not sync:
+        check(lib.vegas_step(ctx.handle, None), "vegas_step")
+        return None
+    r = nat.VegasIterResult()
+    st = lib.vegas_step(ctx.handle, ctypes.byref(r))
+    if st not in (nat.VEGAS_OK, nat.VEGAS_ENONFINITE):
+        check(st, "vegas_step")
+    return r.I, r.sigma, r.n, r.n_nonfinite
+
+
 def vegas_sample_shard(ctx: Context, s_begin: int, count: int) -> None:
     check(nat.load().vegas_sample_shard(ctx.handle, int(s_begin), int(count)), "vegas_sample_shard")
 

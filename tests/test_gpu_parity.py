@@ -361,3 +361,24 @@ def test_two_shards_equal_one_context(prec):
         for c in (ref, sh[0], sh[1]):
             V.vegas_refine(c)
         assert np.array_equal(V.vegas_get_grid(sh[0]), V.vegas_get_grid(sh[1]))
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_step_equals_iterate_then_refine(prec):
+    """vegas_step (finalize and refinement in one launch) gives the same
+    iterations and grids as vegas_iterate followed by vegas_refine."""
+    V = native()
+    d, N, n = 7, 50, 200_000
+    p = params_for("genz_gauss", d)
+    a, _ = _make(V, "genz_gauss", d, N, n, prec, params=p)
+    b, _ = _make(V, "genz_gauss", d, N, n, prec, params=p)
+    tol = TOL[prec]
+    for _ in range(4):
+        Ia = V.vegas_step(a)[0]
+        Ib = V.vegas_iterate(b)[0]
+        V.vegas_refine(b)
+        assert abs(Ia - Ib) <= tol * abs(Ib)
+        ea, eb = V.vegas_get_grid(a), V.vegas_get_grid(b)
+        assert np.max(np.abs(ea - eb)) <= (1e-13 if prec == "fp64" else 1e-5)
+    ra, rb = V.vegas_result(a), V.vegas_result(b)
+    assert abs(ra["I"] - rb["I"]) <= tol * abs(rb["I"]) and ra["n_iter"] == rb["n_iter"] == 4
