@@ -1,0 +1,8 @@
+// Batched sampling kernel: mode ACC_F32_KAHAN, layout 2 (half the lane-private copies) (instantiation unit).
+#include "vegas_batch_sample.cuh"
+
+namespace vegas {
+const void *batch_sample_kernel_f32kahan_half() {
+    return reinterpret_cast<const void *>(&batch_sample_kernel_t<ACC_F32_KAHAN, 2>);
+}
+}  // namespace vegas

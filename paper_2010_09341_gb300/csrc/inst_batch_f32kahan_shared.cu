@@ -1,8 +1,8 @@
-// Batched sampling kernel: mode ACC_F32_KAHAN, lane-private layout = false (generated instantiation unit).
+// Batched sampling kernel: mode ACC_F32_KAHAN, layout 0 (one copy per cell) (instantiation unit).
 #include "vegas_batch_sample.cuh"
 
 namespace vegas {
 const void *batch_sample_kernel_f32kahan_shared() {
-    return reinterpret_cast<const void *>(&batch_sample_kernel_t<ACC_F32_KAHAN, false>);
+    return reinterpret_cast<const void *>(&batch_sample_kernel_t<ACC_F32_KAHAN, 0>);
 }
 }  // namespace vegas

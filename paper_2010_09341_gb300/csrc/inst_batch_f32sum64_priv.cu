@@ -1,8 +1,8 @@
-// Batched sampling kernel: mode ACC_F32_SUM64, lane-private layout = true (generated instantiation unit).
+// Batched sampling kernel: mode ACC_F32_SUM64, layout 1 (lane-private copies) (instantiation unit).
 #include "vegas_batch_sample.cuh"
 
 namespace vegas {
 const void *batch_sample_kernel_f32sum64_priv() {
-    return reinterpret_cast<const void *>(&batch_sample_kernel_t<ACC_F32_SUM64, true>);
+    return reinterpret_cast<const void *>(&batch_sample_kernel_t<ACC_F32_SUM64, 1>);
 }
 }  // namespace vegas

@@ -204,6 +204,7 @@ struct vegas_ctx {
     double nblk4;
     const void *kfn;
     size_t smem;
+    bool priv;          // lane-private shared-memory layout
     int threads;
     int max_blocks;
     bool profiling = false;
@@ -322,6 +323,7 @@ vegas_status vegas_create(const vegas_config *cfg, const vegas_integrand *itg, v
     c->nblk4 = Nd * Nd * Nd * Nd;
     c->kfn = fn;
     c->smem = smem;
+    c->priv = priv;
     c->threads = threads;
     c->max_blocks = occ * di.sms;
 
@@ -378,8 +380,8 @@ static vegas_status launch_sampling(vegas_ctx *c, long long s_begin, long long n
                            (static_cast<long long>(c->threads) * 4);
     long long blocks = std::max(1LL, std::min<long long>(c->max_blocks, want));
     if (c->mode != ACC_F64) {
-        // fixed-point histogram cells: at most 2048 N samples per block
-        const long long cap = 2048LL * c->cfg.n_bins;
+        // fixed-point histogram cells: a bounded number of samples per block
+        const long long cap = block_samples_max(c->mode, c->priv ? 1 : 0, c->cfg.n_bins);
         blocks = std::max(blocks, (n + cap - 1) / cap);
     }
     void *params[] = {&a};
@@ -875,7 +877,10 @@ extern "C" vegas_status vegas_iterate_noalloc(const vegas_config *cfg, const veg
         a.n = std::min(lim, n - s0);
         const long long want = (a.n + threads * 4LL - 1) / (threads * 4LL);
         long long blocks = std::max(1LL, std::min<long long>(static_cast<long long>(occ) * di.sms, want));
-        if (mode != ACC_F64) blocks = std::max(blocks, (a.n + 2048LL * N - 1) / (2048LL * N));
+        if (mode != ACC_F64) {
+            const long long cap = block_samples_max(mode, priv ? 1 : 0, N);
+            blocks = std::max(blocks, (a.n + cap - 1) / cap);
+        }
         void *params[] = {&a};
         VEGAS_CK(cudaLaunchKernel(fn, dim3(static_cast<unsigned>(blocks)), dim3(threads), params, smem, s));
     }

@@ -281,12 +281,28 @@ cudaError_t launch_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *ou
     return cudaGetLastError();
 }
 
-size_t sample_smem(int mode, bool priv, int d, int N) {
+template <int MODE>
+static size_t smem_of(int layout, int d, int N) {
+    return layout == 1 ? sample_smem_bytes<MODE, 1>(d, N)
+                       : (layout == 2 ? sample_smem_bytes<MODE, 2>(d, N) : sample_smem_bytes<MODE, 0>(d, N));
+}
+
+size_t sample_smem(int mode, int layout, int d, int N) {
     switch (mode) {
-    case ACC_F64: return priv ? sample_smem_bytes<ACC_F64, true>(d, N) : sample_smem_bytes<ACC_F64, false>(d, N);
-    case ACC_F32_SUM64: return priv ? sample_smem_bytes<ACC_F32_SUM64, true>(d, N) : sample_smem_bytes<ACC_F32_SUM64, false>(d, N);
-    default: return priv ? sample_smem_bytes<ACC_F32_KAHAN, true>(d, N) : sample_smem_bytes<ACC_F32_KAHAN, false>(d, N);
+    case ACC_F64: return smem_of<ACC_F64>(layout, d, N);
+    case ACC_F32_SUM64: return smem_of<ACC_F32_SUM64>(layout, d, N);
+    default: return smem_of<ACC_F32_KAHAN>(layout, d, N);
     }
+}
+
+template <int MODE>
+static long long cap_of(int layout, int N) {
+    return layout == 1 ? block_sample_cap<MODE, 1>(N)
+                       : (layout == 2 ? block_sample_cap<MODE, 2>(N) : block_sample_cap<MODE, 0>(N));
+}
+
+long long block_samples_max(int mode, int layout, int N) {
+    return mode == ACC_F32_SUM64 ? cap_of<ACC_F32_SUM64>(layout, N) : cap_of<ACC_F32_KAHAN>(layout, N);
 }
 
 }  // namespace vegas

@@ -18,17 +18,23 @@
 namespace vegas {
 
 const void *batch_sample_kernel_f32kahan_priv();
+const void *batch_sample_kernel_f32kahan_half();
 const void *batch_sample_kernel_f32kahan_shared();
 const void *batch_sample_kernel_f32sum64_priv();
+const void *batch_sample_kernel_f32sum64_half();
 const void *batch_sample_kernel_f32sum64_shared();
 
-const void *batch_sample_kernel(int mode, bool priv) {
-    if (mode == ACC_F32_KAHAN) return priv ? batch_sample_kernel_f32kahan_priv() : batch_sample_kernel_f32kahan_shared();
-    if (mode == ACC_F32_SUM64) return priv ? batch_sample_kernel_f32sum64_priv() : batch_sample_kernel_f32sum64_shared();
+const void *batch_sample_kernel(int mode, int layout) {
+    if (mode == ACC_F32_KAHAN)
+        return layout == 1 ? batch_sample_kernel_f32kahan_priv()
+                           : (layout == 2 ? batch_sample_kernel_f32kahan_half() : batch_sample_kernel_f32kahan_shared());
+    if (mode == ACC_F32_SUM64)
+        return layout == 1 ? batch_sample_kernel_f32sum64_priv()
+                           : (layout == 2 ? batch_sample_kernel_f32sum64_half() : batch_sample_kernel_f32sum64_shared());
     return nullptr;
 }
 
-size_t batch_sample_smem(int mode, bool priv, int max_cells) { return sample_smem(mode, priv, max_cells, 1); }
+size_t batch_sample_smem(int mode, int layout, int max_cells) { return sample_smem(mode, layout, max_cells, 1); }
 
 // ------------------------------------------------------------- kernels
 // Iteration result and running combination of every item's slot (one block
@@ -290,7 +296,7 @@ struct vegas_batch {
     int max_cells = 0;     // largest d N the kernels were configured for
     int max_N = 2;
     int tile_samples = 8192;
-    int threads = 512;
+    int threads = kBatchThreads;
     // pinned host buffers
     char *h_plan = nullptr;      // image of the device plan region [L.plan, L.results)
     BatchResult *h_results = nullptr;
@@ -304,7 +310,7 @@ struct vegas_batch {
     BatchArgs args;
     int sm_count = 0;
     size_t smem_optin = 0;
-    bool priv = true;
+    int layout = 1;        // shared-memory layout of the sampling kernel
     const void *kfn = nullptr;
     size_t smem = 0;
     int sample_blocks = 0;
@@ -324,16 +330,19 @@ vegas_status batch_invalidate_graph(vegas_batch *b) {
 // Choose the sampling kernel and its launch for the current largest slot.
 vegas_status batch_configure(vegas_batch *b, int cells) {
     const size_t budget = b->smem_optin > 2048 ? b->smem_optin - 2048 : 0;
-    bool priv = batch_sample_smem(b->mode, true, cells) <= budget;
-    size_t smem = batch_sample_smem(b->mode, priv, cells);
+    // the most lane-private copies that fit
+    int layout = 1;
+    if (batch_sample_smem(b->mode, layout, cells) > budget) layout = 2;
+    if (batch_sample_smem(b->mode, layout, cells) > budget) layout = 0;
+    size_t smem = batch_sample_smem(b->mode, layout, cells);
     if (smem > budget) return VEGAS_EINVAL;
-    const void *fn = batch_sample_kernel(b->mode, priv);
+    const void *fn = batch_sample_kernel(b->mode, layout);
     if (!fn) return VEGAS_EINVAL;
     VB_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
     int occ = 0;
     VB_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, b->threads, smem));
     if (occ < 1) return VEGAS_EINVAL;
-    b->priv = priv;
+    b->layout = layout;
     b->kfn = fn;
     b->smem = smem;
     b->sample_blocks = occ * b->sm_count;
@@ -542,7 +551,7 @@ vegas_status vegas_batch_add(vegas_batch *b, const vegas_config *cfg, const vega
     // the shared-memory working set must fit for the largest slot
     if (d * N > b->max_cells) {
         const size_t budget = b->smem_optin > 2048 ? b->smem_optin - 2048 : 0;
-        if (batch_sample_smem(b->mode, false, d * N) > budget) return VEGAS_EINVAL;
+        if (batch_sample_smem(b->mode, 0, d * N) > budget) return VEGAS_EINVAL;
     }
     int s = -1;
     for (int k = 0; k < b->max_slots; ++k)

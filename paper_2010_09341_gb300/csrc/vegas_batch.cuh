@@ -70,9 +70,14 @@ struct BatchArgs {
     int mode;
 };
 
-// The batched sampling kernel of one mode and layout (instantiated in
-// vegas_batch_inst_*.cu).
-const void *batch_sample_kernel(int mode, bool priv);
-size_t batch_sample_smem(int mode, bool priv, int max_cells);
+// Threads per block of the persistent sampling kernel (one block per SM,
+// up to 128 registers a thread).
+constexpr int kBatchThreads = 512;
+
+// The batched sampling kernel of one mode and shared-memory layout (1 =
+// lane-private copies, 2 = half as many, 0 = one copy per cell; instantiated
+// in inst_batch_*.cu) and its dynamic shared memory for max_cells cells.
+const void *batch_sample_kernel(int mode, int layout);
+size_t batch_sample_smem(int mode, int layout, int max_cells);
 
 }  // namespace vegas

@@ -5,50 +5,104 @@
 // slot's samples into the block's shared-memory cells.  Tiles of one slot are
 // consecutive, so a block usually claims several tiles of the same slot in a
 // row; when the slot changes, the block adds its sums to the old slot's FP64
-// accumulators and stages the new slot's table.
+// accumulators and stages the new slot's table.  The fixed-point cells are
+// also flushed whenever the block has added block_sample_cap samples to them.
 #pragma once
 
 #include "vegas_batch.cuh"
 
 namespace vegas {
 
-// One tile of one slot.  Kept out of line: each (family, dimension tier)
-// variant gets its own register allocation instead of sharing the persistent
-// loop's; the call happens once per tile of thousands of samples.
-template <int MODE, bool PRIV, int FAM, int MAXD, bool EXACT>
-__device__ __noinline__ ThreadSums<MODE> batch_tile(BlockState<MODE, PRIV> bs,
-                                                    RangeParams<typename ModeTraits<MODE>::T> rp,
-                                                    const FamConsts<typename ModeTraits<MODE>::T> *fc,
-                                                    ThreadSums<MODE> ts, unsigned long long s0, int cnt) {
-    sample_range<FAM, MODE, MAXD, EXACT, PRIV>(bs, rp, *fc, ts, s0, cnt);
-    return ts;
+// The current slot's integrand constants, staged per slot switch.  File-scope
+// shared variables (one per precision) so that the out-of-line tile samplers
+// address them as shared memory rather than through a generic pointer.
+__shared__ FamConsts<float> g_batch_fc32;
+__shared__ FamConsts<double> g_batch_fc64;
+template <class T> __device__ __forceinline__ FamConsts<T> &batch_fc();
+template <> __device__ __forceinline__ FamConsts<float> &batch_fc<float>() { return g_batch_fc32; }
+template <> __device__ __forceinline__ FamConsts<double> &batch_fc<double>() { return g_batch_fc64; }
+
+// One range of one slot.  Kept out of line: each (family, dimension tier)
+// variant gets its own register allocation instead of the union of all of
+// them.  Arguments are scalars (passed in registers; a structure argument
+// would live in memory and be re-read in the loop); the running sums are
+// read and written once per call.
+template <int MODE, int PRIV, int FAM, int MAXD, bool EXACT>
+__device__ __noinline__ void batch_range(typename BlockState<MODE, PRIV>::T2 *tab,
+                                         typename BlockState<MODE, PRIV>::H *hist, uint32_t *fine, int d, int N,
+                                         uint32_t key0, uint32_t key1, uint32_t iter,
+                                         typename ModeTraits<MODE>::T jinit, typename ModeTraits<MODE>::T n4,
+                                         float hs, double *acc, unsigned long long s0, int cnt,
+                                         ThreadSums<MODE> *tsp) {
+    BlockState<MODE, PRIV> bs;
+    bs.tab = tab;
+    bs.hist = hist;
+    bs.fine = fine;
+    bs.cells = d * N;
+    RangeParams<typename ModeTraits<MODE>::T> rp;
+    rp.d = d;
+    rp.N = N;
+    rp.key0 = key0;
+    rp.key1 = key1;
+    rp.iter = iter;
+    rp.jinit = jinit;
+    rp.n4 = n4;
+    rp.hs = hs;
+    rp.acc = acc;
+    ThreadSums<MODE> ts = *tsp;
+    sample_range<FAM, MODE, MAXD, EXACT, PRIV>(bs, rp, batch_fc<typename ModeTraits<MODE>::T>(), ts, s0, cnt);
+    *tsp = ts;
 }
 
-template <int MODE, bool PRIV, int FAM>
+template <int MODE, int PRIV, int FAM, int MAXD, bool EXACT>
+__device__ __forceinline__ void batch_call(const BlockState<MODE, PRIV> &bs,
+                                           const RangeParams<typename ModeTraits<MODE>::T> &rp,
+                                           ThreadSums<MODE> &ts, unsigned long long s0, int cnt) {
+    batch_range<MODE, PRIV, FAM, MAXD, EXACT>(bs.tab, bs.hist, bs.fine, rp.d, rp.N, rp.key0, rp.key1, rp.iter,
+                                              rp.jinit, rp.n4, rp.hs, rp.acc, s0, cnt, &ts);
+}
+
+template <int MODE, int PRIV, int FAM>
 __device__ __forceinline__ void batch_dispatch_tier(const BlockState<MODE, PRIV> &bs,
                                                     const RangeParams<typename ModeTraits<MODE>::T> &rp,
-                                                    const FamConsts<typename ModeTraits<MODE>::T> *fc,
                                                     ThreadSums<MODE> &ts, unsigned long long s0, int cnt) {
     if (FAM == F_LO) {
-        ts = batch_tile<MODE, PRIV, FAM, 3, true>(bs, rp, fc, ts, s0, cnt);
+        batch_call<MODE, PRIV, FAM, 3, true>(bs, rp, ts, s0, cnt);
     } else if (rp.d <= 4) {
-        ts = batch_tile<MODE, PRIV, FAM, 4, false>(bs, rp, fc, ts, s0, cnt);
+        batch_call<MODE, PRIV, FAM, 4, false>(bs, rp, ts, s0, cnt);
     } else if (rp.d <= 8) {
-        ts = batch_tile<MODE, PRIV, FAM, 8, false>(bs, rp, fc, ts, s0, cnt);
+        batch_call<MODE, PRIV, FAM, 8, false>(bs, rp, ts, s0, cnt);
     } else if (rp.d <= 16) {
-        ts = batch_tile<MODE, PRIV, FAM, 16, false>(bs, rp, fc, ts, s0, cnt);
+        batch_call<MODE, PRIV, FAM, 16, false>(bs, rp, ts, s0, cnt);
     } else {
-        ts = batch_tile<MODE, PRIV, FAM, 32, false>(bs, rp, fc, ts, s0, cnt);
+        batch_call<MODE, PRIV, FAM, 32, false>(bs, rp, ts, s0, cnt);
     }
 }
 
-template <int MODE, bool PRIV>
-__global__ void __launch_bounds__(512, 1)
+template <int MODE, int PRIV>
+__device__ __forceinline__ void batch_dispatch(int fam, const BlockState<MODE, PRIV> &bs,
+                                               const RangeParams<typename ModeTraits<MODE>::T> &rp,
+                                               ThreadSums<MODE> &ts, unsigned long long s0, int cnt) {
+    switch (fam) {
+    case F_CONST: batch_dispatch_tier<MODE, PRIV, F_CONST>(bs, rp, ts, s0, cnt); break;
+    case F_SUM: batch_dispatch_tier<MODE, PRIV, F_SUM>(bs, rp, ts, s0, cnt); break;
+    case F_GAUSS_SYM: batch_dispatch_tier<MODE, PRIV, F_GAUSS_SYM>(bs, rp, ts, s0, cnt); break;
+    case F_GENZ_OSC: batch_dispatch_tier<MODE, PRIV, F_GENZ_OSC>(bs, rp, ts, s0, cnt); break;
+    case F_GENZ_GAUSS: batch_dispatch_tier<MODE, PRIV, F_GENZ_GAUSS>(bs, rp, ts, s0, cnt); break;
+    case F_GENZ_PROD: batch_dispatch_tier<MODE, PRIV, F_GENZ_PROD>(bs, rp, ts, s0, cnt); break;
+    case F_GENZ_CORNER: batch_dispatch_tier<MODE, PRIV, F_GENZ_CORNER>(bs, rp, ts, s0, cnt); break;
+    case F_LO: batch_dispatch_tier<MODE, PRIV, F_LO>(bs, rp, ts, s0, cnt); break;
+    default: break;
+    }
+}
+
+template <int MODE, int PRIV>
+__global__ void __launch_bounds__(kBatchThreads, 1)
 batch_sample_kernel_t(const BatchArgs ba) {
     using BS = BlockState<MODE, PRIV>;
     using T = typename BS::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ FamConsts<T> fc_s;
+    FamConsts<T> &fc_s = batch_fc<T>();
     __shared__ long long s_tile;
     __shared__ int s_item;
     const PlanHeader hdr = *ba.hdr;
@@ -62,6 +116,8 @@ batch_sample_kernel_t(const BatchArgs ba) {
     int cur = -1;
     int fam = 0;
     long long n_cur = 0;
+    long long cap = 0;     // samples between flushes of the fixed-point cells
+    long long since = 0;   // samples added since the last flush
     SlotDev *sd = nullptr;
     for (;;) {
         if (threadIdx.x == 0) {
@@ -98,6 +154,8 @@ batch_sample_kernel_t(const BatchArgs ba) {
             rp.hs = MODE != ACC_F64 ? sd->hscale : 0.f;
             rp.acc = sd->acc;
             n_cur = sd->n;
+            cap = block_sample_cap<MODE, PRIV>(rp.N);
+            since = 0;
             const FamConsts<T> *src;
             if (MODE == ACC_F64) src = reinterpret_cast<const FamConsts<T> *>(&sd->fc64);
             else src = reinterpret_cast<const FamConsts<T> *>(&sd->fc32);
@@ -110,21 +168,21 @@ batch_sample_kernel_t(const BatchArgs ba) {
             __syncthreads();
             cur = item;
         }
-        const long long s0 = (tile - ba.tile_prefix[item]) * static_cast<long long>(hdr.tile_samples);
-        const int cnt = static_cast<int>(min(static_cast<long long>(hdr.tile_samples), n_cur - s0));
-        if (cnt > 0) {
-            const unsigned long long u0 = static_cast<unsigned long long>(s0);
-            switch (fam) {
-            case F_CONST: batch_dispatch_tier<MODE, PRIV, F_CONST>(bs, rp, &fc_s, ts, u0, cnt); break;
-            case F_SUM: batch_dispatch_tier<MODE, PRIV, F_SUM>(bs, rp, &fc_s, ts, u0, cnt); break;
-            case F_GAUSS_SYM: batch_dispatch_tier<MODE, PRIV, F_GAUSS_SYM>(bs, rp, &fc_s, ts, u0, cnt); break;
-            case F_GENZ_OSC: batch_dispatch_tier<MODE, PRIV, F_GENZ_OSC>(bs, rp, &fc_s, ts, u0, cnt); break;
-            case F_GENZ_GAUSS: batch_dispatch_tier<MODE, PRIV, F_GENZ_GAUSS>(bs, rp, &fc_s, ts, u0, cnt); break;
-            case F_GENZ_PROD: batch_dispatch_tier<MODE, PRIV, F_GENZ_PROD>(bs, rp, &fc_s, ts, u0, cnt); break;
-            case F_GENZ_CORNER: batch_dispatch_tier<MODE, PRIV, F_GENZ_CORNER>(bs, rp, &fc_s, ts, u0, cnt); break;
-            case F_LO: batch_dispatch_tier<MODE, PRIV, F_LO>(bs, rp, &fc_s, ts, u0, cnt); break;
-            default: break;
+        long long s0 = (tile - ba.tile_prefix[item]) * static_cast<long long>(hdr.tile_samples);
+        long long cnt = min(static_cast<long long>(hdr.tile_samples), n_cur - s0);
+        while (cnt > 0) {
+            if (MODE != ACC_F64 && since >= cap) {
+                // the cells are full: add them to the slot's sums and restart
+                flush_block<MODE, PRIV>(bs, ts, rp.hs, sd->acc, &sd->nonfinite);
+                bs.clear();
+                __syncthreads();
+                since = 0;
             }
+            const long long part = MODE != ACC_F64 ? min(cnt, cap - since) : cnt;
+            batch_dispatch<MODE, PRIV>(fam, bs, rp, ts, static_cast<unsigned long long>(s0), static_cast<int>(part));
+            s0 += part;
+            cnt -= part;
+            since += part;
         }
         __syncthreads();  // s_tile / s_item are rewritten by the next claim
     }

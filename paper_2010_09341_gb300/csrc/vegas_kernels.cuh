@@ -45,7 +45,13 @@ const void *sample_kernel(int mode, int fam, int d, bool priv);
 
 inline int tier_of(int d) { return d <= 4 ? 0 : (d <= 8 ? 1 : (d <= 16 ? 2 : 3)); }
 
-size_t sample_smem(int mode, bool priv, int d, int N);
+// Shared memory of one sampling block in layout 0 (one copy per cell), 1
+// (lane-private copies) or 2 (half as many copies).
+size_t sample_smem(int mode, int layout, int d, int N);
+
+// FP32 modes: samples one block may add to its fixed-point histogram cells
+// between flushes (layout as above).
+long long block_samples_max(int mode, int layout, int N);
 
 // Finalize: move the accumulators (unscaled) to `last`, zero them, form
 // I_t and sigma_t, store the record, update the combination and the scales

@@ -11,8 +11,10 @@
 // Shared memory holds, per (dimension, bin) cell, TP copies of the table
 // entry (e - w, w) and HP copies of the histogram cell, so that the 32 lanes
 // of a warp read and update distinct banks whatever bins they draw
-// (lane-private copies).  When the copies do not fit, a single-copy layout is
-// used (PRIV = false) and bank conflicts are accepted.
+// (lane-private copies).  Layouts (template parameter PRIV): 1 = TP and HP
+// copies as above, 2 = half as many (two lanes share a copy: some two-way
+// conflicts, half the memory), 0 = one copy (conflicts accepted) for what
+// fits neither.
 #pragma once
 
 #include "vegas_device.cuh"
@@ -61,9 +63,8 @@ template <> __device__ __forceinline__ const FamConsts<float> &consts<float>(con
 //            accumulator in global memory.
 // The lane's choice of cell array is a select, not a branch, so a warp whose
 // lanes mix coarse and fine values still issues one atomic per dimension.
-// Capacity: a coarse cell receives ~64 values on average per block (the
-// launch keeps block samples <= 2048 N; 512 values would be needed to reach
-// 2^32); a fine cell at most 2048 N values below 2^16.  With S = 0 (first
+// Capacity: a block adds at most block_sample_cap(N) samples between flushes
+// (below), so that no cell can reach 2^32.  With S = 0 (first
 // iteration) the lane-private cells hold FP32 and take every value.  Zero
 // weights touch no cell.
 constexpr float kFineScale = 65536.0f;    // 2^16
@@ -90,12 +91,29 @@ template <> struct ModeTraits<ACC_F32_KAHAN> {
     static constexpr int HP = 32;   // 4-byte cells: a whole warp per wavefront
 };
 
-template <int MODE, bool PRIV>
+// Copies per (dimension, bin) cell of the table entry (TP) and of the
+// histogram cell (HP) in layout PRIV (0, 1 or 2).
+template <int MODE, int PRIV> struct Copies {
+    static constexpr int TP = PRIV == 0 ? 1 : (PRIV == 1 ? ModeTraits<MODE>::TP : ModeTraits<MODE>::TP / 2);
+    static constexpr int HP = PRIV == 0 ? 1 : (PRIV == 1 ? ModeTraits<MODE>::HP : ModeTraits<MODE>::HP / 2);
+};
+
+template <int MODE, int PRIV>
 __host__ __device__ constexpr size_t sample_smem_bytes(int d, int N) {
     using Tr = ModeTraits<MODE>;
     return static_cast<size_t>(d) * N *
-           ((PRIV ? Tr::TP : 1) * 2 * sizeof(typename Tr::T) + (PRIV ? Tr::HP : 1) * sizeof(typename Tr::H) +
+           (Copies<MODE, PRIV>::TP * 2 * sizeof(typename Tr::T) + Copies<MODE, PRIV>::HP * sizeof(typename Tr::H) +
             (MODE != ACC_F64 ? sizeof(uint32_t) : 0));  // single-copy fine cells
+}
+
+// Samples one block may add to its fixed-point cells between two flushes:
+// every bin is drawn with probability 1/N, so a coarse cell copy receives 64
+// values on average, far below the 512 values at the largest coarse value
+// (2^23) that would reach 2^32; a fine cell (one copy, values below 2^16)
+// receives 64 HP on average.
+constexpr long long kValuesPerCopy = 64;
+template <int MODE, int PRIV> __host__ __device__ constexpr long long block_sample_cap(int N) {
+    return kValuesPerCopy * N * Copies<MODE, PRIV>::HP;
 }
 
 __device__ __forceinline__ void red_add_shared(float *p, float v) { atomicAdd(p, v); }
@@ -144,13 +162,13 @@ __device__ __forceinline__ double warp_sum(double v) {
 // Shared-memory working set of one block for one integral: the table (TP
 // copies per cell), the coarse histogram cells (HP copies per cell) and, in
 // the FP32 modes, one fine cell per (dimension, bin).
-template <int MODE, bool PRIV> struct BlockState {
+template <int MODE, int PRIV> struct BlockState {
     using Tr = ModeTraits<MODE>;
     using T = typename Tr::T;
     using T2 = typename Prec<T>::T2;
     using H = typename Tr::H;
-    static constexpr int TP = PRIV ? Tr::TP : 1;
-    static constexpr int HP = PRIV ? Tr::HP : 1;
+    static constexpr int TP = Copies<MODE, PRIV>::TP;
+    static constexpr int HP = Copies<MODE, PRIV>::HP;
     T2 *tab;
     H *hist;
     uint32_t *fine;
@@ -166,6 +184,10 @@ template <int MODE, bool PRIV> struct BlockState {
     __device__ __forceinline__ void stage(const void *gtable) {
         const T2 *g = static_cast<const T2 *>(gtable);
         for (int k = threadIdx.x; k < cells * TP; k += blockDim.x) tab[k] = g[k / TP];
+        clear();
+    }
+    // Zeroes the histogram cells (every thread calls; the caller synchronises).
+    __device__ __forceinline__ void clear() {
         for (int k = threadIdx.x; k < cells * HP; k += blockDim.x) hist[k] = H(0);
         if (MODE != ACC_F64)
             for (int k = threadIdx.x; k < cells; k += blockDim.x) fine[k] = 0u;
@@ -193,7 +215,7 @@ template <class T> struct RangeParams {
 // chunk's FP32 partial sums into the FP64 sums once per chunk).
 // EXACT: the dimension equals MAXD (no per-dimension guards); otherwise
 // 1 <= rp.d <= MAXD at run time.
-template <int FAM, int MODE, int MAXD, bool EXACT, bool PRIV>
+template <int FAM, int MODE, int MAXD, bool EXACT, int PRIV>
 __device__ __forceinline__ void sample_range(const BlockState<MODE, PRIV> &bs,
                                              const RangeParams<typename ModeTraits<MODE>::T> &rp,
                                              const FamConsts<typename ModeTraits<MODE>::T> &fc,
@@ -217,8 +239,9 @@ __device__ __forceinline__ void sample_range(const BlockState<MODE, PRIV> &bs,
     const int stride = blockDim.x;
     for (int k0 = threadIdx.x; k0 < cnt; k0 += kChunk * stride) {
         float p1 = 0.f, p2 = 0.f;
-        // two samples in flight: their Philox and table-load chains interleave
-#pragma unroll 2
+        // two samples in flight (their Philox and table-load chains
+        // interleave), one above 16 dimensions (register budget)
+#pragma unroll(MAXD > 16 ? 1 : 2)
         for (int u = 0; u < kChunk; ++u) {
             const int k = k0 + u * stride;
             if (k >= cnt) break;
@@ -320,7 +343,7 @@ __device__ __forceinline__ void sample_range(const BlockState<MODE, PRIV> &bs,
 // (FP32 cells summed as a warp tree, 5 levels, then promoted once).  Starts
 // with a barrier (every thread's samples are in) and ends with one (the
 // shared cells may be reused).  Resets ts.
-template <int MODE, bool PRIV>
+template <int MODE, int PRIV>
 __device__ __forceinline__ void flush_block(const BlockState<MODE, PRIV> &bs, ThreadSums<MODE> &ts,
                                             float hs, double *acc, unsigned long long *n_nonfinite) {
     using BS = BlockState<MODE, PRIV>;
