@@ -266,7 +266,8 @@ def _time_batched(V, torch, steps=8, warm=2):
     for _ in range(warm):
         b.step()
         b.wait()
-    best, ms = b.autotune([4096, 8192, 16384, 32768, 65536], reps=2)
+    cands = [16384, 32768, 65536, 131072, 262144, 524288]
+    best, ms = b.autotune(cands, reps=2)
     b.step()
     b.wait()
     t0 = time.perf_counter()
@@ -276,12 +277,25 @@ def _time_batched(V, torch, steps=8, warm=2):
     dt = time.perf_counter() - t0
     n_total = sum(it.n_events for it in mix)
     b.close()
+    # issue roofline of one step: every integral's samples at its own bound
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    roof_s = 0.0
+    for it in mix:
+        bounds = roofline_samples_per_s(ops_per_sample(it.family, it.d, "fp32_kahan"), sms, 2070e6)
+        roof_s += it.n_events / min(bounds.values())
+    ms_step = 1e3 * dt / steps
     return {"workload": "512 integrals, d ~ U{2..16}, Genz gauss/prod/corner, c ~ U(0.5,5), "
                         "n ~ logU(1e4,1e7) per iteration, 50 bins, FP32 Kahan, seed 2",
-            "samples_per_step": n_total, "steps": steps, "ms_per_step": 1e3 * dt / steps,
+            "samples_per_step": n_total, "steps": steps, "ms_per_step": ms_step,
+            "roofline": {"bound": "alu", "roofline_ms_per_step": 1e3 * roof_s,
+                         "roofline_samples_per_s": n_total / roof_s,
+                         "frac": 1e3 * roof_s / ms_step,
+                         "basis": "sum over the 512 integrals of n / (issue bound of its family and d) "
+                                  "at %d SMs x 2070 MHz; the step time includes finalize, refinement "
+                                  "and the graph's plan upload and result download" % sms},
             "samples_per_s": n_total * steps / dt,
             "integral_iterations_per_s": 512 * steps / dt,
-            "tile_samples": best, "autotune_ms": dict(zip(["4096", "8192", "16384", "32768", "65536"], ms)),
+            "tile_samples": best, "autotune_ms": dict(zip([str(c) for c in cands], ms)),
             "timing": "wall clock per step incl. graph launch and result download"}
 
 

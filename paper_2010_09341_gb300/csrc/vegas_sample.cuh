@@ -210,12 +210,28 @@ template <class T> struct RangeParams {
     double *acc;     // FP64 accumulators [2 + d N] (values beyond the fixed range)
 };
 
+// Cell indices of one sample's dimensions, one per register or, with PACK,
+// two 16-bit indices per register (d N <= 32768): half the registers for one
+// more operation per dimension.
+template <int MAXD, bool PACK> struct SampleCells {
+    uint32_t c[PACK ? (MAXD + 1) / 2 : MAXD];
+    __device__ __forceinline__ void set(int j, uint32_t cell) {
+        if (!PACK) c[j] = cell;
+        else if (j & 1) c[j >> 1] = __byte_perm(c[j >> 1], cell, 0x5410);
+        else c[j >> 1] = cell;
+    }
+    __device__ __forceinline__ uint32_t get(int j) const {
+        if (!PACK) return c[j];
+        return (j & 1) ? (c[j >> 1] >> 16) : (c[j >> 1] & 0xFFFFu);
+    }
+};
+
 // The block samples [s0, s0 + cnt) of one integral: thread t takes
 // s0 + t + u * blockDim, in chunks of kChunk samples (ACC_F32_SUM64 adds a
 // chunk's FP32 partial sums into the FP64 sums once per chunk).
 // EXACT: the dimension equals MAXD (no per-dimension guards); otherwise
-// 1 <= rp.d <= MAXD at run time.
-template <int FAM, int MODE, int MAXD, bool EXACT, int PRIV>
+// 1 <= rp.d <= MAXD at run time.  PACK: 16-bit cell indices (SampleCells).
+template <int FAM, int MODE, int MAXD, bool EXACT, int PRIV, bool PACK = false>
 __device__ __forceinline__ void sample_range(const BlockState<MODE, PRIV> &bs,
                                              const RangeParams<typename ModeTraits<MODE>::T> &rp,
                                              const FamConsts<typename ModeTraits<MODE>::T> &fc,
@@ -247,7 +263,7 @@ __device__ __forceinline__ void sample_range(const BlockState<MODE, PRIV> &bs,
             if (k >= cnt) break;
             const unsigned long long s = s0 + static_cast<unsigned long long>(k);
             const uint32_t slo = static_cast<uint32_t>(s), shi = static_cast<uint32_t>(s >> 32);
-            uint32_t cellj[MAXD];
+            SampleCells<MAXD, PACK> cellj;
             T J = rp.jinit;
             fam.begin(fc);
 #pragma unroll
@@ -266,7 +282,7 @@ __device__ __forceinline__ void sample_range(const BlockState<MODE, PRIV> &bs,
                             const T x = ffma(ent.y, m, ent.x);
                             J *= ent.y;
                             if (sizeof(T) == 4 && (j & 3) == 3) J *= rp.n4;
-                            cellj[j] = cell;
+                            cellj.set(j, cell);
                             fam.dim(j, x, fc);
                         }
                     }
@@ -298,7 +314,7 @@ __device__ __forceinline__ void sample_range(const BlockState<MODE, PRIV> &bs,
             if (MODE == ACC_F64) {
 #pragma unroll
                 for (int j = 0; j < MAXD; ++j) {
-                    if (EXACT || j < d) red_add_shared(hist_l + cellj[j] * HP, static_cast<H>(v2));
+                    if (EXACT || j < d) red_add_shared(hist_l + cellj.get(j) * HP, static_cast<H>(v2));
                 }
             } else if (v2 == T(0)) {
                 // nothing to add
@@ -315,18 +331,18 @@ __device__ __forceinline__ void sample_range(const BlockState<MODE, PRIV> &bs,
                     const uint32_t step = is_fine ? 1u : static_cast<uint32_t>(HP);
 #pragma unroll
                     for (int j = 0; j < MAXD; ++j) {
-                        if (EXACT || j < d) atomicAdd(base + cellj[j] * step, q);
+                        if (EXACT || j < d) atomicAdd(base + cellj.get(j) * step, q);
                     }
                 } else {
 #pragma unroll
                     for (int j = 0; j < MAXD; ++j) {
-                        if (EXACT || j < d) atomicAdd(rp.acc + 2 + cellj[j], static_cast<double>(v2));
+                        if (EXACT || j < d) atomicAdd(rp.acc + 2 + cellj.get(j), static_cast<double>(v2));
                     }
                 }
             } else {
 #pragma unroll
                 for (int j = 0; j < MAXD; ++j) {
-                    if (EXACT || j < d) red_add_shared(reinterpret_cast<float *>(hist_l) + cellj[j] * HP,
+                    if (EXACT || j < d) red_add_shared(reinterpret_cast<float *>(hist_l) + cellj.get(j) * HP,
                                                        static_cast<float>(v2));
                 }
             }
