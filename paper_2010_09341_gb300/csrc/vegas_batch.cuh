@@ -72,8 +72,8 @@ struct BatchArgs {
 
 // Threads per block of the persistent sampling kernel: one block per SM, 24
 // warps, up to 80 registers a thread.  (Measured on the 512-integral mix:
-// 512 threads 13.7 ms per step, 640 12.9, 768 12.5, 896 12.6, 1024 14.0 --
-// above 768 the out-of-line samplers spill.)
+// 640 threads 10.78 ms per step, 768 10.64, 896 10.73, 1024 11.11 -- with
+// fewer registers the out-of-line samplers spill.)
 constexpr int kBatchThreads = 768;
 
 // The batched sampling kernel of one mode and shared-memory layout (1 =

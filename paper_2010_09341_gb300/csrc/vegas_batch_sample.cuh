@@ -22,7 +22,7 @@ template <class T> __device__ __forceinline__ FamConsts<T> &batch_fc();
 template <> __device__ __forceinline__ FamConsts<float> &batch_fc<float>() { return g_batch_fc32; }
 template <> __device__ __forceinline__ FamConsts<double> &batch_fc<double>() { return g_batch_fc64; }
 
-// One range of one slot.  Kept out of line: each (family, dimension tier)
+// One range of one slot.  Kept out of line: each (family, dimension)
 // variant gets its own register allocation instead of the union of all of
 // them.  Arguments are scalars (passed in registers; a structure argument
 // would live in memory and be re-read in the loop); the running sums are
@@ -62,20 +62,35 @@ __device__ __forceinline__ void batch_call(const BlockState<MODE, PRIV> &bs,
                                               rp.jinit, rp.n4, rp.hs, rp.acc, s0, cnt, &ts);
 }
 
+// Dimensions 1..16 get a sampler each (no per-dimension guards or branches:
+// 12.5 -> 10.6 ms per step of the 512-integral mix against four dimension
+// tiers); 17..32 share the generic one.
 template <int MODE, int PRIV, int FAM>
-__device__ __forceinline__ void batch_dispatch_tier(const BlockState<MODE, PRIV> &bs,
+__device__ __forceinline__ void batch_dispatch_dim(const BlockState<MODE, PRIV> &bs,
                                                     const RangeParams<typename ModeTraits<MODE>::T> &rp,
                                                     ThreadSums<MODE> &ts, unsigned long long s0, int cnt) {
     if (FAM == F_LO) {
         batch_call<MODE, PRIV, FAM, 3, true>(bs, rp, ts, s0, cnt);
-    } else if (rp.d <= 4) {
-        batch_call<MODE, PRIV, FAM, 4, false>(bs, rp, ts, s0, cnt);
-    } else if (rp.d <= 8) {
-        batch_call<MODE, PRIV, FAM, 8, false>(bs, rp, ts, s0, cnt);
-    } else if (rp.d <= 16) {
-        batch_call<MODE, PRIV, FAM, 16, false>(bs, rp, ts, s0, cnt);
-    } else {
-        batch_call<MODE, PRIV, FAM, 32, false>(bs, rp, ts, s0, cnt);
+        return;
+    }
+    switch (rp.d) {
+    case 1: batch_call<MODE, PRIV, FAM, 1, true>(bs, rp, ts, s0, cnt); break;
+    case 2: batch_call<MODE, PRIV, FAM, 2, true>(bs, rp, ts, s0, cnt); break;
+    case 3: batch_call<MODE, PRIV, FAM, 3, true>(bs, rp, ts, s0, cnt); break;
+    case 4: batch_call<MODE, PRIV, FAM, 4, true>(bs, rp, ts, s0, cnt); break;
+    case 5: batch_call<MODE, PRIV, FAM, 5, true>(bs, rp, ts, s0, cnt); break;
+    case 6: batch_call<MODE, PRIV, FAM, 6, true>(bs, rp, ts, s0, cnt); break;
+    case 7: batch_call<MODE, PRIV, FAM, 7, true>(bs, rp, ts, s0, cnt); break;
+    case 8: batch_call<MODE, PRIV, FAM, 8, true>(bs, rp, ts, s0, cnt); break;
+    case 9: batch_call<MODE, PRIV, FAM, 9, true>(bs, rp, ts, s0, cnt); break;
+    case 10: batch_call<MODE, PRIV, FAM, 10, true>(bs, rp, ts, s0, cnt); break;
+    case 11: batch_call<MODE, PRIV, FAM, 11, true>(bs, rp, ts, s0, cnt); break;
+    case 12: batch_call<MODE, PRIV, FAM, 12, true>(bs, rp, ts, s0, cnt); break;
+    case 13: batch_call<MODE, PRIV, FAM, 13, true>(bs, rp, ts, s0, cnt); break;
+    case 14: batch_call<MODE, PRIV, FAM, 14, true>(bs, rp, ts, s0, cnt); break;
+    case 15: batch_call<MODE, PRIV, FAM, 15, true>(bs, rp, ts, s0, cnt); break;
+    case 16: batch_call<MODE, PRIV, FAM, 16, true>(bs, rp, ts, s0, cnt); break;
+    default: batch_call<MODE, PRIV, FAM, 32, false>(bs, rp, ts, s0, cnt); break;
     }
 }
 
@@ -84,14 +99,14 @@ __device__ __forceinline__ void batch_dispatch(int fam, const BlockState<MODE, P
                                                const RangeParams<typename ModeTraits<MODE>::T> &rp,
                                                ThreadSums<MODE> &ts, unsigned long long s0, int cnt) {
     switch (fam) {
-    case F_CONST: batch_dispatch_tier<MODE, PRIV, F_CONST>(bs, rp, ts, s0, cnt); break;
-    case F_SUM: batch_dispatch_tier<MODE, PRIV, F_SUM>(bs, rp, ts, s0, cnt); break;
-    case F_GAUSS_SYM: batch_dispatch_tier<MODE, PRIV, F_GAUSS_SYM>(bs, rp, ts, s0, cnt); break;
-    case F_GENZ_OSC: batch_dispatch_tier<MODE, PRIV, F_GENZ_OSC>(bs, rp, ts, s0, cnt); break;
-    case F_GENZ_GAUSS: batch_dispatch_tier<MODE, PRIV, F_GENZ_GAUSS>(bs, rp, ts, s0, cnt); break;
-    case F_GENZ_PROD: batch_dispatch_tier<MODE, PRIV, F_GENZ_PROD>(bs, rp, ts, s0, cnt); break;
-    case F_GENZ_CORNER: batch_dispatch_tier<MODE, PRIV, F_GENZ_CORNER>(bs, rp, ts, s0, cnt); break;
-    case F_LO: batch_dispatch_tier<MODE, PRIV, F_LO>(bs, rp, ts, s0, cnt); break;
+    case F_CONST: batch_dispatch_dim<MODE, PRIV, F_CONST>(bs, rp, ts, s0, cnt); break;
+    case F_SUM: batch_dispatch_dim<MODE, PRIV, F_SUM>(bs, rp, ts, s0, cnt); break;
+    case F_GAUSS_SYM: batch_dispatch_dim<MODE, PRIV, F_GAUSS_SYM>(bs, rp, ts, s0, cnt); break;
+    case F_GENZ_OSC: batch_dispatch_dim<MODE, PRIV, F_GENZ_OSC>(bs, rp, ts, s0, cnt); break;
+    case F_GENZ_GAUSS: batch_dispatch_dim<MODE, PRIV, F_GENZ_GAUSS>(bs, rp, ts, s0, cnt); break;
+    case F_GENZ_PROD: batch_dispatch_dim<MODE, PRIV, F_GENZ_PROD>(bs, rp, ts, s0, cnt); break;
+    case F_GENZ_CORNER: batch_dispatch_dim<MODE, PRIV, F_GENZ_CORNER>(bs, rp, ts, s0, cnt); break;
+    case F_LO: batch_dispatch_dim<MODE, PRIV, F_LO>(bs, rp, ts, s0, cnt); break;
     default: break;
     }
 }
