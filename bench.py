@@ -35,11 +35,12 @@ D, NBINS, NEVENTS, ALPHA = 8, 50, 10_000_000, 1.5
 PRECISION = "fp32_acc64"
 WORKLOAD = "d=8 Gaussian a=0.1 + d=8 Genz oscillatory (c~U(0,1) seed 1), 50 bins, 1e7 samples/iter each, FP32 sampling, FP64 accumulators"
 
-# Nominal unit counts used for the issue roofline (derived, per SM per clock).
+# Unit counts used for the issue roofline (per SM per clock); the measured
+# costs come from paper_2010_09341_gb300/calib/pipe_costs.cu.
 ISSUE_PER_SM_CLK = 128.0      # 4 schedulers x 32 lanes: one warp instruction each per clock
-MUFU_PER_SM_CLK = 16.0        # special-function lanes
-MULWIDE_ISSUE_CYCLES = 4.0    # a 32x32->64 multiply holds its scheduler for 4 cycles (measured)
-FP64_TFLOPS_NOMINAL = 1.25    # GB300 dense FP64 (FMA = 2 flop)
+MUFU_PER_SM_CLK = 32.0        # special-function lanes (ex2.approx measured at 4 cycles/warp/scheduler)
+MULWIDE_ISSUE_CYCLES = 4.0    # a 32x32->64 multiply holds its scheduler for 4 cycles (measured 4.05)
+FP64_TFLOPS_NOMINAL = 1.25    # GB300 dense FP64 (FMA = 2 flop); measured DFMA rate gives 1.06
 
 
 def _integrals():
@@ -93,10 +94,13 @@ def roofline_samples_per_s(ops, sms: int, clk_hz: float) -> dict:
 
     "issue": every operation costs one issue slot of a scheduler (4 per SM,
     32 lanes each), except a 32x32->64 multiply, which occupies its
-    scheduler for 4 cycles and issues nothing else meanwhile (measured: a
-    multiply chain interleaved with independent FMAs takes the sum of the two
-    times, and one multiply-and-xor step costs 5.3 cycles).  The other pipes
-    bound separately: FP64 at the nominal 1.25 TFLOP/s, MUFU 16 lanes/clk/SM.
+    scheduler for 4 cycles and issues nothing else meanwhile (measured:
+    mul.hi 4.05 cycles per warp instruction; a multiply-and-xor chain
+    interleaved with two independent FMAs takes the sum of the two times).
+    Half-rate integer operations (three-input logic, 32-bit multiply-add:
+    2 cycles measured) are charged one slot, so the bound is optimistic for
+    them.  The other pipes bound separately: FP64 at the nominal 1.25
+    TFLOP/s, MUFU 32 lanes/clk/SM.
     """
     fp64_per_sm_clk = FP64_TFLOPS_NOMINAL * 1e12 / 2.0 / (sms * clk_hz)
     cycles = (ops["total"] - ops.get("mulwide", 0)) + MULWIDE_ISSUE_CYCLES * ops.get("mulwide", 0)
@@ -463,7 +467,7 @@ def main():
     roofline = {"bound": "alu", "achieved": achieved_gops, "peak": peak_gops, "unit": "Gop/s",
                 "frac": achieved_gops / peak_gops, "traffic": _traffic_from_profile(),
                 "kernel": "vegas_sample_kernel", "peak_basis":
-                "min over pipes: issue 128 slots/clk/SM with a 32x32->64 multiply costing 4 slots, FP64 %.2f TFLOP/s, MUFU 16/clk/SM; %d SMs x %.0f MHz (max clock)"
+                "min over pipes: issue 128 slots/clk/SM with a 32x32->64 multiply costing 4 slots, FP64 %.2f TFLOP/s, MUFU 32/clk/SM; %d SMs x %.0f MHz (max clock)"
                 % (FP64_TFLOPS_NOMINAL, sms, clk_max_hz / 1e6), "per_integral": per_fam}
 
     # ---- end to end through the public API with host buffers
