@@ -21,18 +21,20 @@ constexpr int kThreads = 1024;
 
 enum Kind : int {
     K_FFMA, K_IADD, K_LOP3, K_IMAD, K_MULHI, K_MULWIDE_XOR, K_MULWIDE_XOR_2FFMA, K_FFMA_LOP3,
-    K_ATOMS_U32, K_ATOMS_F32, K_DFMA, K_EX2, K_COUNT
+    K_ATOMS_U32, K_ATOMS_F32, K_ATOMS_F64, K_DFMA, K_EX2, K_EXP64, K_COUNT
 };
 
 template <int V>
 __global__ void __launch_bounds__(kThreads) chains(unsigned long long *cycles, unsigned *sink, unsigned seed) {
     __shared__ unsigned cells_u[32 * 8];
     __shared__ float cells_f[32 * 8];
+    __shared__ double cells_d[32 * 8];
     const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
     const unsigned lane = threadIdx.x & 31;
     if (threadIdx.x < 32 * 8) {
         cells_u[threadIdx.x] = 0u;
         cells_f[threadIdx.x] = 0.f;
+        cells_d[threadIdx.x] = 0.0;
     }
     unsigned x[8];
     float f[8];
@@ -75,6 +77,10 @@ __global__ void __launch_bounds__(kThreads) chains(unsigned long long *cycles, u
                 atomicAdd(&cells_u[c * 32 + lane], x[c]);  // lane-private: bank = lane
             } else if (V == K_ATOMS_F32) {
                 atomicAdd(&cells_f[c * 32 + lane], f[c]);
+            } else if (V == K_ATOMS_F64) {
+                atomicAdd(&cells_d[c * 32 + lane], g[c]);
+            } else if (V == K_EXP64) {
+                g[c] = exp(-g[c]);  // stays in (0.3, 1]: converges to 0.567
             } else if (V == K_DFMA) {
                 asm volatile("fma.rn.f64 %0, %0, 0d3FEFFFFFDE7210BE, 0d3E7AD7F29ABCAF48;" : "+d"(g[c]));
             } else if (V == K_EX2) {
@@ -87,7 +93,8 @@ __global__ void __launch_bounds__(kThreads) chains(unsigned long long *cycles, u
     unsigned r = 0;
 #pragma unroll
     for (int c = 0; c < 8; ++c) r += x[c] + __float_as_uint(f[c]) + static_cast<unsigned>(g[c] * 1e3);
-    if (threadIdx.x < 32 * 8) r += cells_u[threadIdx.x] + __float_as_uint(cells_f[threadIdx.x]);
+    if (threadIdx.x < 32 * 8)
+        r += cells_u[threadIdx.x] + __float_as_uint(cells_f[threadIdx.x]) + static_cast<unsigned>(cells_d[threadIdx.x]);
     sink[t] = r;
     if (threadIdx.x == 0) cycles[blockIdx.x] = c1 - c0;
 }
@@ -121,8 +128,10 @@ int main() {
         {"ffma + lop3", 2, chains<K_FFMA_LOP3>},
         {"shared atomic add u32", 1, chains<K_ATOMS_U32>},
         {"shared atomic add f32", 1, chains<K_ATOMS_F32>},
+        {"shared atomic add f64", 1, chains<K_ATOMS_F64>},
         {"dfma", 1, chains<K_DFMA>},
         {"ex2.approx", 1, chains<K_EX2>},
+        {"exp (double, one call)", 1, chains<K_EXP64>},
     };
     unsigned long long *h = new unsigned long long[blocks];
     int rc = 0;

@@ -375,9 +375,12 @@ static SampleArgs make_args(const vegas_ctx *c, long long s_begin, long long n, 
 
 static vegas_status launch_sampling(vegas_ctx *c, long long s_begin, long long n) {
     SampleArgs a = make_args(c, s_begin, n, c->t);
-    // a few samples per thread at least; otherwise fill every SM
-    const long long want = (n + static_cast<long long>(c->threads) * 4 - 1) /
-                           (static_cast<long long>(c->threads) * 4);
+    // a few samples per thread at least (FP32 modes: 4; FP64: 1, a sample
+    // costs tens of cycles of the narrow FP64 pipe, which every SM should
+    // contribute); otherwise fill every SM
+    const long long per_thread = c->mode == ACC_F64 ? 1 : 4;
+    const long long want = (n + static_cast<long long>(c->threads) * per_thread - 1) /
+                           (static_cast<long long>(c->threads) * per_thread);
     long long blocks = std::max(1LL, std::min<long long>(c->max_blocks, want));
     if (c->mode != ACC_F64) {
         // fixed-point histogram cells: a bounded number of samples per block
