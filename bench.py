@@ -355,7 +355,7 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the other workloads")
-    ap.add_argument("--only", choices=["batched", "serving", "lo"], default=None,
+    ap.add_argument("--only", choices=["batched", "serving", "lo", "config1"], default=None,
                     help="run just one of the other workloads and print its JSON (for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -377,6 +377,9 @@ def main():
         B.build()
         if args.only == "batched":
             out = _time_batched(V, torch, steps=args.steps, warm=args.warmup)
+        elif args.only == "config1":
+            out = _time_single(V, torch, "gauss_sym", W.gauss_sym_params(0.1), 4, 50, 100_000, "fp64",
+                               args.steps, warm=args.warmup)
         elif args.only == "lo":
             out = _time_single(V, torch, "lo", W.lo_params(), 3, 100, 100_000_000, "fp32_kahan",
                                args.steps, warm=args.warmup)

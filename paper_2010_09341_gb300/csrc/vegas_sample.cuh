@@ -356,8 +356,7 @@ __device__ __forceinline__ void sample_range(const BlockState<MODE, PRIV> &bs,
 }
 
 // Adds the block's sums to the integral's FP64 accumulators: S1, S2 and the
-// non-finite count by a block reduction, each histogram cell by one warp
-// (FP32 cells summed as a warp tree, 5 levels, then promoted once).  Starts
+// non-finite count by a block reduction, each histogram cell by one thread.  Starts
 // with a barrier (every thread's samples are in) and ends with one (the
 // shared cells may be reused).  Resets ts.
 template <int MODE, int PRIV>
@@ -402,21 +401,33 @@ __device__ __forceinline__ void flush_block(const BlockState<MODE, PRIV> &bs, Th
             if (xn) atomicAdd(n_nonfinite, static_cast<unsigned long long>(xn));
         }
     }
+    // One thread per cell sums the cell's HP copies, reading them from copy
+    // c mod HP on so that the lanes of a warp touch distinct banks.
+    // Fixed-point copies (and the fine cell) are summed exactly as integers
+    // and scaled once; floating-point copies pairwise.
     const bool fixed = hs > 0.f;
-    const float inv_hs = fixed ? 1.0f / hs : 0.f;
-    for (int c = warp; c < bs.cells; c += nwarps) {
-        H h = H(0);
-        for (int k = lane; k < HP; k += 32) {
-            if (MODE != ACC_F64 && fixed)
-                h += static_cast<H>(static_cast<float>(reinterpret_cast<const unsigned int *>(bs.hist)[c * HP + k]) * inv_hs);
-            else
-                h += bs.hist[c * HP + k];
-        }
+    const double inv_hs = fixed ? 1.0 / static_cast<double>(hs) : 0.0;
+    for (int c = threadIdx.x; c < bs.cells; c += blockDim.x) {
+        double h;
+        if (MODE != ACC_F64 && fixed) {
+            const unsigned int *hu = reinterpret_cast<const unsigned int *>(bs.hist) + c * HP;
+            unsigned long long q = 0;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(0xFFFFFFFFu, h, o);
-        if (MODE != ACC_F64 && fixed && lane == 0)
-            h += static_cast<H>(static_cast<float>(bs.fine[c]) * (inv_hs * kFineInv));
-        if (lane == 0 && h != H(0)) atomicAdd(acc + 2 + c, static_cast<double>(h));
+            for (int k = 0; k < HP; ++k) q += hu[(k + c) & (HP - 1)];
+            h = static_cast<double>(q) * inv_hs + static_cast<double>(bs.fine[c]) * (inv_hs * kFineInv);
+        } else {
+            // pairwise: the rounding of a tree of log2(HP) levels
+            const H *hc = bs.hist + c * HP;
+            H a[HP];
+#pragma unroll
+            for (int k = 0; k < HP; ++k) a[k] = hc[(k + c) & (HP - 1)];
+#pragma unroll
+            for (int w = HP / 2; w >= 1; w >>= 1)
+#pragma unroll
+                for (int k = 0; k < w; ++k) a[k] += a[k + w];
+            h = static_cast<double>(a[0]);
+        }
+        if (h != 0.0) atomicAdd(acc + 2 + c, h);
     }
     __syncthreads();
 }
