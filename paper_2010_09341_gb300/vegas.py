@@ -165,9 +165,16 @@ def vegas_run(ctx: Context, n_iter: int):
             "iters": [(x.I, x.sigma, x.n, x.n_nonfinite) for x in its]}
 
 
-def vegas_get_grid(ctx: Context) -> np.ndarray:
+def vegas_get_grid(ctx: Context, out=None) -> np.ndarray:
+    """The grid edges (d, N+1) FP64; into ``out`` (C-contiguous float64, e.g. a
+    pinned buffer's numpy view) when given."""
     d, N = ctx.cfg.n_dim, ctx.cfg.n_bins
-    e = np.zeros((d, N + 1), dtype=np.float64)
+    if out is None:
+        e = np.zeros((d, N + 1), dtype=np.float64)
+    else:
+        e = out
+        if e.dtype != np.float64 or not e.flags["C_CONTIGUOUS"] or e.size != d * (N + 1):
+            raise ValueError("out must be a C-contiguous float64 array of d*(N+1) values")
     check(nat.load().vegas_get_grid(ctx.handle, e.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
           "vegas_get_grid")
     return e
