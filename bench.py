@@ -320,13 +320,23 @@ def _serving(V, rate, n_requests, target, budget, fp64_sample=0):
     srv.batch.close()
     out = {"rate_per_s": rate, "target_rel": target, "budget": budget, **st}
     if fp64_sample:
-        sub = S.requests_from(stream[:fp64_sample], budget=budget, target=target)
-        for r in sub:
-            r.arrival = 0.0
-        st64 = S.serve_single_fp64(sub, time_limit=120)
-        out["fp64_single"] = {"requests": fp64_sample, **st64}
-        out["batched_fp32_vs_fp64_single_integrals_per_s"] = (
-            st["integrals_per_s"] / st64["integrals_per_s"] if st64["integrals_per_s"] else None)
+        # the same first requests, all queued at t = 0, through both forms
+        def queued():
+            sub = S.requests_from(stream[:fp64_sample], budget=budget, target=target)
+            for r in sub:
+                r.arrival = 0.0
+            return sub
+        srv = S.Server(max_slots=1024, pool_bytes=512 << 20)
+        st32 = srv.run(queued(), realtime=False, time_limit=120)
+        srv.batch.close()
+        st64 = S.serve_single_fp64(queued(), time_limit=120)
+        out["same_requests"] = {
+            "requests": fp64_sample, "arrival": "all queued at t = 0",
+            "batched_fp32_kahan": st32, "fp64_single": st64,
+            "integrals_per_s_ratio": (st32["integrals_per_s"] / st64["integrals_per_s"]
+                                      if st64["integrals_per_s"] else None),
+            "converged_per_s_ratio": (st32["converged_per_s"] / st64["converged_per_s"]
+                                      if st64["converged_per_s"] else None)}
     return out
 
 
@@ -391,7 +401,7 @@ def main():
             out = _time_single(V, torch, "lo", W.lo_params(), 3, 100, 100_000_000, "fp32_kahan",
                                args.steps, warm=args.warmup)
         else:
-            out = _serving(V, rate=1000.0, n_requests=1000, target=1e-4, budget=10 ** 9)
+            out = _serving(V, rate=1000.0, n_requests=1000, target=1e-4, budget=10 ** 9, fp64_sample=100)
         print(json.dumps({"only": args.only, **out}))
         return 0
     if world > 1:
@@ -546,7 +556,7 @@ def main():
                                                       100_000_000, "fp32_kahan", 10)
         extra["config4_batched"] = _time_batched(V, torch)
         extra["config5_serving_1e-4"] = _serving(V, rate=1000.0, n_requests=1000, target=1e-4,
-                                                 budget=10 ** 9, fp64_sample=40)
+                                                 budget=10 ** 9, fp64_sample=100)
 
     # ---- CPU baseline: the oracle on this host's cores (rank 0, N = 1)
     cpu = None

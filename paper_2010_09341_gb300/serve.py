@@ -15,7 +15,15 @@ sample budget) arrive over time.  Every loop turn the server
 Samples per iteration: ``n_first`` for the first ``warm_iters`` iterations
 (grid adaptation), then what the target needs from the current estimate,
 n = total_needed / remaining_iterations, rounded up to a power of two and
-kept within [n_first, n_max] and the budget.
+kept within [n_first, n_cap] and the budget, where n_cap = max(n_max,
+step_samples / active integrals): when few integrals are active their
+iterations grow so that a step still fills the GPU.
+
+Give-up rule: from ``give_up_after`` iterations on, an integral whose
+projected total, used * (rel / target)^2, exceeds ``give_up`` times its
+budget is retired unconverged at once instead of spending the rest of the
+budget (the projection assumes the per-sample variance stays as it is; grid
+adaptation only lowers it, hence the factor).
 
 The paper's own distribution of one integration over devices (Sec. 3.1,
 3.2) is not a server; this module is the serving form of the method.
@@ -49,27 +57,62 @@ class Request:
     done: float = -1.0
     result: dict = field(default_factory=dict)
     converged: bool = False
+    gave_up: bool = False
 
 
 def _pow2_ceil(x: float) -> int:
     return 1 << max(0, int(math.ceil(math.log2(max(1.0, x)))))
 
 
+@dataclass
+class SamplePolicy:
+    """Samples per iteration and the give-up rule (module docstring)."""
+    n_first: int = 1 << 17
+    n_max: int = 1 << 24
+    warm_iters: int = 2
+    iters_to_target: int = 4
+    adaptive: bool = True
+    step_samples: int = 1 << 28
+    give_up: float = 4.0
+    give_up_after: int = 6
+
+    def first_n(self, r: Request) -> int:
+        return min(self.n_first, max(2, r.budget))
+
+    def next_n(self, r: Request, used: int, res: dict, n_active: int = 1) -> int:
+        """Samples for the next iteration of one integral."""
+        m = res["n_iter"]
+        left = r.budget - used
+        if not self.adaptive or m < self.warm_iters or res["sigma"] <= 0 or res["I"] == 0:
+            return max(2, min(self.n_first, left))
+        rel = res["sigma"] / abs(res["I"])
+        need_total = used * (rel / r.target_rel) ** 2
+        more = max(0.0, need_total - used)
+        n = _pow2_ceil(more / self.iters_to_target)
+        n_cap = max(self.n_max, _pow2_ceil(self.step_samples / max(1, n_active)) // 2)
+        return int(max(2, min(max(self.n_first, n), n_cap, left)))
+
+    def hopeless(self, r: Request, used: int, res: dict) -> bool:
+        """The projected total exceeds give_up x budget."""
+        if self.give_up <= 0 or res["n_iter"] < self.give_up_after or res["sigma"] <= 0 or res["I"] == 0:
+            return False
+        rel = res["sigma"] / abs(res["I"])
+        return used * (rel / r.target_rel) ** 2 > self.give_up * r.budget
+
+
 class Server:
     def __init__(self, max_slots: int = 1024, pool_bytes: int = 512 << 20,
                  precision: str = "fp32_kahan", n_first: int = 1 << 17, n_max: int = 1 << 24,
                  warm_iters: int = 2, min_iters: int = 3, iters_to_target: int = 4,
-                 adaptive: bool = True, tile_samples: int | None = None):
+                 adaptive: bool = True, tile_samples: int | None = None,
+                 step_samples: int = 1 << 28, give_up: float = 4.0, give_up_after: int = 6):
         self.batch = V.Batch(max_slots=max_slots, pool_bytes=pool_bytes, precision=precision)
         if tile_samples:
             self.batch.set_tile(tile_samples)
         self.precision = precision
-        self.n_first = int(n_first)
-        self.n_max = int(n_max)
-        self.warm_iters = warm_iters
+        self.policy = SamplePolicy(int(n_first), int(n_max), warm_iters, iters_to_target, adaptive,
+                                   int(step_samples), float(give_up), int(give_up_after))
         self.min_iters = min_iters
-        self.iters_to_target = iters_to_target
-        self.adaptive = adaptive
         self.active = {}      # slot -> [Request, samples used, n per iteration]
         self.queue = []       # arrived, not yet admitted (arrival order)
         self.steps = 0
@@ -78,7 +121,7 @@ class Server:
     def _admit(self, now: float) -> None:
         while self.queue:
             r = self.queue[0]
-            n0 = min(self.n_first, max(2, r.budget))
+            n0 = self.policy.first_n(r)
             cfg = V.Config(n_dim=r.d, n_events=n0, n_bins=r.n_bins, alpha=r.alpha, seed=r.seed,
                            integral_id=r.integral_id, precision=self.precision)
             try:
@@ -90,18 +133,6 @@ class Server:
             r.admitted = now
             self.active[slot] = [r, 0, n0]
             self.queue.pop(0)
-
-    def _next_n(self, r: Request, used: int, res: dict) -> int:
-        """Samples for the next iteration of one integral."""
-        m = res["n_iter"]
-        left = r.budget - used
-        if not self.adaptive or m < self.warm_iters or res["sigma"] <= 0 or res["I"] == 0:
-            return max(2, min(self.n_first, left))
-        rel = res["sigma"] / abs(res["I"])
-        need_total = used * (rel / r.target_rel) ** 2
-        more = max(0.0, need_total - used)
-        n = _pow2_ceil(more / self.iters_to_target)
-        return int(max(2, min(max(self.n_first, n), self.n_max, left)))
 
     def step(self, now_fn) -> list:
         """One batched iteration of all active integrals; returns retired requests."""
@@ -120,16 +151,18 @@ class Server:
             rec[1] = used
             conv = (out["n_iter"] >= self.min_iters and out["sigma"] <= r.target_rel * abs(out["I"])
                     and out["I"] != 0)
-            if conv or used >= r.budget:
+            hopeless = not conv and used < r.budget and self.policy.hopeless(r, used, out)
+            if conv or used >= r.budget or hopeless:
                 r.done = now
                 r.converged = bool(conv)
+                r.gave_up = bool(hopeless)
                 r.result = dict(out)
                 r.result["samples"] = used
                 self.batch.remove(slot)
                 del self.active[slot]
                 retired.append(r)
                 continue
-            nn = self._next_n(r, used, out)
+            nn = self.policy.next_n(r, used, out, len(self.active))
             if nn != n:
                 self.batch.set_events(slot, nn)
                 rec[2] = nn
@@ -170,7 +203,9 @@ def summarize(done, wall: float, steps: int, samples: int, n_requests: int) -> d
     conv = sum(1 for r in done if r.converged)
     return {
         "requests": n_requests, "completed": len(done), "converged": conv,
+        "gave_up": sum(1 for r in done if r.gave_up),
         "wall_s": wall, "integrals_per_s": len(done) / wall if wall > 0 else 0.0,
+        "converged_per_s": conv / wall if wall > 0 else 0.0,
         "p50_ms": float(np.percentile(lat, 50) * 1e3) if lat.size else None,
         "p99_ms": float(np.percentile(lat, 99) * 1e3) if lat.size else None,
         "steps": steps, "samples": samples,
@@ -179,39 +214,41 @@ def summarize(done, wall: float, steps: int, samples: int, n_requests: int) -> d
 
 
 def serve_single_fp64(requests, n_first: int = 1 << 17, n_max: int = 1 << 24, warm_iters: int = 2,
-                      min_iters: int = 3, iters_to_target: int = 4, time_limit: float = 60.0):
+                      min_iters: int = 3, iters_to_target: int = 4, time_limit: float = 60.0,
+                      step_samples: int = 1 << 28, give_up: float = 4.0, give_up_after: int = 6):
     """The plain FP64 single-integral form: one context per request, one at a
-    time, the same sample schedule and stopping rule as the server."""
+    time, the same sample schedule, stopping and give-up rules as the server
+    (one integral active, so its iterations may grow to step_samples / 2)."""
     t0 = time.perf_counter()
     done = []
     samples = 0
     steps = 0
-    helper = Server.__new__(Server)
-    helper.n_first, helper.n_max = n_first, n_max
-    helper.warm_iters, helper.iters_to_target, helper.adaptive = warm_iters, iters_to_target, True
+    policy = SamplePolicy(n_first, n_max, warm_iters, iters_to_target, True, int(step_samples),
+                          float(give_up), int(give_up_after))
     for r in sorted(requests, key=lambda q: q.arrival):
         now = time.perf_counter() - t0
         if now < r.arrival:
             time.sleep(r.arrival - now)
-        n = min(n_first, max(2, r.budget))
+        n = policy.first_n(r)
         cfg = V.Config(n_dim=r.d, n_events=n, n_bins=r.n_bins, alpha=r.alpha, seed=r.seed,
                        integral_id=r.integral_id, precision="fp64")
         ctx = V.vegas_create(cfg, r.family, r.params)
         used = 0
         while True:
-            I_t, s_t, n_ok, n_nf = V.vegas_iterate(ctx)
+            V.vegas_step(ctx, sync=True)  # iterate + refine (a refine after the last is unused)
             steps += 1
             samples += n
             used += n
             res = V.vegas_result(ctx)
             conv = res["n_iter"] >= min_iters and res["sigma"] <= r.target_rel * abs(res["I"]) and res["I"] != 0
-            if conv or used >= r.budget:
+            hopeless = not conv and used < r.budget and policy.hopeless(r, used, res)
+            if conv or used >= r.budget or hopeless:
                 r.converged = bool(conv)
+                r.gave_up = bool(hopeless)
                 r.result = dict(res)
                 r.result["samples"] = used
                 break
-            V.vegas_refine(ctx)
-            nn = helper._next_n(r, used, res)
+            nn = policy.next_n(r, used, res)
             if nn != n:
                 V.vegas_set_events(ctx, nn)
                 n = nn
