@@ -87,6 +87,16 @@ def _load():
         lib.oracle_refine.restype = None
         lib.oracle_combine.argtypes = [i32, dp, dp, dp, dp, dp]
         lib.oracle_combine.restype = None
+        lib.oracle_strata_bits.argtypes = [i32, i32, ip]
+        lib.oracle_strata_bits.restype = None
+        lib.oracle_sample_strat.argtypes = [i32, i32, dp, i32, dp, i32, u32, u32, u32, i32, i64,
+                                            u64, ip, dp, dp, dp]
+        lib.oracle_sample_strat.restype = None
+        lib.oracle_iterate_strat.argtypes = [i32, i32, dp, i32, dp, i32, u32, u32, u32, i32, i64,
+                                             i64, i64, dp, dp, dp, dp, dp, lp]
+        lib.oracle_iterate_strat.restype = None
+        lib.oracle_strat_result.argtypes = [ctypes.c_double, ctypes.c_double, i64, i64, dp, dp]
+        lib.oracle_strat_result.restype = None
         _lib = lib
         return lib
 
@@ -259,6 +269,100 @@ def integrate(d, N, family, params, n, n_iter, alpha=1.5, seed=0, integral_id=0,
         acc = iterate(d, N, e, family, params, seed, integral_id, t, n, threads=threads)
         n_eff = n - acc["n_nonfinite"]
         I, var = iteration_result(acc["S1"], acc["S2"], n_eff)
+        its.append((I, float(np.sqrt(var))))
+        e = refine(d, N, acc["hist"], e, alpha, smooth)
+    Ib, sb, c2 = combine([a for a, _ in its], [b for _, b in its])
+    return {"I": Ib, "sigma": sb, "chi2_dof": c2, "iters": its, "edges": e}
+
+
+# ------------------------------------------- stratified + importance hybrid
+def strata_bits(d: int, B: int) -> np.ndarray:
+    """Halvings of each dimension for 2^B hypercubes (Lepage 1980's combined
+    mode, with the strata counts read as powers of two)."""
+    out = np.zeros(d, dtype=np.int32)
+    _load().oracle_strata_bits(d, B, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    return out
+
+
+def sample_strat(d, N, edges, family, params, seed, integral_id, t, B, P, s):
+    """One sample s of a stratified iteration: (bins[d], x[d], J, f)."""
+    lib = _load()
+    e = _f64(edges).reshape(d, N + 1)
+    p = _f64(params if len(params) else [0.0])
+    bins = np.zeros(d, dtype=np.int32)
+    x = np.zeros(d, dtype=np.float64)
+    J = ctypes.c_double()
+    f = ctypes.c_double()
+    lib.oracle_sample_strat(d, N, _dptr(e), FAMILIES[family], _dptr(p), len(params), seed,
+                            integral_id, t, B, P, s,
+                            bins.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _dptr(x),
+                            ctypes.byref(J), ctypes.byref(f))
+    return bins, x, J.value, f.value
+
+
+def iterate_strat(d, N, edges, family, params, seed, integral_id, t, B, P, h_begin=0,
+                  h_end=None, threads=1):
+    """Hypercubes [h_begin, h_end) (default all 2^B) of a stratified iteration
+    with P samples each.  Returns dict(S1, S2, Q, hist, n_nonfinite); pieces run
+    on host threads are added in thread order."""
+    lib = _load()
+    if h_end is None:
+        h_end = 1 << B
+    e = _f64(edges).reshape(d, N + 1)
+    p = _f64(params if len(params) else [0.0])
+    fam = FAMILIES[family]
+    threads = max(1, min(int(threads), max(1, h_end - h_begin)))
+    bounds = np.linspace(h_begin, h_end, threads + 1).astype(np.int64)
+    slots = [[] for _ in range(threads)]
+
+    def run(a, b, slot):
+        S1, S2, Q = ctypes.c_double(0.0), ctypes.c_double(0.0), ctypes.c_double(0.0)
+        nn = ctypes.c_int64(0)
+        h = np.zeros((d, N), dtype=np.float64)
+        vbuf = np.zeros(max(1, P), dtype=np.float64)
+        lib.oracle_iterate_strat(d, N, _dptr(e), fam, _dptr(p), len(params), seed, integral_id, t,
+                                 B, P, int(a), int(b), _dptr(vbuf), ctypes.byref(S1),
+                                 ctypes.byref(S2), ctypes.byref(Q), _dptr(h), ctypes.byref(nn))
+        slot.append((S1.value, S2.value, Q.value, h, nn.value))
+
+    if threads == 1:
+        run(bounds[0], bounds[1], slots[0])
+    else:
+        ths = [threading.Thread(target=run, args=(bounds[i], bounds[i + 1], slots[i]))
+               for i in range(threads)]
+        for th in ths:
+            th.start()
+        for th in ths:
+            th.join()
+    out = {"S1": 0.0, "S2": 0.0, "Q": 0.0, "hist": np.zeros((d, N)), "n_nonfinite": 0}
+    for sl in slots:
+        a1, a2, q, hh, n0 = sl[0]
+        out["S1"] += a1
+        out["S2"] += a2
+        out["Q"] += q
+        out["hist"] += hh
+        out["n_nonfinite"] += n0
+    return out
+
+
+def strat_result(S1, Q, H, P):
+    """(I, var) of a stratified iteration over H hypercubes of P samples."""
+    lib = _load()
+    I = ctypes.c_double()
+    var = ctypes.c_double()
+    lib.oracle_strat_result(S1, Q, H, P, ctypes.byref(I), ctypes.byref(var))
+    return I.value, var.value
+
+
+def integrate_strat(d, N, family, params, B, P, n_iter, alpha=1.5, seed=0, integral_id=0,
+                    threads=1, edges=None, smooth=True):
+    """Full stratified run (2^B hypercubes of P samples per iteration), refining
+    after each iteration.  Returns dict(I, sigma, chi2_dof, iters, edges)."""
+    e = uniform_edges(d, N) if edges is None else _f64(edges).reshape(d, N + 1)
+    its = []
+    for t in range(n_iter):
+        acc = iterate_strat(d, N, e, family, params, seed, integral_id, t, B, P, threads=threads)
+        I, var = strat_result(acc["S1"], acc["Q"], 1 << B, P)
         its.append((I, float(np.sqrt(var))))
         e = refine(d, N, acc["hist"], e, alpha, smooth)
     Ib, sb, c2 = combine([a for a, _ in its], [b for _, b in its])

@@ -333,3 +333,98 @@ void oracle_combine(int m, const double *I, const double *sigma, double *Ibar, d
     *sbar = 1.0 / sqrt(wsum);
     *chi2_dof = m > 1 ? chi2 / (double)(m - 1) : 0.0;
 }
+
+/* ------------------------------------------- stratified + importance hybrid */
+/* Lepage 1980 combines the importance map with stratified sampling: y-space is
+ * cut into equal hypercubes and every hypercube receives the same number P of
+ * samples; the estimate is the mean of the hypercube means and its variance
+ * the sum of the hypercube variances of the mean.  Readings (the paper and
+ * Lepage leave the counts to the implementation):
+ *   - 2^B hypercubes; dimension j is cut into M_j = 2^b_j strata with
+ *     b_j = floor(B/d) + (j < B mod d ? 1 : 0);
+ *   - hypercube h's stratum in dimension j is k_j = floor(h / prod_{i<j} M_i) mod M_j;
+ *   - sample s belongs to hypercube floor(s / P); its uniform word r_j (the
+ *     same Philox counter as in plain sampling) is placed in the stratum as
+ *     y_j = (k_j + r_j 2^-32) / M_j, kept on the 2^-32 lattice by flooring:
+ *     R_j = floor((k_j 2^32 + r_j) / M_j), y_j = R_j 2^-32;
+ *   - the importance map then treats R_j exactly as plain sampling treats r_j;
+ *   - the histograms take (J f)^2 per sample, as in plain sampling;
+ *   - a non-finite J f counts as 0 (and is counted), so every hypercube keeps
+ *     its P samples. */
+void oracle_strata_bits(int d, int B, int32_t *bits) {
+    for (int j = 0; j < d; ++j) bits[j] = B / d + (j < B % d ? 1 : 0);
+}
+
+static uint32_t strat_word(uint32_t r, uint64_t h, int d, int B, int j) {
+    /* k_j: digit j of h in the mixed radix (M_0, M_1, ...) */
+    uint64_t below = 1;
+    for (int i = 0; i < j; ++i) below *= (uint64_t)1 << (B / d + (i < B % d ? 1 : 0));
+    uint64_t Mj = (uint64_t)1 << (B / d + (j < B % d ? 1 : 0));
+    uint64_t k = (h / below) % Mj;
+    return (uint32_t)((k * 4294967296ull + (uint64_t)r) / Mj);
+}
+
+void oracle_sample_strat(int d, int N, const double *edges, int family, const double *params,
+                         int n_params, uint32_t seed, uint32_t integral_id, uint32_t t, int B,
+                         int64_t P, uint64_t s, int32_t *bins, double *x, double *J, double *f) {
+    double jac = 1.0;
+    uint64_t h = s / (uint64_t)P;
+    for (int j = 0; j < d; ++j) {
+        uint32_t r = strat_word(oracle_draw(s, t, j, seed, integral_id), h, d, B, j);
+        uint64_t prod = (uint64_t)r * (uint64_t)N;
+        int32_t i = (int32_t)(prod >> 32);
+        double frac = (double)(uint32_t)(prod & 0xFFFFFFFFu) * (1.0 / 4294967296.0);
+        const double *e = edges + (size_t)j * (size_t)(N + 1);
+        double delta = e[i + 1] - e[i];
+        bins[j] = i;
+        x[j] = e[i] + delta * frac;
+        jac *= (double)N * delta;
+    }
+    *J = jac;
+    *f = oracle_integrand(family, d, params, n_params, x);
+}
+
+/* Hypercubes h in [h_begin, h_end) of iteration t, P samples each:
+ * *S1 += v, *S2 += v^2, hist as in plain sampling, and
+ * *Q += sum over the hypercube of (v - mean_h)^2 (two passes: the mean first).
+ * vbuf: scratch of P doubles. */
+void oracle_iterate_strat(int d, int N, const double *edges, int family, const double *params,
+                          int n_params, uint32_t seed, uint32_t integral_id, uint32_t t, int B,
+                          int64_t P, int64_t h_begin, int64_t h_end, double *vbuf, double *S1,
+                          double *S2, double *Q, double *hist, int64_t *n_nonfinite) {
+    int32_t bins[ORACLE_MAXD];
+    double x[ORACLE_MAXD];
+    if (d < 1 || d > ORACLE_MAXD || P < 1) return;
+    for (int64_t h = h_begin; h < h_end; ++h) {
+        double sum = 0.0;
+        for (int64_t p = 0; p < P; ++p) {
+            double J, f;
+            oracle_sample_strat(d, N, edges, family, params, n_params, seed, integral_id, t, B,
+                                P, (uint64_t)(h * P + p), bins, x, &J, &f);
+            double v = J * f;
+            if (!isfinite(v)) {
+                if (n_nonfinite) *n_nonfinite += 1;
+                v = 0.0;
+            }
+            double v2 = v * v;
+            vbuf[p] = v;
+            sum += v;
+            *S1 += v;
+            *S2 += v2;
+            for (int j = 0; j < d; ++j) hist[(size_t)j * (size_t)N + (size_t)bins[j]] += v2;
+        }
+        double mean = sum / (double)P;
+        double m2 = 0.0;
+        for (int64_t p = 0; p < P; ++p) m2 += (vbuf[p] - mean) * (vbuf[p] - mean);
+        *Q += m2;
+    }
+}
+
+/* Estimate of a stratified iteration over H hypercubes of P samples:
+ * I = S1 / (H P) (the mean of the hypercube means) and
+ * var = sum_h s_h^2 / (H^2 P) with s_h^2 = m2_h / (P - 1), i.e. Q / (H^2 P (P - 1)). */
+void oracle_strat_result(double S1, double Q, int64_t H, int64_t P, double *I, double *var) {
+    double Hd = (double)H, Pd = (double)P;
+    *I = S1 / (Hd * Pd);
+    *var = P > 1 ? Q / (Hd * Hd * Pd * (Pd - 1.0)) : 0.0;
+}

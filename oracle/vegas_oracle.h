@@ -72,6 +72,28 @@ void oracle_iteration_result(double S1, double S2, int64_t n, double *I, double 
 void oracle_refine(int d, int N, const double *hist, const double *edges_in, double alpha,
                    int smooth, double *edges_out);
 
+/* Stratified + importance hybrid (Lepage 1980's combined mode): 2^B
+ * hypercubes, bits[j] = number of halvings of dimension j
+ * (floor(B/d) + (j < B mod d)). */
+void oracle_strata_bits(int d, int B, int32_t *bits);
+
+/* One sample s of a stratified iteration with P samples per hypercube
+ * (hypercube floor(s/P)); otherwise as oracle_sample. */
+void oracle_sample_strat(int d, int N, const double *edges, int family, const double *params,
+                         int n_params, uint32_t seed, uint32_t integral_id, uint32_t t, int B,
+                         int64_t P, uint64_t s, int32_t *bins, double *x, double *J, double *f);
+
+/* Hypercubes [h_begin, h_end) of a stratified iteration: S1, S2, hist as in
+ * oracle_iterate (non-finite v count as 0 and are counted) and
+ * *Q += sum_h sum_p (v - mean_h)^2.  vbuf: scratch of P doubles. */
+void oracle_iterate_strat(int d, int N, const double *edges, int family, const double *params,
+                          int n_params, uint32_t seed, uint32_t integral_id, uint32_t t, int B,
+                          int64_t P, int64_t h_begin, int64_t h_end, double *vbuf, double *S1,
+                          double *S2, double *Q, double *hist, int64_t *n_nonfinite);
+
+/* Stratified estimate: I = S1/(H P), var = Q/(H^2 P (P-1)). */
+void oracle_strat_result(double S1, double Q, int64_t H, int64_t P, double *I, double *var);
+
 /* Inverse-variance combination of m iteration results. */
 void oracle_combine(int m, const double *I, const double *sigma, double *Ibar, double *sbar,
                     double *chi2_dof);
