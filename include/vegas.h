@@ -220,6 +220,36 @@ vegas_status vegas_set_iteration(vegas_ctx *ctx, int32_t t);
 vegas_status vegas_trace(vegas_ctx *ctx, int32_t t, int64_t s_begin, int64_t count,
                          int32_t *dev_bins, double *dev_x, double *dev_w);
 
+/* Stratified + importance hybrid: the combined mode of Lepage's VEGAS (Cornell
+ * CLNS-80/447, 1980; the method the paper takes as VegasFlow's, Sec. 1), in
+ * which y-space is also cut into equal hypercubes that each receive the same
+ * number of samples.  With B != 0 every later iteration uses H = 2^B
+ * hypercubes of P = floor(n_events / H) samples, H P samples in all.
+ * Dimension j is halved b_j = floor(B/d) + (j < B mod d ? 1 : 0) times;
+ * hypercube h's stratum in it, k_j, is the integer in bits
+ * [b_0 + ... + b_(j-1), b_0 + ... + b_j) of h.  Sample s lies in hypercube
+ * s / P, and its Philox word r_j is moved into the stratum,
+ *     R_j = k_j 2^(32 - b_j) + (r_j >> b_j)    (y_j = (k_j + r_j 2^-32) / 2^b_j),
+ * which then takes r_j's place in the grid map (bin, interpolation, J).  The
+ * estimate is the mean of the hypercube means, I = S1 / (H P); its variance
+ * the sum of the hypercubes' variances of the mean,
+ *     sigma^2 = sum_h m2_h / (H^2 P (P - 1)),  m2_h = sum_(s in h) (v_s - mean_h)^2.
+ * The histograms take (J f)^2 per sample as in plain sampling.  A non-finite
+ * J f counts as 0 (and in n_nonfinite), so every hypercube keeps P samples.
+ *   B = 0  : plain importance sampling (the default);
+ *   B = -1 : as many hypercubes as leave P >= 2;
+ *   B > 0  : 2^B hypercubes, fewer where P would drop below 2.
+ * B never exceeds 16 halvings per dimension nor 31 in all.  EINVAL for B
+ * outside [-1, 31] and, in the FP32 modes, when one hypercube's P samples
+ * exceed what one block's fixed-point histogram cells hold between flushes
+ * (64 N copies-per-cell samples; vegas_set_events checks the same).
+ * Stratified iterations are not sharded: vegas_sample_shard returns EINVAL.
+ * vegas_trace follows the setting (sample s of the stratified iteration). */
+vegas_status vegas_set_strata(vegas_ctx *ctx, int32_t B);
+/* The stratification of the next iteration: *B (0: plain), *P (0: plain) and
+ * *n_used, the samples it takes (n_events when plain).  Any pointer may be NULL. */
+vegas_status vegas_get_strata(vegas_ctx *ctx, int32_t *B, int64_t *P, int64_t *n_used);
+
 /* Checkpoint: a byte blob holding config, parameters, FP64 grid, iteration
  * counter and per-iteration results.  export with buf == NULL sets *size.
  * import restores them into a context created with the same configuration. */

@@ -83,6 +83,8 @@ _SIGS = {
     "vegas_get_iteration": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),
     "vegas_set_iteration": (ctypes.c_int, [_P, ctypes.c_int32]),
     "vegas_trace": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, _P, _P, _P]),
+    "vegas_set_strata": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "vegas_get_strata": (ctypes.c_int, [_P, _P, _P, _P]),
     "vegas_export_state": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_size_t)]),
     "vegas_import_state": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
     "vegas_philox": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _P]),

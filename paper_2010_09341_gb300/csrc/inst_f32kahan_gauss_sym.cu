@@ -3,4 +3,5 @@
 
 namespace vegas {
 const void *sample_kernel_f32kahan_gauss_sym(int d, bool priv) { return pick_family<ACC_F32_KAHAN, F_GAUSS_SYM>(d, priv); }
+const void *sample_strat_kernel_f32kahan_gauss_sym(int d, bool priv) { return pick_strat<ACC_F32_KAHAN, F_GAUSS_SYM>(d, priv); }
 }  // namespace vegas

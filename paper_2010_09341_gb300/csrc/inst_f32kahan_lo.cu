@@ -3,4 +3,5 @@
 
 namespace vegas {
 const void *sample_kernel_f32kahan_lo(int d, bool priv) { return pick_family<ACC_F32_KAHAN, F_LO>(d, priv); }
+const void *sample_strat_kernel_f32kahan_lo(int d, bool priv) { return pick_strat<ACC_F32_KAHAN, F_LO>(d, priv); }
 }  // namespace vegas

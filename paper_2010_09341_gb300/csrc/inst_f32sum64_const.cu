@@ -3,4 +3,5 @@
 
 namespace vegas {
 const void *sample_kernel_f32sum64_const(int d, bool priv) { return pick_family<ACC_F32_SUM64, F_CONST>(d, priv); }
+const void *sample_strat_kernel_f32sum64_const(int d, bool priv) { return pick_strat<ACC_F32_SUM64, F_CONST>(d, priv); }
 }  // namespace vegas

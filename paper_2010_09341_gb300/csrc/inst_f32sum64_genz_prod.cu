@@ -3,4 +3,5 @@
 
 namespace vegas {
 const void *sample_kernel_f32sum64_genz_prod(int d, bool priv) { return pick_family<ACC_F32_SUM64, F_GENZ_PROD>(d, priv); }
+const void *sample_strat_kernel_f32sum64_genz_prod(int d, bool priv) { return pick_strat<ACC_F32_SUM64, F_GENZ_PROD>(d, priv); }
 }  // namespace vegas

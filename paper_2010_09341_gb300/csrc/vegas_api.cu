@@ -36,7 +36,7 @@ constexpr size_t kAlign = 256;
 inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-    size_t edges, table, acc, last, nonfinite, hscale, jmul, iters, comb, cstate, total;
+    size_t edges, table, acc, last, nonfinite, hscale, jmul, iters, comb, cstate, q, total;
 };
 
 Layout layout_for(int d, int N) {
@@ -62,6 +62,8 @@ Layout layout_for(int d, int N) {
     off = align_up(off + sizeof(CombRec));
     L.cstate = off;
     off = align_up(off + sizeof(CombState));
+    L.q = off;                                 // stratified: running and last sum of m2
+    off = align_up(off + 2 * sizeof(double));
     L.total = off;
     return L;
 }
@@ -208,6 +210,10 @@ struct vegas_ctx {
     int threads;
     int max_blocks;
     bool profiling = false;
+    double *q;          // stratified: sum of hypercube m2 (running, last)
+    int strat_req = 0;  // requested 2^B hypercubes: 0 off, -1 automatic, else B
+    const void *kfn_strat = nullptr;
+    int max_blocks_strat = 0;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;  // event pool
     size_t ev_used = 0;
 
@@ -310,6 +316,7 @@ vegas_status vegas_create(const vegas_config *cfg, const vegas_integrand *itg, v
     c->iters = reinterpret_cast<IterRec *>(c->ws + L.iters);
     c->comb = reinterpret_cast<CombRec *>(c->ws + L.comb);
     c->cstate = reinterpret_cast<CombState *>(c->ws + L.cstate);
+    c->q = reinterpret_cast<double *>(c->ws + L.q);
     c->t = 0;
     c->n_done = 0;
     c->fc = fc;
@@ -337,6 +344,7 @@ vegas_status vegas_create(const vegas_config *cfg, const vegas_integrand *itg, v
     static const double kOnes[2] = {1.0, 1.0};
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(c->jmul, kOnes, sizeof(kOnes), cudaMemcpyHostToDevice, c->stream);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(c->comb, 0, (L.cstate + sizeof(CombState)) - L.comb, c->stream);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(c->q, 0, 2 * sizeof(double), c->stream);
     if (ce == cudaSuccess) ce = launch_table_from_edges(c->edges, c->table, mode, d, N, c->stream);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
     if (ce != cudaSuccess) {
@@ -346,6 +354,40 @@ vegas_status vegas_create(const vegas_config *cfg, const vegas_integrand *itg, v
     }
     *out = c;
     return VEGAS_OK;
+}
+
+// Stratification in effect for n samples: 2^B hypercubes of P samples, with
+// B = the requested B (or, automatically, as many as leave P >= 2), never more
+// than leave P >= 2, 16 halvings per dimension or 2^31 hypercubes.
+struct Strata {
+    int B = 0;
+    long long H = 0, P = 0;   // P = 0: plain sampling
+};
+
+static Strata strata_for(int req, int d, long long n) {
+    Strata st;
+    if (req == 0 || n < 2) return st;
+    int bmax = 0;
+    while (bmax < 62 && (n >> (bmax + 1)) >= 2) ++bmax;   // largest B with n / 2^B >= 2
+    int B = req < 0 ? bmax : std::min(req, bmax);
+    B = std::min(B, std::min(16 * d, 31));
+    st.B = B;
+    st.H = 1LL << B;
+    st.P = n / st.H;
+    return st;
+}
+
+static void fill_strata(SampleArgs &a, const Strata &st, int d, double *q) {
+    memset(&a.st, 0, sizeof(a.st));
+    a.st.P = static_cast<uint32_t>(st.P);
+    a.st.q = q;
+    uint32_t off = 0;
+    for (int j = 0; j < d; ++j) {
+        const uint32_t b = static_cast<uint32_t>(st.B / d + (j < st.B % d ? 1 : 0));
+        a.st.off[j] = off;
+        a.st.bits[j] = b;
+        off += b;
+    }
 }
 
 static SampleArgs make_args(const vegas_ctx *c, long long s_begin, long long n, int t) {
@@ -370,7 +412,28 @@ static SampleArgs make_args(const vegas_ctx *c, long long s_begin, long long n, 
         a.fc32.q[k] = static_cast<float>(c->fc.q[k]);
     }
     for (int k = 0; k < 8; ++k) a.fc32.s[k] = static_cast<float>(c->fc.s[k]);
+    memset(&a.st, 0, sizeof(a.st));
     return a;
+}
+
+// Hypercubes [h_begin, h_begin + count) of a stratified iteration.
+static vegas_status launch_sampling_strat(vegas_ctx *c, const Strata &st, long long h_begin, long long count) {
+    SampleArgs a = make_args(c, h_begin, count, c->t);
+    fill_strata(a, st, c->cfg.n_dim, c->q);
+    // whole hypercubes per thread, a few samples per thread at least
+    const long long per_thread = std::max(1LL, (c->mode == ACC_F64 ? 1 : 4) / st.P);
+    const long long want = (count + static_cast<long long>(c->threads) * per_thread - 1) /
+                           (static_cast<long long>(c->threads) * per_thread);
+    long long blocks = std::max(1LL, std::min<long long>(c->max_blocks_strat, want));
+    if (c->mode != ACC_F64) {
+        // fixed-point histogram cells: a bounded number of samples per block
+        const long long cap = block_samples_max(c->mode, c->priv ? 1 : 0, c->cfg.n_bins) / st.P;
+        blocks = std::max(blocks, (count + cap - 1) / cap);
+    }
+    void *params[] = {&a};
+    VEGAS_CK(cudaLaunchKernel(c->kfn_strat, dim3(static_cast<unsigned>(blocks)), dim3(c->threads), params,
+                              c->smem, c->stream));
+    return VEGAS_OK;
 }
 
 static vegas_status launch_sampling(vegas_ctx *c, long long s_begin, long long n) {
@@ -408,9 +471,20 @@ static vegas_status sample_samples(vegas_ctx *c, long long s_begin, long long co
         pe = &c->ev[c->ev_used++];
         VEGAS_CK(cudaEventRecord(pe->first, c->stream));
     }
-    for (long long s0 = 0; s0 < count; s0 += lim) {
-        const vegas_status st = launch_sampling(c, s_begin + s0, std::min(lim, count - s0));
-        if (st != VEGAS_OK) return st;
+    const Strata sg = strata_for(c->strat_req, c->cfg.n_dim, c->cfg.n_events);
+    if (sg.P > 0) {
+        // whole hypercubes per launch (samples [s_begin, s_begin + count) are
+        // the whole iteration here: stratified iterations are not sharded)
+        const long long limh = std::max(1LL, lim / sg.P);
+        for (long long h0 = 0; h0 < sg.H; h0 += limh) {
+            const vegas_status st = launch_sampling_strat(c, sg, h0, std::min(limh, sg.H - h0));
+            if (st != VEGAS_OK) return st;
+        }
+    } else {
+        for (long long s0 = 0; s0 < count; s0 += lim) {
+            const vegas_status st = launch_sampling(c, s_begin + s0, std::min(lim, count - s0));
+            if (st != VEGAS_OK) return st;
+        }
     }
     if (pe) VEGAS_CK(cudaEventRecord(pe->second, c->stream));
     return VEGAS_OK;
@@ -433,6 +507,11 @@ static FinalizeArgs finalize_args(vegas_ctx *c) {
     f.n = c->cfg.n_events;
     f.inv_scale0 = 1.0 / c->scale;
     f.jinit0 = c->jinit;
+    const Strata sg = strata_for(c->strat_req, c->cfg.n_dim, c->cfg.n_events);
+    f.strat_H = sg.H;
+    f.strat_P = sg.P;
+    f.q = c->q;
+    if (sg.P > 0) f.n = sg.H * sg.P;
     return f;
 }
 
@@ -477,6 +556,7 @@ vegas_status vegas_step(vegas_ctx *c, vegas_iter_result *out) {
 
 vegas_status vegas_sample_shard(vegas_ctx *c, int64_t s_begin, int64_t count) {
     if (!c || s_begin < 0 || count < 0 || s_begin + count > c->cfg.n_events) return VEGAS_EINVAL;
+    if (c->strat_req != 0) return VEGAS_EINVAL;  // stratified iterations are not sharded
     if (count == 0) return VEGAS_OK;
     return sample_samples(c, s_begin, count);
 }
@@ -587,6 +667,10 @@ vegas_status vegas_get_sums(vegas_ctx *c, double *sums_host) {
 
 vegas_status vegas_set_events(vegas_ctx *c, int64_t n_events) {
     if (!c || n_events < 2) return VEGAS_EINVAL;
+    if (c->strat_req != 0 && c->mode != ACC_F64 &&
+        strata_for(c->strat_req, c->cfg.n_dim, n_events).P >
+            block_samples_max(c->mode, c->priv ? 1 : 0, c->cfg.n_bins))
+        return VEGAS_EINVAL;
     c->cfg.n_events = n_events;
     return VEGAS_OK;
 }
@@ -608,7 +692,50 @@ vegas_status vegas_trace(vegas_ctx *c, int32_t t, int64_t s_begin, int64_t count
     if (!c || t < 0 || s_begin < 0 || count < 0) return VEGAS_EINVAL;
     if (count == 0) return VEGAS_OK;
     SampleArgs a = make_args(c, s_begin, count, t);
+    const Strata sg = strata_for(c->strat_req, c->cfg.n_dim, c->cfg.n_events);
+    if (sg.P > 0) {
+        if (s_begin + count > sg.H * sg.P) return VEGAS_EINVAL;
+        fill_strata(a, sg, c->cfg.n_dim, nullptr);
+    }
     VEGAS_CK(launch_trace(a, c->family, c->mode, 1.0 / c->scale, bins, x, w, c->stream));
+    return VEGAS_OK;
+}
+
+vegas_status vegas_set_strata(vegas_ctx *c, int32_t B) {
+    if (!c || B < -1 || B > 31) return VEGAS_EINVAL;
+    if (B != 0 && !c->kfn_strat) {
+        const void *fn = sample_strat_kernel(c->mode, c->family, c->cfg.n_dim, c->priv);
+        if (!fn) return VEGAS_EINVAL;
+        VEGAS_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      static_cast<int>(c->smem)));
+        int occ = 0;
+        VEGAS_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, c->threads, c->smem));
+        if (occ < 1) return VEGAS_EINVAL;
+        cudaError_t err;
+        const DeviceInfo di = device_info(&err);
+        if (err != cudaSuccess) {
+            set_error("device query", err);
+            return VEGAS_ECUDA;
+        }
+        c->kfn_strat = fn;
+        c->max_blocks_strat = occ * di.sms;
+    }
+    if (B != 0) {
+        // a hypercube must fit one block's fixed-point histogram capacity
+        const Strata sg = strata_for(B, c->cfg.n_dim, c->cfg.n_events);
+        if (c->mode != ACC_F64 && sg.P > block_samples_max(c->mode, c->priv ? 1 : 0, c->cfg.n_bins))
+            return VEGAS_EINVAL;
+    }
+    c->strat_req = B;
+    return VEGAS_OK;
+}
+
+vegas_status vegas_get_strata(vegas_ctx *c, int32_t *B, int64_t *P, int64_t *n_used) {
+    if (!c) return VEGAS_EINVAL;
+    const Strata sg = strata_for(c->strat_req, c->cfg.n_dim, c->cfg.n_events);
+    if (B) *B = sg.P > 0 ? sg.B : 0;
+    if (P) *P = sg.P;
+    if (n_used) *n_used = sg.P > 0 ? sg.H * sg.P : c->cfg.n_events;
     return VEGAS_OK;
 }
 
@@ -623,7 +750,7 @@ struct BlobHeader {
     int32_t t;
     int32_t n_done;
     float hscale;       // fixed-point histogram scale of the next iteration
-    int32_t pad;
+    int32_t strat_req;  // vegas_set_strata's B (0: plain sampling)
     double jmul;        // rescale of v of the next iteration
 };
 constexpr uint32_t kMagic = 0x56454741u;  // "VEGA"
@@ -655,6 +782,7 @@ vegas_status vegas_export_state(vegas_ctx *c, void *buf, size_t *size) {
     h.n_params = static_cast<int32_t>(c->params.size());
     h.t = c->t;
     h.n_done = c->n_done;
+    h.strat_req = c->strat_req;
     memcpy(p, &h, sizeof(h));
     p += sizeof(h);
     memcpy(p, c->params.data(), sizeof(double) * c->params.size());
@@ -714,7 +842,7 @@ vegas_status vegas_import_state(vegas_ctx *c, const void *buf, size_t size) {
     VEGAS_CK(cudaStreamSynchronize(c->stream));
     c->t = h.t;
     c->n_done = h.n_done;
-    return VEGAS_OK;
+    return vegas_set_strata(c, h.strat_req);
 }
 
 vegas_status vegas_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int64_t n,

@@ -29,22 +29,35 @@ __device__ void finalize_stats(const FinalizeArgs &f) {
     const double inv1 = f.inv_scale0 / jm;
     const long long nf = static_cast<long long>(*f.n_nonfinite);
     *f.n_nonfinite = 0ull;
-    const long long ne = f.n - nf;
+    // stratified: a non-finite value counts as 0, so every sample stays in n
+    const bool strat = f.strat_P > 0;
+    const long long ne = strat ? f.n : f.n - nf;
     const double S1 = f.acc[0] * inv1, S2 = f.acc[1] * inv1 * inv1;
     const double m2 = ne > 0 ? f.acc[1] / static_cast<double>(ne) : 0.0;
+    const double m1 = ne > 0 ? f.acc[0] / static_cast<double>(ne) : 0.0;
     f.last[0] = S1;
     f.last[1] = S2;
     f.acc[0] = 0.0;
     f.acc[1] = 0.0;
     double ratio;
     float hs;
-    next_scales(m2, f.jinit0 * jm, &ratio, &hs);
+    next_scales(m2, m1, f.jinit0 * jm, &ratio, &hs);
     *f.hscale = hs;
     f.jmul2[(f.rec + 1) & 1] = jm * ratio;
     IterRec r;
     r.n = ne;
     r.n_nonfinite = nf;
-    if (ne >= 2) {
+    if (strat) {
+        // Lepage 1980's combined mode: the mean of the hypercube means and the
+        // sum of their variances of the mean, var = Q / (H^2 P (P - 1))
+        const double Q = f.q[0] * inv1 * inv1;
+        f.q[1] = Q;
+        f.q[0] = 0.0;
+        const double H = static_cast<double>(f.strat_H), P = static_cast<double>(f.strat_P);
+        r.I = S1 / (H * P);
+        const double var = f.strat_P > 1 ? Q / (H * H * P * (P - 1.0)) : 0.0;
+        r.sigma = var > 0.0 ? sqrt(var) : 0.0;
+    } else if (ne >= 2) {
         const double rn = 1.0 / static_cast<double>(ne);
         const double I = S1 * rn;
         const double var = (S2 * rn - I * I) / static_cast<double>(ne - 1);
@@ -203,7 +216,9 @@ __global__ void trace_kernel(const SampleArgs a, double inv_scale, int32_t *bins
             for (int w = 0; w < 4; ++w) {
                 const int j = 4 * q + w;
                 if (j < MAXD && j < d) {
-                    const Split sp = split_bin(word(r, w), static_cast<uint32_t>(N));
+                    uint32_t rw = word(r, w);
+                    if (a.st.P > 0) rw = strat_word(rw, static_cast<uint32_t>(s / a.st.P), a.st.off[j], a.st.bits[j]);
+                    const Split sp = split_bin(rw, static_cast<uint32_t>(N));
                     const uint32_t cell = static_cast<uint32_t>(j * N) + sp.bin;
                     const T2 ent = tab[cell];
                     const T m = Prec<T>::mant(sp.lo);
@@ -217,7 +232,8 @@ __global__ void trace_kernel(const SampleArgs a, double inv_scale, int32_t *bins
             }
         }
     }
-    const T v = J * fam.finish(fc);
+    T v = J * fam.finish(fc);
+    if (a.st.P > 0 && !isfinite(v)) v = T(0);  // stratified: non-finite counts as 0
     if (ws) ws[k] = static_cast<double>(v) * (inv_scale / jm);
 }
 

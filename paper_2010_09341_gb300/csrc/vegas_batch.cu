@@ -61,7 +61,8 @@ batch_finalize_kernel(const BatchArgs ba) {
             const double jm = sd.jmul;
             double ratio;
             float hs;
-            next_scales(m2, static_cast<double>(sd.jinit32) * jm, &ratio, &hs);
+            const double m1 = ne > 0 ? sd.acc[0] / static_cast<double>(ne) : 0.0;
+            next_scales(m2, m1, static_cast<double>(sd.jinit32) * jm, &ratio, &hs);
             const double inv1 = sd.inv_scale / jm, inv2 = inv1 * inv1;
             inv_s = inv1;
             sd.jmul = jm * ratio;

@@ -42,6 +42,8 @@ struct CombRec {
 // Sampling kernel for (accumulation mode, family, dimension, lane-private
 // layout); nullptr if the combination does not exist.
 const void *sample_kernel(int mode, int fam, int d, bool priv);
+// Stratified sampling kernel for the same arguments (vegas_sample_strat_kernel).
+const void *sample_strat_kernel(int mode, int fam, int d, bool priv);
 
 inline int tier_of(int d) { return d <= 4 ? 0 : (d <= 8 ? 1 : (d <= 16 ? 2 : 3)); }
 
@@ -68,6 +70,11 @@ struct FinalizeArgs {
     int total;            // 2 + d N
     long long n;          // samples of the iteration
     double inv_scale0, jinit0;
+    // stratified iterations (strat_P > 0): strat_H hypercubes of strat_P
+    // samples; q[0] accumulates sum_h m2_h (scaled like S2), q[1] keeps the
+    // last iteration's, unscaled
+    long long strat_H, strat_P;
+    double *q;
 };
 cudaError_t launch_finalize(const FinalizeArgs &f, cudaStream_t stream);
 // Finalize and refinement in one launch (vegas_step).

@@ -23,6 +23,27 @@ namespace vegas {
 
 enum AccMode : int { ACC_F64 = 0, ACC_F32_SUM64 = 1, ACC_F32_KAHAN = 2 };
 
+// Stratified + importance hybrid (Lepage 1980's combined mode).  y-space is cut
+// into 2^B equal hypercubes and hypercube h takes samples hP .. hP + P - 1.
+// Dimension j is halved bits[j] times; h's stratum in it is k_j = bits
+// [off[j], off[j] + bits[j]) of h.  The stratum takes the top bits[j] bits of
+// the sample's Philox word r_j:
+//   R_j = k_j 2^(32 - bits[j]) + floor(r_j / 2^bits[j]),
+// i.e. y_j = (k_j + r_j 2^-32) / 2^bits[j] on the 2^-32 lattice, and the
+// importance map then treats R_j as plain sampling treats r_j.
+struct StratArgs {
+    uint32_t P;          // samples per hypercube; 0: plain sampling
+    uint32_t off[32];
+    uint32_t bits[32];   // each <= 16
+    double *q;           // FP64 accumulator: sum_h sum_p (v - mean_h)^2
+};
+
+// R_j from r_j: the 64-bit pair (h >> off : r) shifted right by bits keeps the
+// stratum's bits of h on top of the word's top 32 - bits bits.
+__device__ __forceinline__ uint32_t strat_word(uint32_t r, uint32_t h, uint32_t off, uint32_t bits) {
+    return __funnelshift_r(r, h >> off, bits);
+}
+
 struct SampleArgs {
     const void *table;        // [d][N] entries (e - w, w): double2 or float2
     double *acc;              // [2 + d N] FP64 accumulators: S1, S2, histograms
@@ -38,6 +59,7 @@ struct SampleArgs {
     const float *hscale;      // FP32 modes: fixed-point scale of v^2 (0: float cells)
     FamConsts<double> fc64;   // integrand constants, FP64 path
     FamConsts<float> fc32;    // the same rounded to FP32, FP32 paths
+    StratArgs st;             // stratified launches: s_begin, n count hypercubes
 };
 
 template <class T> __device__ __forceinline__ const FamConsts<T> &consts(const SampleArgs &a);
@@ -123,13 +145,19 @@ __device__ __forceinline__ int binary_exponent(double x) {  // floor(log2 x) for
     return static_cast<int>((__double_as_longlong(x) >> 52) & 0x7FF) - 1023;
 }
 
-// Scales for the next iteration from m2, the mean of this iteration's scaled
-// v^2 (0 if none): a power of two `ratio` that brings the mean of v^2 near 1
-// (FP32 keeps its full precision for v and v^2 whatever the size of the
-// integral), limited so that the initial weight jinit * jmul * ratio stays
-// within 2^-100..2^100, and the fixed-point histogram scale that maps the
-// rescaled mean to 2^18.
-__device__ __forceinline__ void next_scales(double m2, double jinit_eff, double *ratio, float *hs) {
+// Scales for the next iteration from m2 and m1, the means of this iteration's
+// scaled v^2 and v (0 if none): a power of two `ratio` that brings the mean of
+// v^2 near 1 (FP32 keeps its full precision for v and v^2 whatever the size
+// of the integral), limited so that the initial weight jinit * jmul * ratio
+// stays within 2^-100..2^100, and the fixed-point histogram scale that maps
+// the rescaled mean to 2^18.  The scale is used only where this iteration's
+// m2 predicts the next one's: when m2 exceeds kSettled m1^2 (a relative
+// variance per sample above 1023: the grid is far from adapted, or a few
+// samples dominated the iteration), the next mean of v^2 may be orders of
+// magnitude lower, and a scale fixed from m2 would leave its values a few
+// integer units; the next iteration then keeps FP32 cells (hs = 0).
+constexpr double kSettled = 1024.0;
+__device__ __forceinline__ void next_scales(double m2, double m1, double jinit_eff, double *ratio, float *hs) {
     // exponents from the bits, not from FP64 log2 (a long chain on this GPU's FP64 pipe)
     double r = 1.0;
     float h = 0.f;
@@ -146,7 +174,7 @@ __device__ __forceinline__ void next_scales(double m2, double jinit_eff, double 
         const int cl = binary_exponent(y) + ((yb & 0xFFFFFFFFFFFFFLL) != 0 ? 1 : 0);  // ceil(log2 y)
         int eh = 18 - cl;
         eh = max(-100, min(100, eh));
-        h = __int_as_float((eh + 127) << 23);
+        h = m2 <= kSettled * m1 * m1 ? __int_as_float((eh + 127) << 23) : 0.f;
     }
     *ratio = r;
     *hs = h;
@@ -198,6 +226,7 @@ template <int MODE, int PRIV> struct BlockState {
 template <int MODE> struct ThreadSums {
     double s1d = 0.0, s2d = 0.0;                     // ACC_F64, ACC_F32_SUM64
     float s1f = 0.f, c1f = 0.f, s2f = 0.f, c2f = 0.f;  // ACC_F32_KAHAN
+    double qd = 0.0;                                 // stratified: sum of hypercube m2
     unsigned int nonfinite = 0;
 };
 
@@ -226,6 +255,118 @@ template <int MAXD, bool PACK> struct SampleCells {
     }
 };
 
+// Grid map and integrand of sample s: its Philox words (placed in hypercube
+// h's strata when STRAT), each dimension's cell (recorded in cellj) and
+// v = J f, or 0 when v is not finite (counted in nonfinite).
+template <int FAM, int MODE, int MAXD, bool EXACT, int PRIV, bool PACK, bool STRAT>
+__device__ __forceinline__ typename ModeTraits<MODE>::T map_sample(
+    const typename BlockState<MODE, PRIV>::T2 *tab_l, const RangeParams<typename ModeTraits<MODE>::T> &rp,
+    const FamConsts<typename ModeTraits<MODE>::T> &fc, const StratArgs *st, uint32_t h,
+    unsigned long long s, SampleCells<MAXD, PACK> &cellj, unsigned int &nonfinite) {
+    using BS = BlockState<MODE, PRIV>;
+    using T = typename BS::T;
+    using T2 = typename BS::T2;
+    constexpr int TP = BS::TP;
+    const int d = EXACT ? MAXD : rp.d;
+    const int N = rp.N;
+    const uint32_t slo = static_cast<uint32_t>(s), shi = static_cast<uint32_t>(s >> 32);
+    Integrand<FAM, T, MAXD> fam;
+    T J = rp.jinit;
+    fam.begin(fc);
+#pragma unroll
+    for (int q = 0; q < (MAXD + 3) / 4; ++q) {
+        if (EXACT || 4 * q < d) {
+            const uint4 r = philox4x32_10(make_uint4(slo, shi, rp.iter, static_cast<uint32_t>(q)),
+                                          rp.key0, rp.key1);
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                const int j = 4 * q + w;
+                if (j < MAXD && (EXACT || j < d)) {
+                    uint32_t rw = word(r, w);
+                    if (STRAT) rw = strat_word(rw, h, st->off[j], st->bits[j]);
+                    const Split sp = split_bin(rw, static_cast<uint32_t>(N));
+                    const uint32_t cell = static_cast<uint32_t>(j * N) + sp.bin;
+                    const T2 ent = tab_l[cell * TP];
+                    const T m = Prec<T>::mant(sp.lo);
+                    const T x = ffma(ent.y, m, ent.x);
+                    J *= ent.y;
+                    if (sizeof(T) == 4 && (j & 3) == 3) J *= rp.n4;
+                    cellj.set(j, cell);
+                    fam.dim(j, x, fc);
+                }
+            }
+        }
+    }
+    T v = J * fam.finish(fc);
+    if (!isfinite(v)) {
+        v = T(0);
+        ++nonfinite;
+    }
+    return v;
+}
+
+// Adds v2 = v^2 to the histogram cell of each of the sample's dimensions (the
+// cell arrays and fixed-point rules above).
+template <int MODE, int PRIV, int MAXD, bool EXACT, bool PACK>
+__device__ __forceinline__ void hist_add(const BlockState<MODE, PRIV> &bs, typename BlockState<MODE, PRIV>::H *hist_l,
+                                         const RangeParams<typename ModeTraits<MODE>::T> &rp,
+                                         const SampleCells<MAXD, PACK> &cellj, typename ModeTraits<MODE>::T v2,
+                                         bool fixed, float hs) {
+    using BS = BlockState<MODE, PRIV>;
+    using T = typename BS::T;
+    using H = typename BS::H;
+    constexpr int HP = BS::HP;
+    const int d = EXACT ? MAXD : rp.d;
+    if (MODE == ACC_F64) {
+#pragma unroll
+        for (int j = 0; j < MAXD; ++j) {
+            if (EXACT || j < d) red_add_shared(hist_l + cellj.get(j) * HP, static_cast<H>(v2));
+        }
+    } else if (v2 == T(0)) {
+        // nothing to add
+    } else if (fixed) {
+        const float qf = static_cast<float>(v2) * hs;
+        if (qf < kFixedMax) {
+            // rint by adding 2^23 (the integer lands in the mantissa's
+            // low bits; exact for values below 2^23)
+            const bool is_fine = qf < 1.0f;
+            const float t = __fmaf_rn(qf, is_fine ? kFineScale : 1.0f, 8388608.0f);
+            uint32_t q = __float_as_uint(t) - 0x4B000000u;
+            q = max(q, 1u);
+            unsigned int *base = is_fine ? bs.fine : reinterpret_cast<unsigned int *>(hist_l);
+            const uint32_t step = is_fine ? 1u : static_cast<uint32_t>(HP);
+#pragma unroll
+            for (int j = 0; j < MAXD; ++j) {
+                if (EXACT || j < d) atomicAdd(base + cellj.get(j) * step, q);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < MAXD; ++j) {
+                if (EXACT || j < d) atomicAdd(rp.acc + 2 + cellj.get(j), static_cast<double>(v2));
+            }
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < MAXD; ++j) {
+            if (EXACT || j < d) red_add_shared(reinterpret_cast<float *>(hist_l) + cellj.get(j) * HP,
+                                               static_cast<float>(v2));
+        }
+    }
+}
+
+// Kahan step of the FP32-compensated sums of v and v^2.
+template <int MODE>
+__device__ __forceinline__ void kahan_add(ThreadSums<MODE> &ts, float v, float v2) {
+    const float y1 = v - ts.c1f;
+    const float t1 = ts.s1f + y1;
+    ts.c1f = (t1 - ts.s1f) - y1;
+    ts.s1f = t1;
+    const float y2 = v2 - ts.c2f;
+    const float t2 = ts.s2f + y2;
+    ts.c2f = (t2 - ts.s2f) - y2;
+    ts.s2f = t2;
+}
+
 // The block samples [s0, s0 + cnt) of one integral: thread t takes
 // s0 + t + u * blockDim, in chunks of kChunk samples (ACC_F32_SUM64 adds a
 // chunk's FP32 partial sums into the FP64 sums once per chunk).
@@ -242,14 +383,11 @@ __device__ __forceinline__ void sample_range(const BlockState<MODE, PRIV> &bs,
     using H = typename BS::H;
     constexpr int TP = BS::TP;
     constexpr int HP = BS::HP;
-    const int d = EXACT ? MAXD : rp.d;
-    const int N = rp.N;
     const int lane = threadIdx.x & 31;
     const T2 *tab_l = bs.tab + (lane % TP);
     H *hist_l = bs.hist + (lane % HP);
     const float hs = rp.hs;
     const bool fixed = hs > 0.f;
-    Integrand<FAM, T, MAXD> fam;
 
     constexpr int kChunk = 8;
     const int stride = blockDim.x;
@@ -263,47 +401,12 @@ __device__ __forceinline__ void sample_range(const BlockState<MODE, PRIV> &bs,
             const int k = k0 + u * stride;
             if (k >= cnt) break;
             const unsigned long long s = s0 + static_cast<unsigned long long>(k);
-            const uint32_t slo = static_cast<uint32_t>(s), shi = static_cast<uint32_t>(s >> 32);
             SampleCells<MAXD, PACK> cellj;
-            T J = rp.jinit;
-            fam.begin(fc);
-#pragma unroll
-            for (int q = 0; q < (MAXD + 3) / 4; ++q) {
-                if (EXACT || 4 * q < d) {
-                    const uint4 r = philox4x32_10(make_uint4(slo, shi, rp.iter, static_cast<uint32_t>(q)),
-                                                  rp.key0, rp.key1);
-#pragma unroll
-                    for (int w = 0; w < 4; ++w) {
-                        const int j = 4 * q + w;
-                        if (j < MAXD && (EXACT || j < d)) {
-                            const Split sp = split_bin(word(r, w), static_cast<uint32_t>(N));
-                            const uint32_t cell = static_cast<uint32_t>(j * N) + sp.bin;
-                            const T2 ent = tab_l[cell * TP];
-                            const T m = Prec<T>::mant(sp.lo);
-                            const T x = ffma(ent.y, m, ent.x);
-                            J *= ent.y;
-                            if (sizeof(T) == 4 && (j & 3) == 3) J *= rp.n4;
-                            cellj.set(j, cell);
-                            fam.dim(j, x, fc);
-                        }
-                    }
-                }
-            }
-            T v = J * fam.finish(fc);
-            if (!isfinite(v)) {
-                v = T(0);
-                ++ts.nonfinite;
-            }
+            const T v = map_sample<FAM, MODE, MAXD, EXACT, PRIV, PACK, false>(tab_l, rp, fc, nullptr, 0u, s,
+                                                                              cellj, ts.nonfinite);
             const T v2 = v * v;
             if (MODE == ACC_F32_KAHAN) {
-                const float y1 = static_cast<float>(v) - ts.c1f;
-                const float t1 = ts.s1f + y1;
-                ts.c1f = (t1 - ts.s1f) - y1;
-                ts.s1f = t1;
-                const float y2 = static_cast<float>(v2) - ts.c2f;
-                const float t2 = ts.s2f + y2;
-                ts.c2f = (t2 - ts.s2f) - y2;
-                ts.s2f = t2;
+                kahan_add(ts, static_cast<float>(v), static_cast<float>(v2));
             } else if (MODE == ACC_F32_SUM64) {
                 p1 += static_cast<float>(v);
                 p2 += static_cast<float>(v2);
@@ -312,41 +415,7 @@ __device__ __forceinline__ void sample_range(const BlockState<MODE, PRIV> &bs,
                 ts.s1d += vd;
                 ts.s2d = __fma_rn(vd, vd, ts.s2d);
             }
-            if (MODE == ACC_F64) {
-#pragma unroll
-                for (int j = 0; j < MAXD; ++j) {
-                    if (EXACT || j < d) red_add_shared(hist_l + cellj.get(j) * HP, static_cast<H>(v2));
-                }
-            } else if (v2 == T(0)) {
-                // nothing to add
-            } else if (fixed) {
-                const float qf = static_cast<float>(v2) * hs;
-                if (qf < kFixedMax) {
-                    // rint by adding 2^23 (the integer lands in the mantissa's
-                    // low bits; exact for values below 2^23)
-                    const bool is_fine = qf < 1.0f;
-                    const float t = __fmaf_rn(qf, is_fine ? kFineScale : 1.0f, 8388608.0f);
-                    uint32_t q = __float_as_uint(t) - 0x4B000000u;
-                    q = max(q, 1u);
-                    unsigned int *base = is_fine ? bs.fine : reinterpret_cast<unsigned int *>(hist_l);
-                    const uint32_t step = is_fine ? 1u : static_cast<uint32_t>(HP);
-#pragma unroll
-                    for (int j = 0; j < MAXD; ++j) {
-                        if (EXACT || j < d) atomicAdd(base + cellj.get(j) * step, q);
-                    }
-                } else {
-#pragma unroll
-                    for (int j = 0; j < MAXD; ++j) {
-                        if (EXACT || j < d) atomicAdd(rp.acc + 2 + cellj.get(j), static_cast<double>(v2));
-                    }
-                }
-            } else {
-#pragma unroll
-                for (int j = 0; j < MAXD; ++j) {
-                    if (EXACT || j < d) red_add_shared(reinterpret_cast<float *>(hist_l) + cellj.get(j) * HP,
-                                                       static_cast<float>(v2));
-                }
-            }
+            hist_add<MODE, PRIV, MAXD, EXACT, PACK>(bs, hist_l, rp, cellj, v2, fixed, hs);
         }
         if (MODE == ACC_F32_SUM64) {
             ts.s1d += static_cast<double>(p1);
@@ -355,17 +424,126 @@ __device__ __forceinline__ void sample_range(const BlockState<MODE, PRIV> &bs,
     }
 }
 
+// Stratified form: the block samples hypercubes [h0, h0 + cnt) of one
+// integral, P samples each; thread t takes hypercubes h0 + t + u * blockDim
+// and all of their samples, so each hypercube's spread about its own mean,
+//   m2_h = sum_p (v_p - mean_h)^2 = B - A^2 / P,
+// comes from A = sum (v - c) and B = sum (v - c)^2 with c = the hypercube's
+// first value (shifted sums: no cancellation of the mean).  Samples go two at
+// a time (independent Philox and table-load chains).  In the FP32 modes the
+// partial sums of v, v^2 (FP32_SUM64) and m2 are kept in FP32 and added in
+// FP64 once a thread has taken kChunk samples since the last addition.
+template <int FAM, int MODE, int MAXD, bool EXACT, int PRIV>
+__device__ __forceinline__ void sample_range_strat(const BlockState<MODE, PRIV> &bs,
+                                                   const RangeParams<typename ModeTraits<MODE>::T> &rp,
+                                                   const FamConsts<typename ModeTraits<MODE>::T> &fc,
+                                                   const StratArgs &st, ThreadSums<MODE> &ts, uint32_t h0,
+                                                   int cnt) {
+    using BS = BlockState<MODE, PRIV>;
+    using T = typename BS::T;
+    using T2 = typename BS::T2;
+    using H = typename BS::H;
+    constexpr int TP = BS::TP;
+    constexpr int HP = BS::HP;
+    const int lane = threadIdx.x & 31;
+    const T2 *tab_l = bs.tab + (lane % TP);
+    H *hist_l = bs.hist + (lane % HP);
+    const float hs = rp.hs;
+    const bool fixed = hs > 0.f;
+    const uint32_t P = st.P;
+    const T invP = T(1) / static_cast<T>(P);
+    constexpr uint32_t kChunk = 8;
+    // generic tiers: two samples' cells in 16-bit halves (d N <= 32768), which
+    // keeps them in registers; the exact-dimension kernels have room for both
+    constexpr bool kPack = !EXACT;
+    float p1 = 0.f, p2 = 0.f;   // FP32_SUM64 partial sums of v, v^2
+    T qt = T(0);                // partial sum of m2 (FP32 modes)
+    uint32_t since = 0;         // samples since the partials were last added in FP64
+    auto flush_partials = [&]() {
+        if (MODE == ACC_F32_SUM64) {
+            ts.s1d += static_cast<double>(p1);
+            ts.s2d += static_cast<double>(p2);
+            p1 = 0.f;
+            p2 = 0.f;
+        }
+        ts.qd += static_cast<double>(qt);
+        qt = T(0);
+        since = 0;
+    };
+    auto add_sums = [&](T v, T v2) {
+        if (MODE == ACC_F32_KAHAN) {
+            kahan_add(ts, static_cast<float>(v), static_cast<float>(v2));
+        } else if (MODE == ACC_F32_SUM64) {
+            p1 += static_cast<float>(v);
+            p2 += static_cast<float>(v2);
+        } else {
+            const double vd = static_cast<double>(v);
+            ts.s1d += vd;
+            ts.s2d = __fma_rn(vd, vd, ts.s2d);
+        }
+    };
+    for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+        const uint32_t h = h0 + static_cast<uint32_t>(k);
+        const unsigned long long sb = static_cast<unsigned long long>(h) * P;
+        T c = T(0), a = T(0), b = T(0);
+        uint32_t p = 0;
+        for (; p + 1 < P; p += 2) {
+            SampleCells<MAXD, kPack> ca, cb;
+            const T va = map_sample<FAM, MODE, MAXD, EXACT, PRIV, kPack, true>(tab_l, rp, fc, &st, h, sb + p, ca,
+                                                                               ts.nonfinite);
+            const T vb = map_sample<FAM, MODE, MAXD, EXACT, PRIV, kPack, true>(tab_l, rp, fc, &st, h, sb + p + 1,
+                                                                               cb, ts.nonfinite);
+            const T va2 = va * va, vb2 = vb * vb;
+            add_sums(va, va2);
+            add_sums(vb, vb2);
+            if (p == 0) c = va;
+            const T da = va - c, db = vb - c;
+            a += da + db;
+            b = ffma(da, da, ffma(db, db, b));
+            hist_add<MODE, PRIV, MAXD, EXACT, kPack>(bs, hist_l, rp, ca, va2, fixed, hs);
+            hist_add<MODE, PRIV, MAXD, EXACT, kPack>(bs, hist_l, rp, cb, vb2, fixed, hs);
+            since += 2;
+            if (MODE == ACC_F32_SUM64 && since >= kChunk) {
+                // long hypercubes: the FP32 partials of v, v^2 stay short
+                ts.s1d += static_cast<double>(p1);
+                ts.s2d += static_cast<double>(p2);
+                p1 = 0.f;
+                p2 = 0.f;
+            }
+        }
+        if (p < P) {
+            SampleCells<MAXD, kPack> ca;
+            const T va = map_sample<FAM, MODE, MAXD, EXACT, PRIV, kPack, true>(tab_l, rp, fc, &st, h, sb + p, ca,
+                                                                               ts.nonfinite);
+            const T va2 = va * va;
+            add_sums(va, va2);
+            if (p == 0) c = va;
+            const T da = va - c;
+            a += da;
+            b = ffma(da, da, b);
+            hist_add<MODE, PRIV, MAXD, EXACT, kPack>(bs, hist_l, rp, ca, va2, fixed, hs);
+            since += 1;
+        }
+        const T m2 = b - a * a * invP;
+        qt += m2 > T(0) ? m2 : T(0);
+        if (MODE == ACC_F64 || since >= kChunk) flush_partials();
+    }
+    flush_partials();
+}
+
 // Adds the block's sums to the integral's FP64 accumulators: S1, S2 and the
 // non-finite count by a block reduction, each histogram cell by one thread.  Starts
 // with a barrier (every thread's samples are in) and ends with one (the
 // shared cells may be reused).  Resets ts.
+// q (stratified launches, else null): FP64 accumulator of the hypercube m2 sums.
 template <int MODE, int PRIV>
 __device__ __forceinline__ void flush_block(const BlockState<MODE, PRIV> &bs, ThreadSums<MODE> &ts,
-                                            float hs, double *acc, unsigned long long *n_nonfinite) {
+                                            float hs, double *acc, unsigned long long *n_nonfinite,
+                                            double *q = nullptr) {
     using BS = BlockState<MODE, PRIV>;
     using H = typename BS::H;
     constexpr int HP = BS::HP;
-    __shared__ double red1[32], red2[32];
+    __shared__ double red1[32], red2[32], redq[32];
     __shared__ unsigned int rednf[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
@@ -379,12 +557,14 @@ __device__ __forceinline__ void flush_block(const BlockState<MODE, PRIV> &bs, Th
     }
     b1 = warp_sum(b1);
     b2 = warp_sum(b2);
+    const double bq = q ? warp_sum(ts.qd) : 0.0;
     const unsigned int nf = __reduce_add_sync(0xFFFFFFFFu, ts.nonfinite);
     ts = ThreadSums<MODE>();
     __syncthreads();
     if (lane == 0) {
         red1[warp] = b1;
         red2[warp] = b2;
+        redq[warp] = bq;
         rednf[warp] = nf;
     }
     __syncthreads();
@@ -395,6 +575,10 @@ __device__ __forceinline__ void flush_block(const BlockState<MODE, PRIV> &bs, Th
         x1 = warp_sum(x1);
         x2 = warp_sum(x2);
         xn = __reduce_add_sync(0xFFFFFFFFu, xn);
+        if (q) {
+            const double xq = warp_sum(lane < nwarps ? redq[lane] : 0.0);
+            if (lane == 0) atomicAdd(q, xq);
+        }
         if (lane == 0) {
             atomicAdd(acc + 0, x1);
             atomicAdd(acc + 1, x2);
@@ -465,6 +649,43 @@ vegas_sample_kernel(const SampleArgs a) {
                                                    static_cast<unsigned long long>(a.s_begin + lo),
                                                    static_cast<int>(hi - lo));
     flush_block<MODE, PRIV>(bs, ts, rp.hs, a.acc, a.n_nonfinite);
+}
+
+// Stratified form: hypercubes [a.s_begin, a.s_begin + a.n) of P = a.st.P
+// samples each; each block takes a contiguous range of hypercubes.
+// Above 8 dimensions a block's lane-private cells take most of an SM's shared
+// memory, so one block per SM: its threads may use up to 128 registers.
+template <int FAM, int MODE, int MAXD, bool EXACT, bool PRIV>
+__global__ void __launch_bounds__(512, MAXD > 8 ? 1 : 2)
+vegas_sample_strat_kernel(const SampleArgs a) {
+    using BS = BlockState<MODE, PRIV>;
+    using T = typename BS::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int d = EXACT ? MAXD : a.d;
+    BS bs;
+    bs.carve(smem_raw, d * a.N);
+    bs.stage(a.table);
+    RangeParams<T> rp;
+    rp.d = d;
+    rp.N = a.N;
+    rp.key0 = a.key0;
+    rp.key1 = a.key1;
+    rp.iter = a.iter;
+    rp.jinit = static_cast<T>(a.jinit * (a.jmul ? *a.jmul : 1.0));
+    rp.n4 = static_cast<T>(a.nblk4);
+    rp.hs = (MODE != ACC_F64) ? *a.hscale : 0.f;
+    rp.acc = a.acc;
+    __syncthreads();
+
+    const long long per = (a.n + gridDim.x - 1) / gridDim.x;
+    const long long lo = static_cast<long long>(blockIdx.x) * per;
+    const long long hi = min(a.n, lo + per);
+    ThreadSums<MODE> ts;
+    if (hi > lo)
+        sample_range_strat<FAM, MODE, MAXD, EXACT, PRIV>(bs, rp, consts<T>(a), a.st, ts,
+                                                         static_cast<uint32_t>(a.s_begin + lo),
+                                                         static_cast<int>(hi - lo));
+    flush_block<MODE, PRIV>(bs, ts, rp.hs, a.acc, a.n_nonfinite, a.st.q);
 }
 
 }  // namespace vegas

@@ -223,6 +223,22 @@ def vegas_trace(ctx: Context, t: int, s_begin: int, count: int):
     return bins, x, w
 
 
+def vegas_set_strata(ctx: Context, B: int) -> None:
+    """Stratified + importance hybrid from the next iteration: 2^B hypercubes
+    (0: plain sampling, -1: as many as leave 2 samples per hypercube)."""
+    check(nat.load().vegas_set_strata(ctx.handle, int(B)), "vegas_set_strata")
+
+
+def vegas_get_strata(ctx: Context):
+    """(B, P, n_used) of the next iteration (B = P = 0 when plain)."""
+    B = ctypes.c_int32()
+    P = ctypes.c_int64()
+    n = ctypes.c_int64()
+    check(nat.load().vegas_get_strata(ctx.handle, ctypes.byref(B), ctypes.byref(P), ctypes.byref(n)),
+          "vegas_get_strata")
+    return B.value, P.value, n.value
+
+
 def vegas_export_state(ctx: Context) -> bytes:
     lib = nat.load()
     size = ctypes.c_size_t(0)
@@ -305,14 +321,17 @@ class Integrator:
     """
 
     def __init__(self, n_dim, n_events, events_limit=0, n_bins=50, alpha=1.5, seed=0,
-                 integral_id=0, precision="fp32_kahan", smooth=True, stream=None):
+                 integral_id=0, precision="fp32_kahan", smooth=True, stream=None, strata=0):
         self.cfg = Config(n_dim, n_events, n_bins, events_limit, alpha, seed, integral_id,
                           precision, smooth)
         self.stream = stream
+        self.strata = strata   # vegas_set_strata's B: 0 plain, -1 automatic
         self.ctx = None
 
     def compile(self, family: str, params=()):
         self.ctx = vegas_create(self.cfg, family, params, stream=self.stream)
+        if self.strata:
+            vegas_set_strata(self.ctx, self.strata)
         return self
 
     def run_integration(self, n_iter: int):
