@@ -266,6 +266,40 @@ def _time_single(V, torch, family, params, d, N, n, prec, iters, warm=2, iid=0):
             "kernel_ms": sum(kms) / max(1, len(kms)), "I": res["I"], "sigma": res["sigma"]}
 
 
+def _time_strat(V, torch, family, params, d, N, n, prec, iters=10, warm=5):
+    """Plain against stratified sampling (vegas_set_strata(-1)) on one integral:
+    kernel time per iteration, the standard error of an iteration times the
+    square root of its samples (sigma sqrt(n), the per-sample spread the
+    estimator sees), and the time to reach a given sigma relative to plain
+    sampling (sigma^2 t, lower is better)."""
+    out = {}
+    for B in (0, -1):
+        cfg = V.Config(n_dim=d, n_events=n, n_bins=N, alpha=ALPHA, seed=0, integral_id=0,
+                       precision=prec)
+        ctx = V.vegas_create(cfg, family, params)
+        V.vegas_set_strata(ctx, B)
+        for _ in range(warm):
+            V.vegas_step(ctx, sync=False)
+        V.vegas_profile(ctx, True)
+        sig = []
+        for _ in range(iters):
+            sig.append(V.vegas_step(ctx)[1])
+        kms = V.vegas_profile_read(ctx)
+        Bt, P, used = V.vegas_get_strata(ctx)
+        res = V.vegas_result(ctx)
+        V.vegas_destroy(ctx)
+        k_ms = sum(kms) / len(kms)
+        s_rms = math.sqrt(sum(x * x for x in sig) / len(sig))
+        out["stratified" if B else "plain"] = {
+            "hypercubes": 2 ** Bt if P else 0, "samples_per_hypercube": P, "samples": used,
+            "kernel_ms": k_ms, "samples_per_s": used / (k_ms / 1e3),
+            "sigma_sqrt_n": s_rms * math.sqrt(used), "I": res["I"], "sigma": res["sigma"]}
+    a, b = out["plain"], out["stratified"]
+    out["time_to_equal_sigma_vs_plain"] = (b["sigma_sqrt_n"] ** 2 / b["samples_per_s"]) / \
+        (a["sigma_sqrt_n"] ** 2 / a["samples_per_s"])
+    return out
+
+
 def _time_batched(V, torch, steps=8, warm=2):
     """The uneven 512-integral mix: one step = one iteration of every integral."""
     from paper_2010_09341_gb300 import workloads as W
@@ -372,7 +406,7 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the other workloads")
-    ap.add_argument("--only", choices=["batched", "serving", "lo", "config1"], default=None,
+    ap.add_argument("--only", choices=["batched", "serving", "lo", "config1", "strat"], default=None,
                     help="run just one of the other workloads and print its JSON (for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -397,6 +431,9 @@ def main():
         elif args.only == "config1":
             out = _time_single(V, torch, "gauss_sym", W.gauss_sym_params(0.1), 4, 50, 100_000, "fp64",
                                args.steps, warm=args.warmup)
+        elif args.only == "strat":
+            out = {fam: _time_strat(V, torch, fam, p, D, NBINS, NEVENTS, PRECISION)
+                   for fam, p in _integrals()}
         elif args.only == "lo":
             out = _time_single(V, torch, "lo", W.lo_params(), 3, 100, 100_000_000, "fp32_kahan",
                                args.steps, warm=args.warmup)
@@ -552,6 +589,9 @@ def main():
                                                              "fp64", 3)
             extra["config2_fp32_kahan_" + fam] = _time_single(V, torch, fam, p, D, NBINS, NEVENTS,
                                                               "fp32_kahan", 10)
+        for fam, p in _integrals():
+            extra["stratified_hybrid_" + fam] = _time_strat(V, torch, fam, p, D, NBINS, NEVENTS,
+                                                            PRECISION)
         extra["config3_lo_fp32_kahan"] = _time_single(V, torch, "lo", W.lo_params(), 3, 100,
                                                       100_000_000, "fp32_kahan", 10)
         extra["config4_batched"] = _time_batched(V, torch)

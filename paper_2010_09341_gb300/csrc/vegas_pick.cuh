@@ -4,6 +4,7 @@
 #pragma once
 
 #include "vegas_kernels.cuh"
+#include "vegas_strat.cuh"
 
 namespace vegas {
 

@@ -424,113 +424,6 @@ __device__ __forceinline__ void sample_range(const BlockState<MODE, PRIV> &bs,
     }
 }
 
-// Stratified form: the block samples hypercubes [h0, h0 + cnt) of one
-// integral, P samples each; thread t takes hypercubes h0 + t + u * blockDim
-// and all of their samples, so each hypercube's spread about its own mean,
-//   m2_h = sum_p (v_p - mean_h)^2 = B - A^2 / P,
-// comes from A = sum (v - c) and B = sum (v - c)^2 with c = the hypercube's
-// first value (shifted sums: no cancellation of the mean).  Samples go two at
-// a time (independent Philox and table-load chains).  In the FP32 modes the
-// partial sums of v, v^2 (FP32_SUM64) and m2 are kept in FP32 and added in
-// FP64 once a thread has taken kChunk samples since the last addition.
-template <int FAM, int MODE, int MAXD, bool EXACT, int PRIV>
-__device__ __forceinline__ void sample_range_strat(const BlockState<MODE, PRIV> &bs,
-                                                   const RangeParams<typename ModeTraits<MODE>::T> &rp,
-                                                   const FamConsts<typename ModeTraits<MODE>::T> &fc,
-                                                   const StratArgs &st, ThreadSums<MODE> &ts, uint32_t h0,
-                                                   int cnt) {
-    using BS = BlockState<MODE, PRIV>;
-    using T = typename BS::T;
-    using T2 = typename BS::T2;
-    using H = typename BS::H;
-    constexpr int TP = BS::TP;
-    constexpr int HP = BS::HP;
-    const int lane = threadIdx.x & 31;
-    const T2 *tab_l = bs.tab + (lane % TP);
-    H *hist_l = bs.hist + (lane % HP);
-    const float hs = rp.hs;
-    const bool fixed = hs > 0.f;
-    const uint32_t P = st.P;
-    const T invP = T(1) / static_cast<T>(P);
-    constexpr uint32_t kChunk = 8;
-    // generic tiers: two samples' cells in 16-bit halves (d N <= 32768), which
-    // keeps them in registers; the exact-dimension kernels have room for both
-    constexpr bool kPack = !EXACT;
-    float p1 = 0.f, p2 = 0.f;   // FP32_SUM64 partial sums of v, v^2
-    T qt = T(0);                // partial sum of m2 (FP32 modes)
-    uint32_t since = 0;         // samples since the partials were last added in FP64
-    auto flush_partials = [&]() {
-        if (MODE == ACC_F32_SUM64) {
-            ts.s1d += static_cast<double>(p1);
-            ts.s2d += static_cast<double>(p2);
-            p1 = 0.f;
-            p2 = 0.f;
-        }
-        ts.qd += static_cast<double>(qt);
-        qt = T(0);
-        since = 0;
-    };
-    auto add_sums = [&](T v, T v2) {
-        if (MODE == ACC_F32_KAHAN) {
-            kahan_add(ts, static_cast<float>(v), static_cast<float>(v2));
-        } else if (MODE == ACC_F32_SUM64) {
-            p1 += static_cast<float>(v);
-            p2 += static_cast<float>(v2);
-        } else {
-            const double vd = static_cast<double>(v);
-            ts.s1d += vd;
-            ts.s2d = __fma_rn(vd, vd, ts.s2d);
-        }
-    };
-    for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
-        const uint32_t h = h0 + static_cast<uint32_t>(k);
-        const unsigned long long sb = static_cast<unsigned long long>(h) * P;
-        T c = T(0), a = T(0), b = T(0);
-        uint32_t p = 0;
-        for (; p + 1 < P; p += 2) {
-            SampleCells<MAXD, kPack> ca, cb;
-            const T va = map_sample<FAM, MODE, MAXD, EXACT, PRIV, kPack, true>(tab_l, rp, fc, &st, h, sb + p, ca,
-                                                                               ts.nonfinite);
-            const T vb = map_sample<FAM, MODE, MAXD, EXACT, PRIV, kPack, true>(tab_l, rp, fc, &st, h, sb + p + 1,
-                                                                               cb, ts.nonfinite);
-            const T va2 = va * va, vb2 = vb * vb;
-            add_sums(va, va2);
-            add_sums(vb, vb2);
-            if (p == 0) c = va;
-            const T da = va - c, db = vb - c;
-            a += da + db;
-            b = ffma(da, da, ffma(db, db, b));
-            hist_add<MODE, PRIV, MAXD, EXACT, kPack>(bs, hist_l, rp, ca, va2, fixed, hs);
-            hist_add<MODE, PRIV, MAXD, EXACT, kPack>(bs, hist_l, rp, cb, vb2, fixed, hs);
-            since += 2;
-            if (MODE == ACC_F32_SUM64 && since >= kChunk) {
-                // long hypercubes: the FP32 partials of v, v^2 stay short
-                ts.s1d += static_cast<double>(p1);
-                ts.s2d += static_cast<double>(p2);
-                p1 = 0.f;
-                p2 = 0.f;
-            }
-        }
-        if (p < P) {
-            SampleCells<MAXD, kPack> ca;
-            const T va = map_sample<FAM, MODE, MAXD, EXACT, PRIV, kPack, true>(tab_l, rp, fc, &st, h, sb + p, ca,
-                                                                               ts.nonfinite);
-            const T va2 = va * va;
-            add_sums(va, va2);
-            if (p == 0) c = va;
-            const T da = va - c;
-            a += da;
-            b = ffma(da, da, b);
-            hist_add<MODE, PRIV, MAXD, EXACT, kPack>(bs, hist_l, rp, ca, va2, fixed, hs);
-            since += 1;
-        }
-        const T m2 = b - a * a * invP;
-        qt += m2 > T(0) ? m2 : T(0);
-        if (MODE == ACC_F64 || since >= kChunk) flush_partials();
-    }
-    flush_partials();
-}
-
 // Adds the block's sums to the integral's FP64 accumulators: S1, S2 and the
 // non-finite count by a block reduction, each histogram cell by one thread.  Starts
 // with a barrier (every thread's samples are in) and ends with one (the
@@ -649,43 +542,6 @@ vegas_sample_kernel(const SampleArgs a) {
                                                    static_cast<unsigned long long>(a.s_begin + lo),
                                                    static_cast<int>(hi - lo));
     flush_block<MODE, PRIV>(bs, ts, rp.hs, a.acc, a.n_nonfinite);
-}
-
-// Stratified form: hypercubes [a.s_begin, a.s_begin + a.n) of P = a.st.P
-// samples each; each block takes a contiguous range of hypercubes.
-// Above 8 dimensions a block's lane-private cells take most of an SM's shared
-// memory, so one block per SM: its threads may use up to 128 registers.
-template <int FAM, int MODE, int MAXD, bool EXACT, bool PRIV>
-__global__ void __launch_bounds__(512, MAXD > 8 ? 1 : 2)
-vegas_sample_strat_kernel(const SampleArgs a) {
-    using BS = BlockState<MODE, PRIV>;
-    using T = typename BS::T;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int d = EXACT ? MAXD : a.d;
-    BS bs;
-    bs.carve(smem_raw, d * a.N);
-    bs.stage(a.table);
-    RangeParams<T> rp;
-    rp.d = d;
-    rp.N = a.N;
-    rp.key0 = a.key0;
-    rp.key1 = a.key1;
-    rp.iter = a.iter;
-    rp.jinit = static_cast<T>(a.jinit * (a.jmul ? *a.jmul : 1.0));
-    rp.n4 = static_cast<T>(a.nblk4);
-    rp.hs = (MODE != ACC_F64) ? *a.hscale : 0.f;
-    rp.acc = a.acc;
-    __syncthreads();
-
-    const long long per = (a.n + gridDim.x - 1) / gridDim.x;
-    const long long lo = static_cast<long long>(blockIdx.x) * per;
-    const long long hi = min(a.n, lo + per);
-    ThreadSums<MODE> ts;
-    if (hi > lo)
-        sample_range_strat<FAM, MODE, MAXD, EXACT, PRIV>(bs, rp, consts<T>(a), a.st, ts,
-                                                         static_cast<uint32_t>(a.s_begin + lo),
-                                                         static_cast<int>(hi - lo));
-    flush_block<MODE, PRIV>(bs, ts, rp.hs, a.acc, a.n_nonfinite, a.st.q);
 }
 
 }  // namespace vegas
