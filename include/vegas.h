@@ -51,7 +51,8 @@ typedef enum {
     VEGAS_ECUDA = 3,      /* a CUDA runtime call failed                       */
     VEGAS_ETIMEOUT = 4,   /* a bounded device wait ran out                    */
     VEGAS_EBUSY = 5,      /* no free slot (batched form)                      */
-    VEGAS_ENONFINITE = 6  /* every integrand value of the iteration was non-finite */
+    VEGAS_ENONFINITE = 6, /* every integrand value of the iteration was non-finite */
+    VEGAS_EJIT = 7        /* a user integrand did not compile (vegas_jit_log)   */
 } vegas_status;
 
 /* Arithmetic of the sampling path.
@@ -93,12 +94,14 @@ typedef enum {
     VEGAS_F_GENZ_GAUSS = 4,
     VEGAS_F_GENZ_PROD = 5,
     VEGAS_F_GENZ_CORNER = 6,
-    VEGAS_F_LO = 7
+    VEGAS_F_LO = 7,
+    VEGAS_F_USER = 8      /* a user's source, vegas_create_user (not vegas_create) */
 } vegas_family;
 
 #define VEGAS_MAX_DIM 32
 #define VEGAS_MAX_BINS 1024
 #define VEGAS_MAX_ITERS 4096  /* per-iteration records kept (a ring); iterations are unbounded */
+#define VEGAS_MAX_USER_PARAMS 72  /* parameters of a user integrand */
 
 typedef struct {
     int32_t family;         /* vegas_family                                   */
@@ -150,6 +153,31 @@ size_t vegas_workspace_bytes(const vegas_config *cfg);
  * parameter count, ENOMEM if ws_bytes is below vegas_workspace_bytes. */
 vegas_status vegas_create(const vegas_config *cfg, const vegas_integrand *integrand,
                           void *stream, void *dev_workspace, size_t ws_bytes, vegas_ctx **out);
+
+/* A user integrand, as the paper's integrator takes one (Sec. 3.1: the
+ * integrand is a function of the sample array passed to compile()).  source
+ * is CUDA C++ that defines, at global scope,
+ *     template <class T> __device__ T user_integrand(const T *x, int d, const T *p);
+ * returning f at the mapped point x[0..d-1] (each in [0,1]) with parameters
+ * p[0..n_params-1] (n_params <= VEGAS_MAX_USER_PARAMS, copied at create).  T is
+ * float in the FP32 precisions and double in VEGAS_FP64; the standard math
+ * functions of both types may be called (exp, cos, pow, ...).  The library
+ * compiles it at run time with NVRTC for sm_103a together with its own
+ * sampling, stratified-sampling and trace kernels, so the integrand is inlined
+ * into the same fused kernel as the built-in families; each (source,
+ * precision, d, layout) is compiled once per process and kept loaded until
+ * exit.  The first values of f should lie within the FP32 range in the FP32
+ * precisions (v is rescaled from the second iteration on).  Everything else is
+ * as vegas_create with family VEGAS_F_USER (vegas_export_state records the
+ * parameters but not the source: import into a context made from the same
+ * source).  VEGAS_EJIT if the source does not compile or NVRTC cannot be
+ * loaded (vegas_jit_log gives the compiler's messages).  The batched form and
+ * vegas_iterate_noalloc take built-in families only. */
+vegas_status vegas_create_user(const vegas_config *cfg, const char *source, const double *params,
+                               int32_t n_params, void *stream, void *dev_workspace, size_t ws_bytes,
+                               vegas_ctx **out);
+/* The compiler's messages of this thread's last vegas_create_user. */
+const char *vegas_jit_log(void);
 
 /* Run one iteration on the current grid: sample, accumulate S1, S2 and the
  * histograms, then form I_t, sigma_t and update the combination on the

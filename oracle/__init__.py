@@ -32,6 +32,7 @@ FAMILIES = {
     "genz_prod": 5,
     "genz_corner": 6,
     "lo": 7,
+    "user": 8,
 }
 
 _lib = None
@@ -87,6 +88,8 @@ def _load():
         lib.oracle_refine.restype = None
         lib.oracle_combine.argtypes = [i32, dp, dp, dp, dp, dp]
         lib.oracle_combine.restype = None
+        lib.oracle_set_user.argtypes = [ctypes.c_void_p]
+        lib.oracle_set_user.restype = None
         lib.oracle_strata_bits.argtypes = [i32, i32, ip]
         lib.oracle_strata_bits.restype = None
         lib.oracle_sample_strat.argtypes = [i32, i32, dp, i32, dp, i32, u32, u32, u32, i32, i64,
@@ -367,3 +370,11 @@ def integrate_strat(d, N, family, params, B, P, n_iter, alpha=1.5, seed=0, integ
         e = refine(d, N, acc["hist"], e, alpha, smooth)
     Ib, sb, c2 = combine([a for a, _ in its], [b for _, b in its])
     return {"I": Ib, "sigma": sb, "chi2_dof": c2, "iters": its, "edges": e}
+
+
+# ------------------------------------------------------- user integrands
+def set_user(fn_address: int) -> None:
+    """Family "user" evaluates the host function at fn_address,
+    double f(const double *x, int d, const double *p) (the test compiles the
+    user's source for the host)."""
+    _load().oracle_set_user(ctypes.c_void_p(fn_address))

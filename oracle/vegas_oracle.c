@@ -121,9 +121,15 @@ static double lo_integrand(const double *x, const double *p) {
     return lo_density(x[0]) * lo_density(x[1]) * bw * (1.0 + c * c) / shat * 2.0 * norm;
 }
 
+static oracle_user_fn g_user_fn = 0;
+
+void oracle_set_user(oracle_user_fn f) { g_user_fn = f; }
+
 double oracle_integrand(int family, int d, const double *p, int n_params, const double *x) {
     (void)n_params;
     switch (family) {
+    case ORACLE_F_USER:
+        return g_user_fn ? g_user_fn(x, d, p) : 0.0;
     case ORACLE_F_CONST:
         return 1.0;
     case ORACLE_F_SUM: {

@@ -29,8 +29,14 @@ enum {
     ORACLE_F_GENZ_GAUSS = 4,/* f = exp(-sum c_i^2 (x_i - w_i)^2)              */
     ORACLE_F_GENZ_PROD = 5, /* f = prod (c_i^-2 + (x_i - w_i)^2)^-1           */
     ORACLE_F_GENZ_CORNER = 6,/* f = (1 + sum c_i x_i)^-(d+1)                  */
-    ORACLE_F_LO = 7         /* LO-style 2->2 toy, d = 3 (see the .c file)     */
+    ORACLE_F_LO = 7,        /* LO-style 2->2 toy, d = 3 (see the .c file)     */
+    ORACLE_F_USER = 8       /* the function set by oracle_set_user            */
 };
+
+/* The integrand of ORACLE_F_USER: f(x, d, params), FP64, set by the test
+ * from the user's source compiled for the host (one per process). */
+typedef double (*oracle_user_fn)(const double *x, int d, const double *params);
+void oracle_set_user(oracle_user_fn f);
 
 /* Philox4x32-10 block function (Salmon, Moraes, Dror, Shaw, SC'11). */
 void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);

@@ -12,11 +12,13 @@ import os
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libvegas.so")
 
-VEGAS_OK, VEGAS_EINVAL, VEGAS_ENOMEM, VEGAS_ECUDA, VEGAS_ETIMEOUT, VEGAS_EBUSY, VEGAS_ENONFINITE = range(7)
+(VEGAS_OK, VEGAS_EINVAL, VEGAS_ENOMEM, VEGAS_ECUDA, VEGAS_ETIMEOUT, VEGAS_EBUSY, VEGAS_ENONFINITE,
+ VEGAS_EJIT) = range(8)
 VEGAS_FP64, VEGAS_FP32_ACC64, VEGAS_FP32_KAHAN = 0, 1, 2
 PRECISIONS = {"fp64": VEGAS_FP64, "fp32_acc64": VEGAS_FP32_ACC64, "fp32_kahan": VEGAS_FP32_KAHAN}
 FAMILIES = {"const": 0, "sum": 1, "gauss_sym": 2, "genz_osc": 3, "genz_gauss": 4,
-            "genz_prod": 5, "genz_corner": 6, "lo": 7}
+            "genz_prod": 5, "genz_corner": 6, "lo": 7, "user": 8}
+MAX_USER_PARAMS = 72
 MAX_DIM, MAX_BINS, MAX_ITERS = 32, 1024, 4096
 
 
@@ -55,6 +57,8 @@ class VegasError(RuntimeError):
         lib = load()
         msg = lib.vegas_strerror(status).decode()
         extra = lib.vegas_last_error_string().decode() if status == VEGAS_ECUDA else ""
+        if status == VEGAS_EJIT:
+            extra = lib.vegas_jit_log().decode(errors="replace").strip()
         super().__init__("%s: %s%s" % (what, msg, (" (" + extra + ")") if extra else ""))
 
 
@@ -84,6 +88,10 @@ _SIGS = {
     "vegas_set_iteration": (ctypes.c_int, [_P, ctypes.c_int32]),
     "vegas_trace": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, _P, _P, _P]),
     "vegas_set_strata": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "vegas_create_user": (ctypes.c_int, [ctypes.POINTER(VegasConfig), ctypes.c_char_p,
+                                         ctypes.POINTER(ctypes.c_double), ctypes.c_int32, _P, _P,
+                                         ctypes.c_size_t, ctypes.POINTER(_P)]),
+    "vegas_jit_log": (ctypes.c_char_p, []),
     "vegas_get_strata": (ctypes.c_int, [_P, _P, _P, _P]),
     "vegas_export_state": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_size_t)]),
     "vegas_import_state": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),

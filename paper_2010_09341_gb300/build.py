@@ -31,6 +31,33 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libvegas.so")
 
 
+# Kernel headers compiled again at run time, with a user integrand (NVRTC):
+# embedded in the library as string literals by gen_jit_sources().
+JIT_HEADERS = ["vegas_device.cuh", "vegas_sample.cuh", "vegas_strat.cuh", "vegas_trace.cuh"]
+JIT_GEN = os.path.join(CSRC, "_jit_sources.h")
+
+
+def gen_jit_sources() -> None:
+    """Write csrc/_jit_sources.h: each header of JIT_HEADERS as a raw string
+    literal, in a table of (name, text) for the run-time compiler."""
+    deps = [os.path.join(CSRC, h) for h in JIT_HEADERS]
+    if not _stale(JIT_GEN, deps + [os.path.abspath(__file__)]):
+        return
+    delim = "vegasjitsrc"
+    out = ["// Generated by build.py from the kernel headers: do not edit.",
+           "#pragma once", "namespace vegas {", "struct JitHeader { const char *name; const char *text; };",
+           "static const JitHeader kJitHeaders[] = {"]
+    for h in JIT_HEADERS:
+        txt = open(os.path.join(CSRC, h)).read()
+        assert ")" + delim not in txt
+        out.append('    {"%s", R"%s(%s)%s"},' % (h, delim, txt, delim))
+    out += ["};", "static const int kJitHeaderCount = %d;" % len(JIT_HEADERS), "}  // namespace vegas", ""]
+    tmp = JIT_GEN + ".tmp%d" % os.getpid()
+    with open(tmp, "w") as f:
+        f.write("\n".join(out))
+    os.replace(tmp, JIT_GEN)
+
+
 def _sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
@@ -51,6 +78,7 @@ def _stale(target, deps):
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     """Compile every csrc/*.cu and link libvegas.so; returns its path."""
     os.makedirs(BUILD, exist_ok=True)
+    gen_jit_sources()
     cc = nvcc()
     srcs = _sources()
     hdrs = _headers()
@@ -78,7 +106,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
             list(ex.map(run, jobs))
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + ".tmp%d" % os.getpid()
-        run([cc, *ARCH, "-shared", "-o", tmp, *objs])
+        run([cc, *ARCH, "-shared", "-o", tmp, *objs, "-ldl"])
         os.replace(tmp, LIB)
     return LIB
 

@@ -214,6 +214,7 @@ struct vegas_ctx {
     int strat_req = 0;  // requested 2^B hypercubes: 0 off, -1 automatic, else B
     const void *kfn_strat = nullptr;
     int max_blocks_strat = 0;
+    JitKernels jit;     // user integrand's run-time compiled kernels (family VEGAS_F_USER)
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;  // event pool
     size_t ev_used = 0;
 
@@ -236,6 +237,7 @@ const char *vegas_strerror(vegas_status st) {
     case VEGAS_ETIMEOUT: return "device wait timed out";
     case VEGAS_EBUSY: return "no free slot";
     case VEGAS_ENONFINITE: return "every integrand value was non-finite";
+    case VEGAS_EJIT: return "the user integrand could not be compiled";
     default: return "unknown status";
     }
 }
@@ -257,15 +259,19 @@ size_t vegas_workspace_bytes(const vegas_config *cfg) {
     return layout_for(cfg->n_dim, cfg->n_bins).total;
 }
 
-vegas_status vegas_create(const vegas_config *cfg, const vegas_integrand *itg, void *stream,
-                          void *dev_workspace, size_t ws_bytes, vegas_ctx **out) {
+// vegas_create and vegas_create_user: source == nullptr for a built-in family.
+static vegas_status create_impl(const vegas_config *cfg, const vegas_integrand *itg, const char *source,
+                                void *stream, void *dev_workspace, size_t ws_bytes, vegas_ctx **out) {
     if (!out) return VEGAS_EINVAL;
     *out = nullptr;
     if (!config_ok(cfg) || !itg) return VEGAS_EINVAL;
     const int d = cfg->n_dim, N = cfg->n_bins;
     if (itg->n_dim != d) return VEGAS_EINVAL;
-    const int np = n_params_for(itg->family, d);
-    if (np < 0 || itg->n_params != np || (np > 0 && !itg->params)) return VEGAS_EINVAL;
+    const bool user = source != nullptr;
+    if (user != (itg->family == VEGAS_F_USER)) return VEGAS_EINVAL;
+    const int np = user ? itg->n_params : n_params_for(itg->family, d);
+    if (np < 0 || np > VEGAS_MAX_USER_PARAMS || itg->n_params != np || (np > 0 && !itg->params))
+        return VEGAS_EINVAL;
     if (itg->family == VEGAS_F_LO && d != 3) return VEGAS_EINVAL;
     const Layout L = layout_for(d, N);
     if (!dev_workspace || (reinterpret_cast<uintptr_t>(dev_workspace) % kAlign) != 0)
@@ -274,7 +280,17 @@ vegas_status vegas_create(const vegas_config *cfg, const vegas_integrand *itg, v
 
     FamilyConsts fc;
     double norm = 1.0, fmax = 1.0;
-    if (!prepare_family(itg->family, d, itg->params, fc, norm, fmax)) return VEGAS_EINVAL;
+    if (user) {
+        // the parameters in order through p[], q[], s[] (one FP64 array of 72)
+        memset(&fc, 0, sizeof(fc));
+        double *flat = reinterpret_cast<double *>(&fc);
+        for (int k = 0; k < np; ++k) {
+            if (!std::isfinite(itg->params[k])) return VEGAS_EINVAL;
+            flat[k] = itg->params[k];
+        }
+    } else if (!prepare_family(itg->family, d, itg->params, fc, norm, fmax)) {
+        return VEGAS_EINVAL;
+    }
 
     cudaError_t err;
     const DeviceInfo di = device_info(&err);
@@ -288,7 +304,17 @@ vegas_status vegas_create(const vegas_config *cfg, const vegas_integrand *itg, v
     bool priv = sample_smem(mode, true, d, N) <= budget;
     const size_t smem = sample_smem(mode, priv, d, N);
     if (smem > budget) return VEGAS_EINVAL;  // d N too large for shared memory
-    const void *fn = sample_kernel(mode, itg->family, d, priv);
+    JitKernels jit;
+    if (user) {
+        const int rc = jit_user_kernels(source, mode, d, priv, &jit, nullptr);
+        if (rc != 0) {
+            snprintf(g_last_error, sizeof(g_last_error), "vegas_create_user: %s",
+                     rc == 1 ? "the run-time compiler could not be loaded"
+                             : (rc == 2 ? "the source did not compile (vegas_jit_log)" : "loading the module failed"));
+            return rc == 3 ? VEGAS_ECUDA : VEGAS_EJIT;
+        }
+    }
+    const void *fn = user ? jit.sample : sample_kernel(mode, itg->family, d, priv);
     if (!fn) return VEGAS_EINVAL;
     VEGAS_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   static_cast<int>(smem)));
@@ -300,6 +326,7 @@ vegas_status vegas_create(const vegas_config *cfg, const vegas_integrand *itg, v
     vegas_ctx *c = new vegas_ctx();
     c->cfg = *cfg;
     c->family = itg->family;
+    c->jit = jit;
     c->mode = mode;
     c->params.assign(itg->params, itg->params + np);
     c->stream = static_cast<cudaStream_t>(stream);
@@ -355,6 +382,25 @@ vegas_status vegas_create(const vegas_config *cfg, const vegas_integrand *itg, v
     *out = c;
     return VEGAS_OK;
 }
+
+vegas_status vegas_create(const vegas_config *cfg, const vegas_integrand *itg, void *stream,
+                          void *dev_workspace, size_t ws_bytes, vegas_ctx **out) {
+    return create_impl(cfg, itg, nullptr, stream, dev_workspace, ws_bytes, out);
+}
+
+vegas_status vegas_create_user(const vegas_config *cfg, const char *source, const double *params,
+                               int32_t n_params, void *stream, void *dev_workspace, size_t ws_bytes,
+                               vegas_ctx **out) {
+    if (!source || !cfg) return VEGAS_EINVAL;
+    vegas_integrand itg;
+    itg.family = VEGAS_F_USER;
+    itg.n_dim = cfg->n_dim;
+    itg.params = params;
+    itg.n_params = n_params;
+    return create_impl(cfg, &itg, source, stream, dev_workspace, ws_bytes, out);
+}
+
+const char *vegas_jit_log(void) { return jit_last_log(); }
 
 // Stratification in effect for n samples: 2^B hypercubes of P samples, with
 // B = the requested B (or, automatically, as many as leave P >= 2), never more
@@ -697,14 +743,18 @@ vegas_status vegas_trace(vegas_ctx *c, int32_t t, int64_t s_begin, int64_t count
         if (s_begin + count > sg.H * sg.P) return VEGAS_EINVAL;
         fill_strata(a, sg, c->cfg.n_dim, nullptr);
     }
-    VEGAS_CK(launch_trace(a, c->family, c->mode, 1.0 / c->scale, bins, x, w, c->stream));
+    if (c->family == VEGAS_F_USER)
+        VEGAS_CK(launch_trace_fn(c->jit.trace, a, 1.0 / c->scale, bins, x, w, c->stream));
+    else
+        VEGAS_CK(launch_trace(a, c->family, c->mode, 1.0 / c->scale, bins, x, w, c->stream));
     return VEGAS_OK;
 }
 
 vegas_status vegas_set_strata(vegas_ctx *c, int32_t B) {
     if (!c || B < -1 || B > 31) return VEGAS_EINVAL;
     if (B != 0 && !c->kfn_strat) {
-        const void *fn = sample_strat_kernel(c->mode, c->family, c->cfg.n_dim, c->priv);
+        const void *fn = c->family == VEGAS_F_USER ? c->jit.strat
+                                                   : sample_strat_kernel(c->mode, c->family, c->cfg.n_dim, c->priv);
         if (!fn) return VEGAS_EINVAL;
         VEGAS_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       static_cast<int>(c->smem)));

@@ -8,6 +8,7 @@
 // launch latency, not arithmetic.
 #include "vegas_kernels.cuh"
 #include "vegas_refine.cuh"
+#include "vegas_trace.cuh"
 
 namespace vegas {
 
@@ -188,55 +189,7 @@ cudaError_t launch_table_from_edges(const double *edges, void *table, int mode, 
 }
 
 // ---------------------------------------------------------------- trace
-// One thread per sample; the same split, map, Jacobian and integrand code as
-// the sampling kernel, reading the table from global memory.
-template <int FAM, int MODE, int MAXD>
-__global__ void trace_kernel(const SampleArgs a, double inv_scale, int32_t *bins, double *xs,
-                             double *ws) {
-    using T = typename ModeTraits<MODE>::T;
-    using T2 = typename Prec<T>::T2;
-    const long long k = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (k >= a.n) return;
-    const int d = a.d, N = a.N;
-    const T2 *tab = static_cast<const T2 *>(a.table);
-    Integrand<FAM, T, MAXD> fam;
-    const FamConsts<T> &fc = consts<T>(a);
-    const unsigned long long s = static_cast<unsigned long long>(a.s_begin + k);
-    const uint32_t slo = static_cast<uint32_t>(s), shi = static_cast<uint32_t>(s >> 32);
-    const double jm = a.jmul ? *a.jmul : 1.0;
-    T J = static_cast<T>(a.jinit * jm);
-    const T n4 = static_cast<T>(a.nblk4);
-    fam.begin(fc);
-#pragma unroll
-    for (int q = 0; q < (MAXD + 3) / 4; ++q) {
-        if (4 * q < d) {
-            const uint4 r = philox4x32_10(make_uint4(slo, shi, a.iter, static_cast<uint32_t>(q)),
-                                          a.key0, a.key1);
-#pragma unroll
-            for (int w = 0; w < 4; ++w) {
-                const int j = 4 * q + w;
-                if (j < MAXD && j < d) {
-                    uint32_t rw = word(r, w);
-                    if (a.st.P > 0) rw = strat_word(rw, static_cast<uint32_t>(s / a.st.P), a.st.off[j], a.st.bits[j]);
-                    const Split sp = split_bin(rw, static_cast<uint32_t>(N));
-                    const uint32_t cell = static_cast<uint32_t>(j * N) + sp.bin;
-                    const T2 ent = tab[cell];
-                    const T m = Prec<T>::mant(sp.lo);
-                    const T x = ffma(ent.y, m, ent.x);
-                    J *= ent.y;
-                    if (sizeof(T) == 4 && (j & 3) == 3) J *= n4;
-                    fam.dim(j, x, fc);
-                    if (bins) bins[k * d + j] = static_cast<int32_t>(sp.bin);
-                    if (xs) xs[k * d + j] = static_cast<double>(x);
-                }
-            }
-        }
-    }
-    T v = J * fam.finish(fc);
-    if (a.st.P > 0 && !isfinite(v)) v = T(0);  // stratified: non-finite counts as 0
-    if (ws) ws[k] = static_cast<double>(v) * (inv_scale / jm);
-}
-
+// trace_kernel: vegas_trace.cuh
 template <int MODE, int FAM>
 static const void *trace_pick(int tier) {
     switch (tier) {
@@ -270,6 +223,11 @@ cudaError_t launch_trace(const SampleArgs &a, int fam, int mode, double inv_scal
     // only changes how sums are kept, which the trace does not do.
     if (mode == ACC_F64) fn = trace_pick_fam<ACC_F64>(fam, tier);
     else fn = trace_pick_fam<ACC_F32_KAHAN>(fam, tier);
+    return launch_trace_fn(fn, a, inv_scale, bins, x, w, stream);
+}
+
+cudaError_t launch_trace_fn(const void *fn, const SampleArgs &a, double inv_scale, int32_t *bins,
+                            double *x, double *w, cudaStream_t stream) {
     if (!fn) return cudaErrorInvalidValue;
     if (a.n <= 0) return cudaSuccess;
     const unsigned threads = 256;

@@ -10,8 +10,24 @@
 // histograms live in shared memory.
 #pragma once
 
+#ifdef __CUDACC_RTC__
+// Run-time compilation (NVRTC, user integrands) has no standard headers: the
+// fixed-width integer types the kernels use.
+typedef unsigned int uint32_t;
+typedef int int32_t;
+typedef unsigned long long uint64_t;
+typedef long long int64_t;
+typedef unsigned long size_t;
+#else
 #include <cstdint>
 #include <cuda_runtime.h>
+#endif
+
+// The user integrand of the F_USER family: defined, at global scope, by the
+// source passed to vegas_create_user and compiled with these headers at run
+// time.  x: the d mapped coordinates, p: the parameters, in the path's
+// precision T (float in the FP32 modes, double in the FP64 mode).
+template <class T> __device__ T user_integrand(const T *x, int d, const T *p);
 
 namespace vegas {
 
@@ -88,8 +104,10 @@ enum Family : int {
     F_GENZ_GAUSS = 4,
     F_GENZ_PROD = 5,
     F_GENZ_CORNER = 6,
-    F_LO = 7
+    F_LO = 7,
+    F_USER = 8   // user source, compiled at run time (vegas_create_user)
 };
+
 
 // Per-integral constants a family needs, prepared on the host in FP64 and
 // passed to the kernels in both precisions:
@@ -155,10 +173,14 @@ __device__ __forceinline__ double frcp(double x) { return 1.0 / x; }
 //   GENZ_PROD    prod *= q_j^2... see below        f = 1/prod
 //   GENZ_CORNER  acc += p_j x  (acc0 = 1)          f = 2^(-(d+1) log2 acc)
 //   LO           x kept in registers               f from s0..s6
+//   USER         x kept in registers               f = user_integrand(x, d, p), p = the
+//                                                  parameters in p[], q[], s[] in order
 template <int FAM, class T, int MAXD> struct Integrand {
     using C = FamConsts<T>;
     T acc;
     T x0, x1, x2;
+    T xs[FAM == F_USER ? MAXD : 1];
+    int nd;
 
     __device__ __forceinline__ void begin(const C &fc) {
         if (FAM == F_GENZ_OSC) acc = fc.s[1];     // 2 pi u
@@ -187,6 +209,9 @@ template <int FAM, class T, int MAXD> struct Integrand {
             if (j == 0) x0 = x;
             else if (j == 1) x1 = x;
             else if (j == 2) x2 = x;
+        } else if (FAM == F_USER) {
+            xs[FAM == F_USER ? j : 0] = x;
+            nd = j + 1;
         }
     }
 
@@ -199,6 +224,7 @@ template <int FAM, class T, int MAXD> struct Integrand {
         if (FAM == F_GENZ_GAUSS) return fexp2(s0 * acc);
         if (FAM == F_GENZ_PROD) return frcp(acc);
         if (FAM == F_GENZ_CORNER) return fexp2(s0 * flog2(acc));
+        if (FAM == F_USER) return ::user_integrand<T>(xs, nd, reinterpret_cast<const T *>(&fc));
         if (FAM == F_LO) {
             // s0 = sqrtS^2, s1 = M^2, s2 = (M Gamma)^2, s3 = cut,
             // s4 = mll_lo^2, s5 = mll_hi^2; the constant 2 (35/32)^2 norm is

@@ -94,6 +94,24 @@ cudaError_t launch_table_from_edges(const double *edges, void *table, int mode, 
 cudaError_t launch_trace(const SampleArgs &a, int fam, int mode, double inv_scale, int32_t *bins,
                          double *x, double *w, cudaStream_t stream);
 
+// The same with the trace kernel given (a run-time compiled user integrand's).
+cudaError_t launch_trace_fn(const void *fn, const SampleArgs &a, double inv_scale, int32_t *bins,
+                            double *x, double *w, cudaStream_t stream);
+
+// Kernels of a user integrand compiled at run time (vegas_jit.cu): sampling,
+// stratified sampling and trace for one (mode, d, layout).
+struct JitKernels {
+    const void *sample = nullptr;
+    const void *strat = nullptr;
+    const void *trace = nullptr;
+};
+// 0: compiled (or found in the cache); 1: the run-time compiler could not be
+// loaded; 2: the source did not compile (log holds the compiler's messages);
+// 3: a CUDA call failed (log holds its message).
+int jit_user_kernels(const char *source, int mode, int d, bool priv, JitKernels *out, const char **log);
+// The compiler's messages of this thread's last run-time compilation.
+const char *jit_last_log();
+
 cudaError_t launch_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out, long long n,
                           cudaStream_t stream);
 

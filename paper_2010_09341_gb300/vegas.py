@@ -69,7 +69,11 @@ def vegas_workspace_bytes(cfg: Config) -> int:
     return int(nat.load().vegas_workspace_bytes(ctypes.byref(c)))
 
 
-def vegas_create(cfg: Config, family: str, params=(), stream=None, workspace=None) -> Context:
+def vegas_create(cfg: Config, family: str, params=(), stream=None, workspace=None,
+                 source: str = None) -> Context:
+    """A context for a built-in family, or, with family "user", for the CUDA C++
+    ``source`` defining ``template <class T> __device__ T user_integrand(const
+    T *x, int d, const T *p)`` (compiled at run time by the library)."""
     lib = nat.load()
     c = cfg.to_c()
     nbytes = lib.vegas_workspace_bytes(ctypes.byref(c))
@@ -78,14 +82,21 @@ def vegas_create(cfg: Config, family: str, params=(), stream=None, workspace=Non
     if workspace is None:
         workspace = torch.empty(int(nbytes), dtype=torch.uint8, device="cuda")
     p = np.ascontiguousarray(np.asarray(params, dtype=np.float64))
-    itg = nat.VegasIntegrand(nat.FAMILIES[family], int(cfg.n_dim),
-                             p.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if p.size else None,
-                             int(p.size))
+    pp = p.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if p.size else None
     stream, sp = _stream_ptr(stream)
     h = ctypes.c_void_p()
-    check(lib.vegas_create(ctypes.byref(c), ctypes.byref(itg), sp,
-                           ctypes.c_void_p(workspace.data_ptr()), ctypes.c_size_t(workspace.numel()),
-                           ctypes.byref(h)), "vegas_create")
+    if family == "user":
+        if source is None:
+            raise ValueError("family 'user' needs the integrand's source")
+        check(lib.vegas_create_user(ctypes.byref(c), source.encode(), pp, int(p.size), sp,
+                                    ctypes.c_void_p(workspace.data_ptr()),
+                                    ctypes.c_size_t(workspace.numel()), ctypes.byref(h)),
+              "vegas_create_user")
+    else:
+        itg = nat.VegasIntegrand(nat.FAMILIES[family], int(cfg.n_dim), pp, int(p.size))
+        check(lib.vegas_create(ctypes.byref(c), ctypes.byref(itg), sp,
+                               ctypes.c_void_p(workspace.data_ptr()), ctypes.c_size_t(workspace.numel()),
+                               ctypes.byref(h)), "vegas_create")
     return Context(h, cfg, family, p, workspace, stream)
 
 
@@ -328,8 +339,13 @@ class Integrator:
         self.strata = strata   # vegas_set_strata's B: 0 plain, -1 automatic
         self.ctx = None
 
-    def compile(self, family: str, params=()):
-        self.ctx = vegas_create(self.cfg, family, params, stream=self.stream)
+    def compile(self, integrand: str, params=()):
+        """A built-in family's name, or CUDA C++ source defining user_integrand
+        (the paper's compile(integrand); compiled at run time)."""
+        if integrand in nat.FAMILIES:
+            self.ctx = vegas_create(self.cfg, integrand, params, stream=self.stream)
+        else:
+            self.ctx = vegas_create(self.cfg, "user", params, stream=self.stream, source=integrand)
         if self.strata:
             vegas_set_strata(self.ctx, self.strata)
         return self
