@@ -300,6 +300,50 @@ def _time_strat(V, torch, family, params, d, N, n, prec, iters=10, warm=5):
     return out
 
 
+USER_GENZ_GAUSS = r"""
+template <class T> __device__ T user_integrand(const T *x, int d, const T *p) {
+    T q = T(0);
+    for (int j = 0; j < d; ++j) {
+        const T t = p[j] * (x[j] - p[d + j]);
+        q += t * t;
+    }
+    return exp(-q);
+}
+"""
+
+
+def _time_user(V, torch, d=8, N=NBINS, n=NEVENTS, prec=PRECISION, iters=10, warm=3):
+    """A user integrand compiled at run time (the Genz Gaussian as user source,
+    d = 8, c ~ U(0.5, 5), w ~ U(0, 1), seed 2) against the same integrand as the
+    built-in family: run-time compilation time and kernel time per iteration."""
+    from paper_2010_09341_gb300 import workloads as W
+    p = W.genz_params("genz_gauss", d, seed=2)
+    out = {}
+    for kind in ("user", "builtin"):
+        cfg = V.Config(n_dim=d, n_events=n, n_bins=N, alpha=ALPHA, seed=0, integral_id=0,
+                       precision=prec)
+        t0 = time.perf_counter()
+        if kind == "user":
+            ctx = V.vegas_create(cfg, "user", p, source=USER_GENZ_GAUSS + "\n// %d\n" % os.getpid())
+        else:
+            ctx = V.vegas_create(cfg, "genz_gauss", p)
+        t_create = time.perf_counter() - t0
+        for _ in range(warm):
+            V.vegas_step(ctx, sync=False)
+        V.vegas_profile(ctx, True)
+        for _ in range(iters):
+            V.vegas_step(ctx, sync=False)
+        kms = V.vegas_profile_read(ctx)
+        res = V.vegas_result(ctx)
+        V.vegas_destroy(ctx)
+        k_ms = sum(kms) / len(kms)
+        out[kind] = {"create_s": t_create, "kernel_ms": k_ms, "samples_per_s": n / (k_ms / 1e3),
+                     "I": res["I"], "sigma": res["sigma"]}
+    out["workload"] = "Genz Gaussian d=%d, %d bins, %g samples/iter, %s; user source vs built-in family" % (
+        d, N, n, prec)
+    return out
+
+
 def _time_batched(V, torch, steps=8, warm=2):
     """The uneven 512-integral mix: one step = one iteration of every integral."""
     from paper_2010_09341_gb300 import workloads as W
@@ -406,7 +450,7 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the other workloads")
-    ap.add_argument("--only", choices=["batched", "serving", "lo", "config1", "strat"], default=None,
+    ap.add_argument("--only", choices=["batched", "serving", "lo", "config1", "strat", "user"], default=None,
                     help="run just one of the other workloads and print its JSON (for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -434,6 +478,8 @@ def main():
         elif args.only == "strat":
             out = {fam: _time_strat(V, torch, fam, p, D, NBINS, NEVENTS, PRECISION)
                    for fam, p in _integrals()}
+        elif args.only == "user":
+            out = _time_user(V, torch)
         elif args.only == "lo":
             out = _time_single(V, torch, "lo", W.lo_params(), 3, 100, 100_000_000, "fp32_kahan",
                                args.steps, warm=args.warmup)
@@ -592,6 +638,7 @@ def main():
         for fam, p in _integrals():
             extra["stratified_hybrid_" + fam] = _time_strat(V, torch, fam, p, D, NBINS, NEVENTS,
                                                             PRECISION)
+        extra["user_integrand_genz_gauss_d8"] = _time_user(V, torch)
         extra["config3_lo_fp32_kahan"] = _time_single(V, torch, "lo", W.lo_params(), 3, 100,
                                                       100_000_000, "fp32_kahan", 10)
         extra["config4_batched"] = _time_batched(V, torch)
