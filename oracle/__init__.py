@@ -33,6 +33,7 @@ FAMILIES = {
     "genz_corner": 6,
     "lo": 7,
     "user": 8,
+    "lo_pdf": 9,
 }
 
 _lib = None
@@ -88,6 +89,11 @@ def _load():
         lib.oracle_refine.restype = None
         lib.oracle_combine.argtypes = [i32, dp, dp, dp, dp, dp]
         lib.oracle_combine.restype = None
+        lib.oracle_set_pdf_grid.argtypes = [i32, i32, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                            ctypes.c_double, dp]
+        lib.oracle_set_pdf_grid.restype = None
+        lib.oracle_pdf_xg.argtypes = [ctypes.c_double, ctypes.c_double]
+        lib.oracle_pdf_xg.restype = ctypes.c_double
         lib.oracle_set_user.argtypes = [ctypes.c_void_p]
         lib.oracle_set_user.restype = None
         lib.oracle_strata_bits.argtypes = [i32, i32, ip]
@@ -378,3 +384,20 @@ def set_user(fn_address: int) -> None:
     double f(const double *x, int d, const double *p) (the test compiles the
     user's source for the host)."""
     _load().oracle_set_user(ctypes.c_void_p(fn_address))
+
+
+# ------------------------------------------------------ parton-density grid
+_pdf_keep = []
+
+
+def set_pdf_grid(xg, u0, u1, v0, v1) -> None:
+    """Family "lo_pdf" takes x g(x, Q^2) from xg (nx x nq) on uniform knots in
+    ln x from u0 to u1 and ln Q^2 from v0 to v1."""
+    t = _f64(xg)
+    nx, nq = t.shape
+    _pdf_keep[:] = [t]
+    _load().oracle_set_pdf_grid(nx, nq, u0, u1, v0, v1, _dptr(t))
+
+
+def pdf_xg(x: float, q2: float) -> float:
+    return float(_load().oracle_pdf_xg(x, q2))

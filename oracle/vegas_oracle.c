@@ -93,6 +93,7 @@ int oracle_n_params(int family, int d) {
     case ORACLE_F_GENZ_PROD: return 2 * d;      /* c_1..c_d, w_1..w_d        */
     case ORACLE_F_GENZ_CORNER: return d;        /* c_1..c_d                  */
     case ORACLE_F_LO: return 7;                 /* sqrtS M Gamma cut lo hi norm */
+    case ORACLE_F_LO_PDF: return 7;             /* the same; g from the grid   */
     default: return -1;
     }
 }
@@ -121,6 +122,99 @@ static double lo_integrand(const double *x, const double *p) {
     return lo_density(x[0]) * lo_density(x[1]) * bw * (1.0 + c * c) / shat * 2.0 * norm;
 }
 
+/* ---------------------------------------------------- parton-density grid */
+/* A tabulated density as the paper's companion tool evaluates them (PDFFlow,
+ * Sec. 2): values of x g(x, Q^2) on a uniform grid in (u, v) = (ln x, ln Q^2),
+ * interpolated by cubic Hermite polynomials in each variable (the tensor
+ * product, first along u at four v-knots, then along v), with the tangent at a
+ * knot the central difference of its neighbours, and the one-sided difference
+ * at the first and last knot.  Outside the grid, u and v are clamped to it. */
+static int g_pdf_nx = 0, g_pdf_nq = 0;
+static double g_pdf_u0, g_pdf_u1, g_pdf_v0, g_pdf_v1;
+static const double *g_pdf_xg = 0;
+
+void oracle_set_pdf_grid(int nx, int nq, double u0, double u1, double v0, double v1, const double *xg) {
+    g_pdf_nx = nx;
+    g_pdf_nq = nq;
+    g_pdf_u0 = u0;
+    g_pdf_u1 = u1;
+    g_pdf_v0 = v0;
+    g_pdf_v1 = v1;
+    g_pdf_xg = xg;
+}
+
+/* Cubic Hermite basis on [0, 1]: value at t of the cubic with values y0, y1
+ * and slopes m0, m1 (per unit t) at t = 0, 1. */
+static double hermite(double t, double y0, double y1, double m0, double m1) {
+    double t2 = t * t, t3 = t2 * t;
+    return (2.0 * t3 - 3.0 * t2 + 1.0) * y0 + (t3 - 2.0 * t2 + t) * m0 + (-2.0 * t3 + 3.0 * t2) * y1 +
+           (t3 - t2) * m1;
+}
+
+/* Slope per knot spacing at knot k of the samples y[0..n-1] (stride s). */
+static double knot_slope(const double *y, int n, int s, int k) {
+    if (k == 0) return y[s] - y[0];
+    if (k == n - 1) return y[(n - 1) * s] - y[(n - 2) * s];
+    return (y[(k + 1) * s] - y[(k - 1) * s]) / 2.0;
+}
+
+/* Cell index and position in the cell of coordinate w on n uniform knots
+ * from w0 to w1 (w clamped to the grid). */
+static void locate(double w, double w0, double w1, int n, int *k, double *t) {
+    double h = (w1 - w0) / (double)(n - 1);
+    double r = (w - w0) / h;
+    if (r < 0.0) r = 0.0;
+    if (r > (double)(n - 1)) r = (double)(n - 1);
+    int i = (int)floor(r);
+    if (i > n - 2) i = n - 2;
+    *k = i;
+    *t = r - (double)i;
+}
+
+/* Interpolation along u of row... the value at (u-cell iu, position tu) of
+ * the column j of the table. */
+static double along_u(int iu, double tu, int j) {
+    const double *col = g_pdf_xg + j;
+    int s = g_pdf_nq;
+    return hermite(tu, col[iu * s], col[(iu + 1) * s], knot_slope(col, g_pdf_nx, s, iu),
+                   knot_slope(col, g_pdf_nx, s, iu + 1));
+}
+
+double oracle_pdf_xg(double x, double q2) {
+    if (!g_pdf_xg || g_pdf_nx < 2 || g_pdf_nq < 2) return 0.0;
+    int iu, iv;
+    double tu, tv;
+    locate(log(x), g_pdf_u0, g_pdf_u1, g_pdf_nx, &iu, &tu);
+    locate(log(q2), g_pdf_v0, g_pdf_v1, g_pdf_nq, &iv, &tv);
+    /* the u-interpolants at the v-knots iv-1 .. iv+2 that exist */
+    double w[4];
+    int jlo = iv - 1 < 0 ? 0 : iv - 1;
+    int jhi = iv + 2 > g_pdf_nq - 1 ? g_pdf_nq - 1 : iv + 2;
+    for (int j = jlo; j <= jhi; ++j) w[j - (iv - 1)] = along_u(iu, tu, j);
+    /* slopes along v at knots iv and iv+1, from those values */
+    double m0 = iv == 0 ? w[2] - w[1] : (w[2] - w[0]) / 2.0;
+    double m1 = iv + 1 == g_pdf_nq - 1 ? w[2] - w[1] : (w[3] - w[1]) / 2.0;
+    return hermite(tv, w[1], w[2], m0, m1);
+}
+
+/* LO toy with the density from the grid at the factorisation scale Q^2 = shat:
+ * f = g(x1, shat) g(x2, shat) BW(shat) (1 + c^2)/shat * 2 * norm with the same
+ * cuts as lo_integrand, g = (x g)/x. */
+static double lo_pdf_integrand(const double *x, const double *p) {
+    double sqrtS = p[0], M = p[1], G = p[2], cut = p[3], mlo = p[4], mhi = p[5], norm = p[6];
+    double shat = x[0] * x[1] * (sqrtS * sqrtS);
+    double mll = sqrt(shat);
+    if (!(mll >= mlo && mll <= mhi)) return 0.0;
+    double c = 2.0 * x[2] - 1.0;
+    if (!(fabs(c) < cut)) return 0.0;
+    double M2 = M * M;
+    double dm = shat - M2;
+    double bw = 1.0 / (dm * dm + M2 * G * G);
+    double g1 = oracle_pdf_xg(x[0], shat) / x[0];
+    double g2 = oracle_pdf_xg(x[1], shat) / x[1];
+    return g1 * g2 * bw * (1.0 + c * c) / shat * 2.0 * norm;
+}
+
 static oracle_user_fn g_user_fn = 0;
 
 void oracle_set_user(oracle_user_fn f) { g_user_fn = f; }
@@ -130,6 +224,8 @@ double oracle_integrand(int family, int d, const double *p, int n_params, const 
     switch (family) {
     case ORACLE_F_USER:
         return g_user_fn ? g_user_fn(x, d, p) : 0.0;
+    case ORACLE_F_LO_PDF:
+        return lo_pdf_integrand(x, p);
     case ORACLE_F_CONST:
         return 1.0;
     case ORACLE_F_SUM: {

@@ -30,8 +30,19 @@ enum {
     ORACLE_F_GENZ_PROD = 5, /* f = prod (c_i^-2 + (x_i - w_i)^2)^-1           */
     ORACLE_F_GENZ_CORNER = 6,/* f = (1 + sum c_i x_i)^-(d+1)                  */
     ORACLE_F_LO = 7,        /* LO-style 2->2 toy, d = 3 (see the .c file)     */
-    ORACLE_F_USER = 8       /* the function set by oracle_set_user            */
+    ORACLE_F_USER = 8,      /* the function set by oracle_set_user            */
+    ORACLE_F_LO_PDF = 9     /* LO toy with g(x, Q^2 = shat) from the grid set by
+                               oracle_set_pdf_grid                            */
 };
+
+/* Parton-density grid of ORACLE_F_LO_PDF: xg[i * nq + j] = x g(x, Q^2) at
+ * ln x = u0 + i (u1 - u0)/(nx - 1), ln Q^2 = v0 + j (v1 - v0)/(nq - 1)
+ * (nx, nq >= 2).  The table is referenced, not copied. */
+void oracle_set_pdf_grid(int nx, int nq, double u0, double u1, double v0, double v1, const double *xg);
+
+/* x g(x, Q^2) from that grid: bicubic Hermite interpolation in (ln x, ln Q^2),
+ * see the .c file. */
+double oracle_pdf_xg(double x, double q2);
 
 /* The integrand of ORACLE_F_USER: f(x, d, params), FP64, set by the test
  * from the user's source compiled for the host (one per process). */

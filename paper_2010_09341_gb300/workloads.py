@@ -19,6 +19,8 @@ from __future__ import annotations
 
 from dataclasses import dataclass, field
 
+import math
+
 import numpy as np
 
 # LO-style 2->2 toy: 13 TeV collider, Z-like Breit-Wigner, |cos theta| < 0.95,
@@ -51,6 +53,32 @@ def genz_params(family: str, d: int, seed: int, c_lo: float = 0.5, c_hi: float =
 
 def lo_params() -> np.ndarray:
     return np.array(LO_PARAMS, dtype=np.float64)
+
+
+# Grid of a synthetic parton density (no PDF sets are available here): the
+# LO toy's x^-1/2 (1-x)^b shape with a mild scale dependence of b, normalised
+# to unit integral at every scale, tabulated as x g(x, Q^2) on uniform knots
+# in ln x and ln Q^2 (the layout of the density grids the paper's companion
+# tool interpolates).
+PDF_X_MIN, PDF_Q_MIN, PDF_Q_MAX = 1e-6, 10.0, 1000.0
+
+
+def pdf_grid(nx: int = 96, nq: int = 48, b0: float = 3.0, b1: float = 0.5):
+    """(xg[nx, nq], u0, u1, v0, v1): x g(x, Q^2) = N(Q^2) x^(1/2) (1-x)^b(Q^2)
+    with b = b0 + b1 ln(Q^2/Qmin^2)/ln(Qmax^2/Qmin^2) and N = 1/B(1/2, b+1);
+    u = ln x from ln(1e-6) to 0, v = ln Q^2 from ln(10^2) to ln(1000^2).
+    b1 = 0 gives the LO toy's own density at every scale."""
+    from scipy.special import beta
+    u0, u1 = math.log(PDF_X_MIN), 0.0
+    v0, v1 = math.log(PDF_Q_MIN ** 2), math.log(PDF_Q_MAX ** 2)
+    u = np.linspace(u0, u1, nx)
+    v = np.linspace(v0, v1, nq)
+    x = np.exp(u)[:, None]
+    b = b0 + b1 * (v - v0) / (v1 - v0)
+    N = 1.0 / beta(0.5, b + 1.0)
+    xg = N[None, :] * np.sqrt(x) * (1.0 - np.minimum(x, 1.0)) ** b[None, :]
+    xg[-1, :] = 0.0  # x = 1
+    return np.ascontiguousarray(xg), u0, u1, v0, v1
 
 
 @dataclass
