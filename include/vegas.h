@@ -95,7 +95,8 @@ typedef enum {
     VEGAS_F_GENZ_PROD = 5,
     VEGAS_F_GENZ_CORNER = 6,
     VEGAS_F_LO = 7,
-    VEGAS_F_USER = 8      /* a user's source, vegas_create_user (not vegas_create) */
+    VEGAS_F_USER = 8,     /* a user's source, vegas_create_user (not vegas_create) */
+    VEGAS_F_LO_PDF = 9    /* LO with its density from a grid (vegas_set_pdf_grid) */
 } vegas_family;
 
 #define VEGAS_MAX_DIM 32
@@ -277,6 +278,25 @@ vegas_status vegas_set_strata(vegas_ctx *ctx, int32_t B);
 /* The stratification of the next iteration: *B (0: plain), *P (0: plain) and
  * *n_used, the samples it takes (n_events when plain).  Any pointer may be NULL. */
 vegas_status vegas_get_strata(vegas_ctx *ctx, int32_t *B, int64_t *P, int64_t *n_used);
+
+/* Density grid of the VEGAS_F_LO_PDF family: the LO toy of VEGAS_F_LO (same
+ * parameters, cuts and Breit-Wigner) with the parton density g(x, Q^2) taken
+ * at the scale Q^2 = shat from a tabulated grid, as the paper's companion tool
+ * (PDFFlow, Sec. 2) evaluates parton densities from grids on the GPU:
+ *     f = g(x1, shat) g(x2, shat) BW(shat) (1 + c^2)/shat * 2 * norm.
+ * dev_xg (device, FP64, row-major nx x nq, 2 <= nx, nq, nx nq <= 6144) holds
+ * x g(x, Q^2) at ln x = u0 + i (u1 - u0)/(nx - 1), ln Q^2 = v0 + j (v1 - v0)/(nq - 1).
+ * Between knots: bicubic Hermite interpolation in (ln x, ln Q^2) with each
+ * knot's tangent the central difference of its neighbours (one-sided at the
+ * first and last knot); outside the grid the coordinates are clamped to it.
+ * The caller owns dev_xg and keeps it alive and unchanged while the context
+ * samples; each sampling block copies it into shared memory in the path's
+ * precision.  Call before the first iteration (iterating without a grid:
+ * EINVAL); may be called again with another grid.  EINVAL for another family,
+ * bad sizes or ranges, or a grid that does not fit shared memory with the
+ * context's cells. */
+vegas_status vegas_set_pdf_grid(vegas_ctx *ctx, const double *dev_xg, int32_t nx, int32_t nq, double u0,
+                                double u1, double v0, double v1);
 
 /* Checkpoint: a byte blob holding config, parameters, FP64 grid, iteration
  * counter and per-iteration results.  export with buf == NULL sets *size.

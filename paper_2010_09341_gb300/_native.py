@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(PKG, "libvegas.so")
 VEGAS_FP64, VEGAS_FP32_ACC64, VEGAS_FP32_KAHAN = 0, 1, 2
 PRECISIONS = {"fp64": VEGAS_FP64, "fp32_acc64": VEGAS_FP32_ACC64, "fp32_kahan": VEGAS_FP32_KAHAN}
 FAMILIES = {"const": 0, "sum": 1, "gauss_sym": 2, "genz_osc": 3, "genz_gauss": 4,
-            "genz_prod": 5, "genz_corner": 6, "lo": 7, "user": 8}
+            "genz_prod": 5, "genz_corner": 6, "lo": 7, "user": 8, "lo_pdf": 9}
 MAX_USER_PARAMS = 72
 MAX_DIM, MAX_BINS, MAX_ITERS = 32, 1024, 4096
 
@@ -92,6 +92,8 @@ _SIGS = {
                                          ctypes.POINTER(ctypes.c_double), ctypes.c_int32, _P, _P,
                                          ctypes.c_size_t, ctypes.POINTER(_P)]),
     "vegas_jit_log": (ctypes.c_char_p, []),
+    "vegas_set_pdf_grid": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_double, ctypes.c_double]),
     "vegas_get_strata": (ctypes.c_int, [_P, _P, _P, _P]),
     "vegas_export_state": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_size_t)]),
     "vegas_import_state": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),

@@ -78,6 +78,7 @@ int n_params_for(int family, int d) {
     case VEGAS_F_GENZ_PROD: return 2 * d;
     case VEGAS_F_GENZ_CORNER: return d;
     case VEGAS_F_LO: return 7;
+    case VEGAS_F_LO_PDF: return 7;
     default: return -1;
     }
 }
@@ -156,7 +157,8 @@ bool prepare_family(int family, int d, const double *p, FamilyConsts &fc, double
         }
         fc.s[0] = -static_cast<double>(d + 1);
         break;
-    case VEGAS_F_LO: {
+    case VEGAS_F_LO:
+    case VEGAS_F_LO_PDF: {
         const double sqrtS = p[0], M = p[1], G = p[2], cut = p[3], mlo = p[4], mhi = p[5], nrm = p[6];
         if (!(sqrtS > 0 && M > 0 && G > 0 && cut > 0 && mlo >= 0 && mhi > mlo)) return false;
         fc.s[0] = sqrtS * sqrtS;
@@ -165,7 +167,9 @@ bool prepare_family(int family, int d, const double *p, FamilyConsts &fc, double
         fc.s[3] = cut;
         fc.s[4] = mlo * mlo;
         fc.s[5] = mhi * mhi;
-        const double gn = 35.0 / 32.0;
+        // LO: the parametric density's normalisation (35/32)^2 is a constant
+        // factor; LO_PDF takes g from the grid (vegas_set_pdf_grid)
+        const double gn = family == VEGAS_F_LO ? 35.0 / 32.0 : 1.0;
         norm = 2.0 * gn * gn * nrm;
         // size of f near the resonance: g(x)^2 ~ 1/sqrt(tau0), BW/shat ~ 1/(M^2 G)^2
         fmax = std::fabs(norm) * (sqrtS / M) / (M * M * M * M * G * G);
@@ -215,6 +219,8 @@ struct vegas_ctx {
     const void *kfn_strat = nullptr;
     int max_blocks_strat = 0;
     JitKernels jit;     // user integrand's run-time compiled kernels (family VEGAS_F_USER)
+    const double *pdf = nullptr;  // VEGAS_F_LO_PDF: the caller's density grid (device)
+    int pdf_n = 0;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;  // event pool
     size_t ev_used = 0;
 
@@ -272,7 +278,7 @@ static vegas_status create_impl(const vegas_config *cfg, const vegas_integrand *
     const int np = user ? itg->n_params : n_params_for(itg->family, d);
     if (np < 0 || np > VEGAS_MAX_USER_PARAMS || itg->n_params != np || (np > 0 && !itg->params))
         return VEGAS_EINVAL;
-    if (itg->family == VEGAS_F_LO && d != 3) return VEGAS_EINVAL;
+    if ((itg->family == VEGAS_F_LO || itg->family == VEGAS_F_LO_PDF) && d != 3) return VEGAS_EINVAL;
     const Layout L = layout_for(d, N);
     if (!dev_workspace || (reinterpret_cast<uintptr_t>(dev_workspace) % kAlign) != 0)
         return VEGAS_EINVAL;
@@ -459,6 +465,8 @@ static SampleArgs make_args(const vegas_ctx *c, long long s_begin, long long n, 
     }
     for (int k = 0; k < 8; ++k) a.fc32.s[k] = static_cast<float>(c->fc.s[k]);
     memset(&a.st, 0, sizeof(a.st));
+    a.pdf = c->pdf;
+    a.pdf_n = c->pdf_n;
     return a;
 }
 
@@ -505,6 +513,7 @@ static vegas_status launch_sampling(vegas_ctx *c, long long s_begin, long long n
 // Sampling of samples [s_begin, s_begin + count) of the next iteration into
 // the accumulators (split into launches of at most events_limit samples).
 static vegas_status sample_samples(vegas_ctx *c, long long s_begin, long long count) {
+    if (c->family == VEGAS_F_LO_PDF && !c->pdf) return VEGAS_EINVAL;  // vegas_set_pdf_grid first
     const long long lim = c->cfg.events_limit > 0 ? c->cfg.events_limit : count;
     std::pair<cudaEvent_t, cudaEvent_t> *pe = nullptr;
     if (c->profiling) {
@@ -736,6 +745,7 @@ vegas_status vegas_set_iteration(vegas_ctx *c, int32_t t) {
 vegas_status vegas_trace(vegas_ctx *c, int32_t t, int64_t s_begin, int64_t count, int32_t *bins,
                          double *x, double *w) {
     if (!c || t < 0 || s_begin < 0 || count < 0) return VEGAS_EINVAL;
+    if (c->family == VEGAS_F_LO_PDF && !c->pdf) return VEGAS_EINVAL;
     if (count == 0) return VEGAS_OK;
     SampleArgs a = make_args(c, s_begin, count, t);
     const Strata sg = strata_for(c->strat_req, c->cfg.n_dim, c->cfg.n_events);
@@ -777,6 +787,51 @@ vegas_status vegas_set_strata(vegas_ctx *c, int32_t B) {
             return VEGAS_EINVAL;
     }
     c->strat_req = B;
+    return VEGAS_OK;
+}
+
+vegas_status vegas_set_pdf_grid(vegas_ctx *c, const double *dev_xg, int32_t nx, int32_t nq, double u0,
+                                double u1, double v0, double v1) {
+    if (!c || c->family != VEGAS_F_LO_PDF || !dev_xg || nx < 2 || nq < 2 ||
+        static_cast<long long>(nx) * nq > kMaxPdfValues || !(u1 > u0) || !(v1 > v0) || !std::isfinite(u0) ||
+        !std::isfinite(u1) || !std::isfinite(v0) || !std::isfinite(v1) ||
+        (reinterpret_cast<uintptr_t>(dev_xg) % alignof(double)) != 0)
+        return VEGAS_EINVAL;
+    // shared memory: the block's cells and the grid in the path's precision
+    const size_t tsize = c->mode == ACC_F64 ? sizeof(double) : sizeof(float);
+    const size_t smem = sample_smem(c->mode, c->priv ? 1 : 0, c->cfg.n_dim, c->cfg.n_bins) +
+                        static_cast<size_t>(nx) * nq * tsize;
+    cudaError_t err;
+    const DeviceInfo di = device_info(&err);
+    if (err != cudaSuccess) {
+        set_error("device query", err);
+        return VEGAS_ECUDA;
+    }
+    if (smem + 1024 > di.smem_optin) return VEGAS_EINVAL;
+    int occ = 0;
+    VEGAS_CK(cudaFuncSetAttribute(c->kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+    VEGAS_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, c->kfn, c->threads, smem));
+    if (occ < 1) return VEGAS_EINVAL;
+    c->max_blocks = occ * di.sms;
+    if (c->kfn_strat) {
+        int occ_s = 0;
+        VEGAS_CK(cudaFuncSetAttribute(c->kfn_strat, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      static_cast<int>(smem)));
+        VEGAS_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_s, c->kfn_strat, c->threads, smem));
+        if (occ_s < 1) return VEGAS_EINVAL;
+        c->max_blocks_strat = occ_s * di.sms;
+    }
+    c->smem = smem;
+    // grid_xg works in log2 units: first knot and knots per unit of log2 x, log2 Q^2
+    const double log2e = 1.4426950408889634;
+    c->fc.p[0] = u0 * log2e;
+    c->fc.p[1] = static_cast<double>(nx - 1) / ((u1 - u0) * log2e);
+    c->fc.p[2] = v0 * log2e;
+    c->fc.p[3] = static_cast<double>(nq - 1) / ((v1 - v0) * log2e);
+    c->fc.p[4] = nx;
+    c->fc.p[5] = nq;
+    c->pdf = dev_xg;
+    c->pdf_n = nx * nq;
     return VEGAS_OK;
 }
 
@@ -993,6 +1048,7 @@ extern "C" vegas_status vegas_iterate_noalloc(const vegas_config *cfg, const veg
     const int np = n_params_for(itg->family, d);
     if (np < 0 || itg->n_params != np || (np > 0 && !itg->params)) return VEGAS_EINVAL;
     if (itg->family == VEGAS_F_LO && d != 3) return VEGAS_EINVAL;
+    if (itg->family == VEGAS_F_LO_PDF) return VEGAS_EINVAL;  // needs a context's density grid
     FamilyConsts fc;
     double norm = 1.0, fmax = 1.0;
     if (!prepare_family(itg->family, d, itg->params, fc, norm, fmax)) return VEGAS_EINVAL;

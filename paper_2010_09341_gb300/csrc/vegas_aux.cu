@@ -211,6 +211,7 @@ static const void *trace_pick_fam(int fam, int tier) {
     case F_GENZ_PROD: return trace_pick<MODE, F_GENZ_PROD>(tier);
     case F_GENZ_CORNER: return trace_pick<MODE, F_GENZ_CORNER>(tier);
     case F_LO: return tier == 0 ? reinterpret_cast<const void *>(&trace_kernel<F_LO, MODE, 4>) : nullptr;
+    case F_LO_PDF: return tier == 0 ? reinterpret_cast<const void *>(&trace_kernel<F_LO_PDF, MODE, 4>) : nullptr;
     default: return nullptr;
     }
 }
@@ -234,7 +235,9 @@ cudaError_t launch_trace_fn(const void *fn, const SampleArgs &a, double inv_scal
     const unsigned blocks = static_cast<unsigned>((a.n + threads - 1) / threads);
     SampleArgs args = a;
     void *params[] = {&args, &inv_scale, &bins, &x, &w};
-    return cudaLaunchKernel(fn, dim3(blocks), dim3(threads), params, 0, stream);
+    // a density grid is staged in shared memory (at most kMaxPdfValues FP64 values: 48 KB)
+    const size_t smem = a.pdf ? static_cast<size_t>(a.pdf_n) * sizeof(double) : 0;
+    return cudaLaunchKernel(fn, dim3(blocks), dim3(threads), params, smem, stream);
 }
 
 // --------------------------------------------------------------- Philox

@@ -546,6 +546,7 @@ vegas_status vegas_batch_add(vegas_batch *b, const vegas_config *cfg, const vega
     const int np = host_n_params(itg->family, d);
     if (np < 0 || itg->n_params != np || (np > 0 && !itg->params)) return VEGAS_EINVAL;
     if (itg->family == VEGAS_F_LO && d != 3) return VEGAS_EINVAL;
+    if (itg->family == VEGAS_F_LO_PDF) return VEGAS_EINVAL;  // its density grid is per context
     FamilyConsts fc;
     double norm = 1.0, fmax = 1.0;
     if (!host_prepare_family(itg->family, d, itg->params, fc, norm, fmax)) return VEGAS_EINVAL;

@@ -105,8 +105,50 @@ enum Family : int {
     F_GENZ_PROD = 5,
     F_GENZ_CORNER = 6,
     F_LO = 7,
-    F_USER = 8   // user source, compiled at run time (vegas_create_user)
+    F_USER = 8,   // user source, compiled at run time (vegas_create_user)
+    F_LO_PDF = 9  // LO toy with its density from a tabulated grid (vegas_set_pdf_grid)
 };
+
+// Cubic through four equally spaced values f0..f3 on [1, 2], at t in [0, 1]
+// from f1: the Hermite cubic whose tangents are the central differences
+// (f2 - f0)/2 and (f3 - f1)/2 (the Catmull-Rom form).
+template <class T> __device__ __forceinline__ T catmull_rom(T f0, T f1, T f2, T f3, T t) {
+    const T a = T(3) * (f1 - f2) + f3 - f0;
+    const T b = T(2) * f0 - T(5) * f1 + T(4) * f2 - f3;
+    const T c = f2 - f0;
+    return f1 + T(0.5) * t * (c + t * (b + t * a));
+}
+
+// x g(x, Q^2) from a density grid (F_LO_PDF): tbl[i nq + j] on uniform knots
+// in (log2 x, log2 Q^2), bicubic Hermite with central-difference tangents;
+// a knot outside the grid takes the linear ghost value 2 f_edge - f_next,
+// which makes the tangent at the first and last knot one-sided.  Coordinates
+// are clamped to the grid.  g[0..5] = log2 x of the first knot, knots per unit
+// of log2 x, the same for log2 Q^2, nx, nq.
+template <class T> __device__ __forceinline__ T grid_xg(const T *tbl, const T *g, T lx, T lq) {
+    const int nx = static_cast<int>(g[4]), nq = static_cast<int>(g[5]);
+    T ru = (lx - g[0]) * g[1];
+    T rv = (lq - g[2]) * g[3];
+    ru = fmin(fmax(ru, T(0)), T(nx - 1));
+    rv = fmin(fmax(rv, T(0)), T(nq - 1));
+    const int i = min(static_cast<int>(ru), nx - 2);
+    const int j = min(static_cast<int>(rv), nq - 2);
+    const T tu = ru - T(i), tv = rv - T(j);
+    T w[4];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        const int jj = min(max(j - 1 + b, 0), nq - 1);
+        const T *col = tbl + jj;
+        const T f1 = col[i * nq], f2 = col[(i + 1) * nq];
+        T f0 = col[max(i - 1, 0) * nq], f3 = col[min(i + 2, nx - 1) * nq];
+        if (i == 0) f0 = T(2) * f1 - f2;
+        if (i + 2 == nx) f3 = T(2) * f2 - f1;
+        w[b] = catmull_rom(f0, f1, f2, f3, tu);
+    }
+    if (j == 0) w[0] = T(2) * w[1] - w[2];
+    if (j + 2 == nq) w[3] = T(2) * w[2] - w[1];
+    return catmull_rom(w[0], w[1], w[2], w[3], tv);
+}
 
 
 // Per-integral constants a family needs, prepared on the host in FP64 and
@@ -181,6 +223,7 @@ template <int FAM, class T, int MAXD> struct Integrand {
     T x0, x1, x2;
     T xs[FAM == F_USER ? MAXD : 1];
     int nd;
+    const T *tbl;   // F_LO_PDF: the density grid (shared memory)
 
     __device__ __forceinline__ void begin(const C &fc) {
         if (FAM == F_GENZ_OSC) acc = fc.s[1];     // 2 pi u
@@ -205,7 +248,7 @@ template <int FAM, class T, int MAXD> struct Integrand {
             // the initial weight.  Multiply the denominators, invert once.
             const T t = fc.p[j] * (x - fc.q[j]);
             acc *= ffma(t, t, T(1));
-        } else if (FAM == F_LO) {
+        } else if (FAM == F_LO || FAM == F_LO_PDF) {
             if (j == 0) x0 = x;
             else if (j == 1) x1 = x;
             else if (j == 2) x2 = x;
@@ -225,6 +268,21 @@ template <int FAM, class T, int MAXD> struct Integrand {
         if (FAM == F_GENZ_PROD) return frcp(acc);
         if (FAM == F_GENZ_CORNER) return fexp2(s0 * flog2(acc));
         if (FAM == F_USER) return ::user_integrand<T>(xs, nd, reinterpret_cast<const T *>(&fc));
+        if (FAM == F_LO_PDF) {
+            // the LO toy with g(x, Q^2 = shat) = grid_xg / x; s0..s5 as for LO,
+            // p[0..5] the grid (grid_xg), the constant 2 norm in the initial weight
+            const T s1 = fc.s[1], s2 = fc.s[2], s3 = fc.s[3], s4 = fc.s[4], s5 = fc.s[5];
+            const T shat = x0 * x1 * s0;
+            const T c = ffma(T(2), x2, T(-1));
+            const bool in = (shat >= s4) && (shat <= s5) && (fabs_t(c) < s3);
+            const T lq = flog2(shat);
+            const T g1 = grid_xg(tbl, fc.p, flog2(x0), lq);
+            const T g2 = grid_xg(tbl, fc.p, flog2(x1), lq);
+            const T dm = shat - s1;
+            const T den = ffma(dm, dm, s2) * shat * x0 * x1;
+            const T val = g1 * g2 * ffma(c, c, T(1)) * frcp(den);
+            return in ? val : T(0);
+        }
         if (FAM == F_LO) {
             // s0 = sqrtS^2, s1 = M^2, s2 = (M Gamma)^2, s3 = cut,
             // s4 = mll_lo^2, s5 = mll_hi^2; the constant 2 (35/32)^2 norm is

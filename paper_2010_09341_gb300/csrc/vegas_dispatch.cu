@@ -11,6 +11,7 @@ const void *sample_kernel_f64_genz_gauss(int d, bool priv);
 const void *sample_kernel_f64_genz_prod(int d, bool priv);
 const void *sample_kernel_f64_genz_corner(int d, bool priv);
 const void *sample_kernel_f64_lo(int d, bool priv);
+const void *sample_kernel_f64_lo_pdf(int d, bool priv);
 const void *sample_kernel_f32sum64_const(int d, bool priv);
 const void *sample_kernel_f32sum64_sum(int d, bool priv);
 const void *sample_kernel_f32sum64_gauss_sym(int d, bool priv);
@@ -19,6 +20,7 @@ const void *sample_kernel_f32sum64_genz_gauss(int d, bool priv);
 const void *sample_kernel_f32sum64_genz_prod(int d, bool priv);
 const void *sample_kernel_f32sum64_genz_corner(int d, bool priv);
 const void *sample_kernel_f32sum64_lo(int d, bool priv);
+const void *sample_kernel_f32sum64_lo_pdf(int d, bool priv);
 const void *sample_kernel_f32kahan_const(int d, bool priv);
 const void *sample_kernel_f32kahan_sum(int d, bool priv);
 const void *sample_kernel_f32kahan_gauss_sym(int d, bool priv);
@@ -27,6 +29,7 @@ const void *sample_kernel_f32kahan_genz_gauss(int d, bool priv);
 const void *sample_kernel_f32kahan_genz_prod(int d, bool priv);
 const void *sample_kernel_f32kahan_genz_corner(int d, bool priv);
 const void *sample_kernel_f32kahan_lo(int d, bool priv);
+const void *sample_kernel_f32kahan_lo_pdf(int d, bool priv);
 
 const void *sample_strat_kernel_f64_const(int d, bool priv);
 const void *sample_strat_kernel_f64_sum(int d, bool priv);
@@ -36,6 +39,7 @@ const void *sample_strat_kernel_f64_genz_gauss(int d, bool priv);
 const void *sample_strat_kernel_f64_genz_prod(int d, bool priv);
 const void *sample_strat_kernel_f64_genz_corner(int d, bool priv);
 const void *sample_strat_kernel_f64_lo(int d, bool priv);
+const void *sample_strat_kernel_f64_lo_pdf(int d, bool priv);
 const void *sample_strat_kernel_f32sum64_const(int d, bool priv);
 const void *sample_strat_kernel_f32sum64_sum(int d, bool priv);
 const void *sample_strat_kernel_f32sum64_gauss_sym(int d, bool priv);
@@ -44,6 +48,7 @@ const void *sample_strat_kernel_f32sum64_genz_gauss(int d, bool priv);
 const void *sample_strat_kernel_f32sum64_genz_prod(int d, bool priv);
 const void *sample_strat_kernel_f32sum64_genz_corner(int d, bool priv);
 const void *sample_strat_kernel_f32sum64_lo(int d, bool priv);
+const void *sample_strat_kernel_f32sum64_lo_pdf(int d, bool priv);
 const void *sample_strat_kernel_f32kahan_const(int d, bool priv);
 const void *sample_strat_kernel_f32kahan_sum(int d, bool priv);
 const void *sample_strat_kernel_f32kahan_gauss_sym(int d, bool priv);
@@ -52,6 +57,7 @@ const void *sample_strat_kernel_f32kahan_genz_gauss(int d, bool priv);
 const void *sample_strat_kernel_f32kahan_genz_prod(int d, bool priv);
 const void *sample_strat_kernel_f32kahan_genz_corner(int d, bool priv);
 const void *sample_strat_kernel_f32kahan_lo(int d, bool priv);
+const void *sample_strat_kernel_f32kahan_lo_pdf(int d, bool priv);
 
 const void *sample_kernel(int mode, int fam, int d, bool priv) {
     switch (mode) {
@@ -65,6 +71,7 @@ const void *sample_kernel(int mode, int fam, int d, bool priv) {
         case F_GENZ_PROD: return sample_kernel_f64_genz_prod(d, priv);
         case F_GENZ_CORNER: return sample_kernel_f64_genz_corner(d, priv);
         case F_LO: return sample_kernel_f64_lo(d, priv);
+        case F_LO_PDF: return sample_kernel_f64_lo_pdf(d, priv);
         default: return nullptr;
         }
     case ACC_F32_SUM64:
@@ -77,6 +84,7 @@ const void *sample_kernel(int mode, int fam, int d, bool priv) {
         case F_GENZ_PROD: return sample_kernel_f32sum64_genz_prod(d, priv);
         case F_GENZ_CORNER: return sample_kernel_f32sum64_genz_corner(d, priv);
         case F_LO: return sample_kernel_f32sum64_lo(d, priv);
+        case F_LO_PDF: return sample_kernel_f32sum64_lo_pdf(d, priv);
         default: return nullptr;
         }
     case ACC_F32_KAHAN:
@@ -89,6 +97,7 @@ const void *sample_kernel(int mode, int fam, int d, bool priv) {
         case F_GENZ_PROD: return sample_kernel_f32kahan_genz_prod(d, priv);
         case F_GENZ_CORNER: return sample_kernel_f32kahan_genz_corner(d, priv);
         case F_LO: return sample_kernel_f32kahan_lo(d, priv);
+        case F_LO_PDF: return sample_kernel_f32kahan_lo_pdf(d, priv);
         default: return nullptr;
         }
     default: return nullptr;
@@ -107,6 +116,7 @@ const void *sample_strat_kernel(int mode, int fam, int d, bool priv) {
         case F_GENZ_PROD: return sample_strat_kernel_f64_genz_prod(d, priv);
         case F_GENZ_CORNER: return sample_strat_kernel_f64_genz_corner(d, priv);
         case F_LO: return sample_strat_kernel_f64_lo(d, priv);
+        case F_LO_PDF: return sample_strat_kernel_f64_lo_pdf(d, priv);
         default: return nullptr;
         }
     case ACC_F32_SUM64:
@@ -119,6 +129,7 @@ const void *sample_strat_kernel(int mode, int fam, int d, bool priv) {
         case F_GENZ_PROD: return sample_strat_kernel_f32sum64_genz_prod(d, priv);
         case F_GENZ_CORNER: return sample_strat_kernel_f32sum64_genz_corner(d, priv);
         case F_LO: return sample_strat_kernel_f32sum64_lo(d, priv);
+        case F_LO_PDF: return sample_strat_kernel_f32sum64_lo_pdf(d, priv);
         default: return nullptr;
         }
     case ACC_F32_KAHAN:
@@ -131,6 +142,7 @@ const void *sample_strat_kernel(int mode, int fam, int d, bool priv) {
         case F_GENZ_PROD: return sample_strat_kernel_f32kahan_genz_prod(d, priv);
         case F_GENZ_CORNER: return sample_strat_kernel_f32kahan_genz_corner(d, priv);
         case F_LO: return sample_strat_kernel_f32kahan_lo(d, priv);
+        case F_LO_PDF: return sample_strat_kernel_f32kahan_lo_pdf(d, priv);
         default: return nullptr;
         }
     default: return nullptr;

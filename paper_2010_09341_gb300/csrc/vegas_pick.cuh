@@ -20,7 +20,7 @@ static const void *pick_priv(bool priv) {
 template <int MODE, int FAM>
 static const void *pick_family(int d, bool priv) {
     constexpr bool kExact = MODE != ACC_F64;  // the FP64 path is FP64-pipe bound either way
-    if (FAM == F_LO) {
+    if (FAM == F_LO || FAM == F_LO_PDF) {
         if (d != 3) return nullptr;
         return (kExact && priv) ? pick_priv<MODE, FAM, 3, true>(true) : pick_priv<MODE, FAM, 4, false>(priv);
     }
@@ -54,7 +54,7 @@ static const void *pick_strat_priv(bool priv) {
 template <int MODE, int FAM>
 static const void *pick_strat(int d, bool priv) {
     constexpr bool kExact = MODE != ACC_F64;
-    if (FAM == F_LO) {
+    if (FAM == F_LO || FAM == F_LO_PDF) {
         if (d != 3) return nullptr;
         return (kExact && priv) ? pick_strat_priv<MODE, FAM, 3, true>(true) : pick_strat_priv<MODE, FAM, 4, false>(priv);
     }

@@ -60,7 +60,10 @@ struct SampleArgs {
     FamConsts<double> fc64;   // integrand constants, FP64 path
     FamConsts<float> fc32;    // the same rounded to FP32, FP32 paths
     StratArgs st;             // stratified launches: s_begin, n count hypercubes
+    const double *pdf;        // F_LO_PDF: the density grid, pdf_n FP64 values (device)
+    int pdf_n;
 };
+
 
 template <class T> __device__ __forceinline__ const FamConsts<T> &consts(const SampleArgs &a);
 template <> __device__ __forceinline__ const FamConsts<double> &consts<double>(const SampleArgs &a) {
@@ -126,6 +129,18 @@ __host__ __device__ constexpr size_t sample_smem_bytes(int d, int N) {
     return static_cast<size_t>(d) * N *
            (Copies<MODE, PRIV>::TP * 2 * sizeof(typename Tr::T) + Copies<MODE, PRIV>::HP * sizeof(typename Tr::H) +
             (MODE != ACC_F64 ? sizeof(uint32_t) : 0));  // single-copy fine cells
+}
+
+// F_LO_PDF: the density grid, converted to the path's precision, follows the
+// block's cells in shared memory; every thread calls this after carve/stage.
+template <int FAM, int MODE, int PRIV>
+__device__ __forceinline__ const typename ModeTraits<MODE>::T *stage_pdf(unsigned char *raw, const SampleArgs &a,
+                                                                          int d) {
+    using T = typename ModeTraits<MODE>::T;
+    if (FAM != F_LO_PDF) return nullptr;
+    T *t = reinterpret_cast<T *>(raw + sample_smem_bytes<MODE, PRIV>(d, a.N));
+    for (int k = threadIdx.x; k < a.pdf_n; k += blockDim.x) t[k] = static_cast<T>(a.pdf[k]);
+    return t;
 }
 
 // Samples one block may add to its fixed-point cells between two flushes:
@@ -237,6 +252,7 @@ template <class T> struct RangeParams {
     T jinit, n4;
     float hs;        // fixed-point scale of v^2 (FP32 modes); 0: FP32 cells
     double *acc;     // FP64 accumulators [2 + d N] (values beyond the fixed range)
+    const T *aux = nullptr;  // F_LO_PDF: the density grid in shared memory
 };
 
 // Cell indices of one sample's dimensions, one per register or, with PACK,
@@ -271,6 +287,7 @@ __device__ __forceinline__ typename ModeTraits<MODE>::T map_sample(
     const int N = rp.N;
     const uint32_t slo = static_cast<uint32_t>(s), shi = static_cast<uint32_t>(s >> 32);
     Integrand<FAM, T, MAXD> fam;
+    if (FAM == F_LO_PDF) fam.tbl = rp.aux;
     T J = rp.jinit;
     fam.begin(fc);
 #pragma unroll
@@ -522,6 +539,7 @@ vegas_sample_kernel(const SampleArgs a) {
     bs.carve(smem_raw, d * a.N);
     bs.stage(a.table);
     RangeParams<T> rp;
+    rp.aux = stage_pdf<FAM, MODE, PRIV>(smem_raw, a, d);
     rp.d = d;
     rp.N = a.N;
     rp.key0 = a.key0;

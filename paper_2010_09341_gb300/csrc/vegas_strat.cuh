@@ -135,6 +135,7 @@ vegas_sample_strat_kernel(const SampleArgs a) {
     bs.carve(smem_raw, d * a.N);
     bs.stage(a.table);
     RangeParams<T> rp;
+    rp.aux = stage_pdf<FAM, MODE, PRIV>(smem_raw, a, d);
     rp.d = d;
     rp.N = a.N;
     rp.key0 = a.key0;

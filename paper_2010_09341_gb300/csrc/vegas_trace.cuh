@@ -16,11 +16,19 @@ __global__ void trace_kernel(const SampleArgs a, double inv_scale, int32_t *bins
                              double *ws) {
     using T = typename ModeTraits<MODE>::T;
     using T2 = typename Prec<T>::T2;
+    extern __shared__ __align__(16) unsigned char trace_smem[];
     const long long k = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    Integrand<FAM, T, MAXD> fam;
+    if (FAM == F_LO_PDF) {
+        // the density grid in shared memory, in the path's precision
+        T *t = reinterpret_cast<T *>(trace_smem);
+        for (int i = threadIdx.x; i < a.pdf_n; i += blockDim.x) t[i] = static_cast<T>(a.pdf[i]);
+        __syncthreads();
+        fam.tbl = t;
+    }
     if (k >= a.n) return;
     const int d = a.d, N = a.N;
     const T2 *tab = static_cast<const T2 *>(a.table);
-    Integrand<FAM, T, MAXD> fam;
     const FamConsts<T> &fc = consts<T>(a);
     const unsigned long long s = static_cast<unsigned long long>(a.s_begin + k);
     const uint32_t slo = static_cast<uint32_t>(s), shi = static_cast<uint32_t>(s >> 32);

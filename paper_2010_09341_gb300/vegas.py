@@ -240,6 +240,19 @@ def vegas_set_strata(ctx: Context, B: int) -> None:
     check(nat.load().vegas_set_strata(ctx.handle, int(B)), "vegas_set_strata")
 
 
+def vegas_set_pdf_grid(ctx: Context, xg: torch.Tensor, u0: float, u1: float, v0: float,
+                       v1: float) -> None:
+    """Density grid of an "lo_pdf" context: xg (nx, nq) float64 CUDA tensor of
+    x g(x, Q^2) on uniform knots in ln x (u0..u1) and ln Q^2 (v0..v1).  The
+    context keeps a reference to the tensor."""
+    assert xg.is_cuda and xg.dtype == torch.float64 and xg.dim() == 2
+    xg = xg.contiguous()
+    check(nat.load().vegas_set_pdf_grid(ctx.handle, ctypes.c_void_p(xg.data_ptr()), int(xg.shape[0]),
+                                        int(xg.shape[1]), float(u0), float(u1), float(v0), float(v1)),
+          "vegas_set_pdf_grid")
+    ctx.pdf_grid = xg
+
+
 def vegas_get_strata(ctx: Context):
     """(B, P, n_used) of the next iteration (B = P = 0 when plain)."""
     B = ctypes.c_int32()
