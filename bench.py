@@ -344,6 +344,39 @@ def _time_user(V, torch, d=8, N=NBINS, n=NEVENTS, prec=PRECISION, iters=10, warm
     return out
 
 
+def _time_lo_pdf(V, torch, n=100_000_000, iters=10, warm=2, prec="fp32_kahan"):
+    """Config 3 with the density taken from a grid (96 x 48 knots of a synthetic
+    scale-dependent density, bicubic in ln x, ln Q^2 at Q^2 = shat) against the
+    analytic LO toy: samples/s of the sampling kernel and of whole iterations."""
+    from paper_2010_09341_gb300 import workloads as W
+    xg, u0, u1, v0, v1 = W.pdf_grid(96, 48)
+    t = torch.from_numpy(xg).cuda()
+    cfg = V.Config(n_dim=3, n_events=n, n_bins=100, alpha=ALPHA, seed=0, integral_id=0, precision=prec)
+    ctx = V.vegas_create(cfg, "lo_pdf", W.lo_params())
+    V.vegas_set_pdf_grid(ctx, t, u0, u1, v0, v1)
+    for _ in range(warm):
+        V.vegas_step(ctx, sync=False)
+    V.vegas_profile(ctx, True)
+    s = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(s)
+    for _ in range(iters):
+        V.vegas_step(ctx, sync=False)
+    b.record(s)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    kms = V.vegas_profile_read(ctx)
+    res = V.vegas_result(ctx)
+    V.vegas_destroy(ctx)
+    k_ms = sum(kms) / len(kms)
+    return {"workload": "LO toy d=3, density from a 96x48 (ln x, ln Q^2) grid at Q^2 = shat, 100 bins, "
+                        "%g samples/iter, %s" % (n, prec),
+            "samples_per_s": n * iters / (ms / 1e3), "kernel_ms": k_ms,
+            "kernel_samples_per_s": n / (k_ms / 1e3), "ms_per_iter": ms / iters,
+            "I": res["I"], "sigma": res["sigma"]}
+
+
 def _time_batched(V, torch, steps=8, warm=2):
     """The uneven 512-integral mix: one step = one iteration of every integral."""
     from paper_2010_09341_gb300 import workloads as W
@@ -450,7 +483,8 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the other workloads")
-    ap.add_argument("--only", choices=["batched", "serving", "lo", "config1", "strat", "user"], default=None,
+    ap.add_argument("--only", choices=["batched", "serving", "lo", "config1", "strat", "user", "lo_pdf"],
+                    default=None,
                     help="run just one of the other workloads and print its JSON (for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -478,6 +512,8 @@ def main():
         elif args.only == "strat":
             out = {fam: _time_strat(V, torch, fam, p, D, NBINS, NEVENTS, PRECISION)
                    for fam, p in _integrals()}
+        elif args.only == "lo_pdf":
+            out = _time_lo_pdf(V, torch)
         elif args.only == "user":
             out = _time_user(V, torch)
         elif args.only == "lo":
@@ -641,6 +677,7 @@ def main():
         extra["user_integrand_genz_gauss_d8"] = _time_user(V, torch)
         extra["config3_lo_fp32_kahan"] = _time_single(V, torch, "lo", W.lo_params(), 3, 100,
                                                       100_000_000, "fp32_kahan", 10)
+        extra["config3_lo_pdf_grid_fp32_kahan"] = _time_lo_pdf(V, torch)
         extra["config4_batched"] = _time_batched(V, torch)
         extra["config5_serving_1e-4"] = _serving(V, rate=1000.0, n_requests=1000, target=1e-4,
                                                  budget=10 ** 9, fp64_sample=100)

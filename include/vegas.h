@@ -284,7 +284,7 @@ vegas_status vegas_get_strata(vegas_ctx *ctx, int32_t *B, int64_t *P, int64_t *n
  * at the scale Q^2 = shat from a tabulated grid, as the paper's companion tool
  * (PDFFlow, Sec. 2) evaluates parton densities from grids on the GPU:
  *     f = g(x1, shat) g(x2, shat) BW(shat) (1 + c^2)/shat * 2 * norm.
- * dev_xg (device, FP64, row-major nx x nq, 2 <= nx, nq, nx nq <= 6144) holds
+ * dev_xg (device, FP64, row-major nx x nq, 2 <= nx, nq, (nx + 2)(nq + 2) <= 6144) holds
  * x g(x, Q^2) at ln x = u0 + i (u1 - u0)/(nx - 1), ln Q^2 = v0 + j (v1 - v0)/(nq - 1).
  * Between knots: bicubic Hermite interpolation in (ln x, ln Q^2) with each
  * knot's tangent the central difference of its neighbours (one-sided at the

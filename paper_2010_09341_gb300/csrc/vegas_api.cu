@@ -220,7 +220,7 @@ struct vegas_ctx {
     int max_blocks_strat = 0;
     JitKernels jit;     // user integrand's run-time compiled kernels (family VEGAS_F_USER)
     const double *pdf = nullptr;  // VEGAS_F_LO_PDF: the caller's density grid (device)
-    int pdf_n = 0;
+    int pdf_nx = 0, pdf_nq = 0;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;  // event pool
     size_t ev_used = 0;
 
@@ -466,7 +466,8 @@ static SampleArgs make_args(const vegas_ctx *c, long long s_begin, long long n, 
     for (int k = 0; k < 8; ++k) a.fc32.s[k] = static_cast<float>(c->fc.s[k]);
     memset(&a.st, 0, sizeof(a.st));
     a.pdf = c->pdf;
-    a.pdf_n = c->pdf_n;
+    a.pdf_nx = c->pdf_nx;
+    a.pdf_nq = c->pdf_nq;
     return a;
 }
 
@@ -793,14 +794,14 @@ vegas_status vegas_set_strata(vegas_ctx *c, int32_t B) {
 vegas_status vegas_set_pdf_grid(vegas_ctx *c, const double *dev_xg, int32_t nx, int32_t nq, double u0,
                                 double u1, double v0, double v1) {
     if (!c || c->family != VEGAS_F_LO_PDF || !dev_xg || nx < 2 || nq < 2 ||
-        static_cast<long long>(nx) * nq > kMaxPdfValues || !(u1 > u0) || !(v1 > v0) || !std::isfinite(u0) ||
+        static_cast<long long>(nx + 2) * (nq + 2) > kMaxPdfValues || !(u1 > u0) || !(v1 > v0) || !std::isfinite(u0) ||
         !std::isfinite(u1) || !std::isfinite(v0) || !std::isfinite(v1) ||
         (reinterpret_cast<uintptr_t>(dev_xg) % alignof(double)) != 0)
         return VEGAS_EINVAL;
     // shared memory: the block's cells and the grid in the path's precision
     const size_t tsize = c->mode == ACC_F64 ? sizeof(double) : sizeof(float);
     const size_t smem = sample_smem(c->mode, c->priv ? 1 : 0, c->cfg.n_dim, c->cfg.n_bins) +
-                        static_cast<size_t>(nx) * nq * tsize;
+                        static_cast<size_t>(nx + 2) * (nq + 2) * tsize;
     cudaError_t err;
     const DeviceInfo di = device_info(&err);
     if (err != cudaSuccess) {
@@ -831,7 +832,8 @@ vegas_status vegas_set_pdf_grid(vegas_ctx *c, const double *dev_xg, int32_t nx, 
     c->fc.p[4] = nx;
     c->fc.p[5] = nq;
     c->pdf = dev_xg;
-    c->pdf_n = nx * nq;
+    c->pdf_nx = nx;
+    c->pdf_nq = nq;
     return VEGAS_OK;
 }
 

@@ -235,8 +235,8 @@ cudaError_t launch_trace_fn(const void *fn, const SampleArgs &a, double inv_scal
     const unsigned blocks = static_cast<unsigned>((a.n + threads - 1) / threads);
     SampleArgs args = a;
     void *params[] = {&args, &inv_scale, &bins, &x, &w};
-    // a density grid is staged in shared memory (at most kMaxPdfValues FP64 values: 48 KB)
-    const size_t smem = a.pdf ? static_cast<size_t>(a.pdf_n) * sizeof(double) : 0;
+    // a density grid is staged, padded, in shared memory (at most kMaxPdfValues FP64 values: 48 KB)
+    const size_t smem = a.pdf ? static_cast<size_t>(a.pdf_nx + 2) * (a.pdf_nq + 2) * sizeof(double) : 0;
     return cudaLaunchKernel(fn, dim3(blocks), dim3(threads), params, smem, stream);
 }
 

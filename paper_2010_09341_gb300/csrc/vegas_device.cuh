@@ -109,46 +109,7 @@ enum Family : int {
     F_LO_PDF = 9  // LO toy with its density from a tabulated grid (vegas_set_pdf_grid)
 };
 
-// Cubic through four equally spaced values f0..f3 on [1, 2], at t in [0, 1]
-// from f1: the Hermite cubic whose tangents are the central differences
-// (f2 - f0)/2 and (f3 - f1)/2 (the Catmull-Rom form).
-template <class T> __device__ __forceinline__ T catmull_rom(T f0, T f1, T f2, T f3, T t) {
-    const T a = T(3) * (f1 - f2) + f3 - f0;
-    const T b = T(2) * f0 - T(5) * f1 + T(4) * f2 - f3;
-    const T c = f2 - f0;
-    return f1 + T(0.5) * t * (c + t * (b + t * a));
-}
 
-// x g(x, Q^2) from a density grid (F_LO_PDF): tbl[i nq + j] on uniform knots
-// in (log2 x, log2 Q^2), bicubic Hermite with central-difference tangents;
-// a knot outside the grid takes the linear ghost value 2 f_edge - f_next,
-// which makes the tangent at the first and last knot one-sided.  Coordinates
-// are clamped to the grid.  g[0..5] = log2 x of the first knot, knots per unit
-// of log2 x, the same for log2 Q^2, nx, nq.
-template <class T> __device__ __forceinline__ T grid_xg(const T *tbl, const T *g, T lx, T lq) {
-    const int nx = static_cast<int>(g[4]), nq = static_cast<int>(g[5]);
-    T ru = (lx - g[0]) * g[1];
-    T rv = (lq - g[2]) * g[3];
-    ru = fmin(fmax(ru, T(0)), T(nx - 1));
-    rv = fmin(fmax(rv, T(0)), T(nq - 1));
-    const int i = min(static_cast<int>(ru), nx - 2);
-    const int j = min(static_cast<int>(rv), nq - 2);
-    const T tu = ru - T(i), tv = rv - T(j);
-    T w[4];
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-        const int jj = min(max(j - 1 + b, 0), nq - 1);
-        const T *col = tbl + jj;
-        const T f1 = col[i * nq], f2 = col[(i + 1) * nq];
-        T f0 = col[max(i - 1, 0) * nq], f3 = col[min(i + 2, nx - 1) * nq];
-        if (i == 0) f0 = T(2) * f1 - f2;
-        if (i + 2 == nx) f3 = T(2) * f2 - f1;
-        w[b] = catmull_rom(f0, f1, f2, f3, tu);
-    }
-    if (j == 0) w[0] = T(2) * w[1] - w[2];
-    if (j + 2 == nq) w[3] = T(2) * w[2] - w[1];
-    return catmull_rom(w[0], w[1], w[2], w[3], tv);
-}
 
 
 // Per-integral constants a family needs, prepared on the host in FP64 and
@@ -201,6 +162,50 @@ __device__ __forceinline__ float frsqrt(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double frsqrt(double x) { return rsqrt(x); }
 __device__ __forceinline__ float frcp(float x) { return 1.0f / x; }
 __device__ __forceinline__ double frcp(double x) { return 1.0 / x; }
+
+// Weights of the cubic through four equally spaced values f0..f3 at t in
+// [0, 1] from f1: the Hermite cubic whose tangents are the central
+// differences (f2 - f0)/2 and (f3 - f1)/2 (the Catmull-Rom form),
+// value = w0 f0 + w1 f1 + w2 f2 + w3 f3.
+template <class T> struct CubicWeights {
+    T w0, w1, w2, w3;
+    __device__ __forceinline__ explicit CubicWeights(T t) {
+        const T t2 = t * t, t3 = t2 * t;
+        w0 = T(0.5) * (T(2) * t2 - t - t3);
+        w1 = T(0.5) * (T(3) * t3 - T(5) * t2 + T(2));
+        w2 = T(0.5) * (T(4) * t2 + t - T(3) * t3);
+        w3 = T(0.5) * (t3 - t2);
+    }
+};
+
+// Cell index and weights of one coordinate of a density grid: r = knots from
+// the first (clamped to the grid), cell i in [0, n-2], weights at r - i.
+template <class T> __device__ __forceinline__ int grid_cell(T r, int n, T *t) {
+    r = fmin(fmax(r, T(0)), T(n - 1));
+    const int i = min(static_cast<int>(r), n - 2);
+    *t = r - T(i);
+    return i;
+}
+
+// x g(x, Q^2) from a density grid (F_LO_PDF): bicubic Hermite in
+// (log2 x, log2 Q^2) with central-difference tangents.  tbl is the grid padded
+// by one knot on every side, (nx + 2) x (nq + 2) row-major, the padding the
+// linear ghost value 2 f_edge - f_next (which makes the tangent at the first
+// and last knot one-sided); so the 4 x 4 knots around any cell are in the
+// table.  iu / wu: the cell and weights along x, jv / wv along Q^2, pitch =
+// nq + 2.
+template <class T>
+__device__ __forceinline__ T grid_xg(const T *tbl, int pitch, int iu, const CubicWeights<T> &wu, int jv,
+                                     const CubicWeights<T> &wv) {
+    const T *r = tbl + iu * pitch + jv;
+    T acc[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const T *row = r + a * pitch;
+        acc[a] = ffma(wv.w3, row[3], ffma(wv.w2, row[2], ffma(wv.w1, row[1], wv.w0 * row[0])));
+    }
+    return ffma(wu.w3, acc[3], ffma(wu.w2, acc[2], ffma(wu.w1, acc[1], wu.w0 * acc[0])));
+}
 
 // The integrand is split into a per-dimension update (called as each x_j is
 // produced) and a final step.  Normalisation constants that do not depend on
@@ -275,9 +280,16 @@ template <int FAM, class T, int MAXD> struct Integrand {
             const T shat = x0 * x1 * s0;
             const T c = ffma(T(2), x2, T(-1));
             const bool in = (shat >= s4) && (shat <= s5) && (fabs_t(c) < s3);
-            const T lq = flog2(shat);
-            const T g1 = grid_xg(tbl, fc.p, flog2(x0), lq);
-            const T g2 = grid_xg(tbl, fc.p, flog2(x1), lq);
+            // p[0..5]: log2 x of the first knot, knots per unit of log2 x, the
+            // same for log2 Q^2, nx, nq; the scale's weights serve both densities
+            const int nx = static_cast<int>(fc.p[4]), nq = static_cast<int>(fc.p[5]);
+            T tv, t1, t2;
+            const int jv = grid_cell((flog2(shat) - fc.p[2]) * fc.p[3], nq, &tv);
+            const int i1 = grid_cell((flog2(x0) - fc.p[0]) * fc.p[1], nx, &t1);
+            const int i2 = grid_cell((flog2(x1) - fc.p[0]) * fc.p[1], nx, &t2);
+            const CubicWeights<T> wv(tv), w1(t1), w2(t2);
+            const T g1 = grid_xg(tbl, nq + 2, i1, w1, jv, wv);
+            const T g2 = grid_xg(tbl, nq + 2, i2, w2, jv, wv);
             const T dm = shat - s1;
             const T den = ffma(dm, dm, s2) * shat * x0 * x1;
             const T val = g1 * g2 * ffma(c, c, T(1)) * frcp(den);

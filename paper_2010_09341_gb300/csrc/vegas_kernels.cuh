@@ -98,7 +98,8 @@ cudaError_t launch_trace(const SampleArgs &a, int fam, int mode, double inv_scal
 cudaError_t launch_trace_fn(const void *fn, const SampleArgs &a, double inv_scale, int32_t *bins,
                             double *x, double *w, cudaStream_t stream);
 
-// Largest density grid (nx nq values) of the F_LO_PDF family: 48 KB of FP64.
+// Largest density grid of the F_LO_PDF family, counted with its padding,
+// (nx + 2)(nq + 2) values: 48 KB of FP64.
 constexpr int kMaxPdfValues = 6144;
 
 // Kernels of a user integrand compiled at run time (vegas_jit.cu): sampling,

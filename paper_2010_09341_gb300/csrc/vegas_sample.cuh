@@ -60,8 +60,8 @@ struct SampleArgs {
     FamConsts<double> fc64;   // integrand constants, FP64 path
     FamConsts<float> fc32;    // the same rounded to FP32, FP32 paths
     StratArgs st;             // stratified launches: s_begin, n count hypercubes
-    const double *pdf;        // F_LO_PDF: the density grid, pdf_n FP64 values (device)
-    int pdf_n;
+    const double *pdf;        // F_LO_PDF: the density grid, pdf_nx x pdf_nq FP64 values (device)
+    int pdf_nx, pdf_nq;
 };
 
 
@@ -131,15 +131,40 @@ __host__ __device__ constexpr size_t sample_smem_bytes(int d, int N) {
             (MODE != ACC_F64 ? sizeof(uint32_t) : 0));  // single-copy fine cells
 }
 
-// F_LO_PDF: the density grid, converted to the path's precision, follows the
-// block's cells in shared memory; every thread calls this after carve/stage.
+// F_LO_PDF: the density grid (nx x nq FP64, row-major) copied to t in the
+// path's precision, padded by one knot on every side with the linear ghost
+// values 2 f_edge - f_next (a corner: the ghost of the ghost row); every
+// thread of the block calls this, the caller synchronises.
+template <class T>
+__device__ __forceinline__ void stage_grid(T *t, const double *g, int nx, int nq) {
+    const int P = nq + 2;
+    const int total = (nx + 2) * P;
+    for (int k = threadIdx.x; k < total; k += blockDim.x) {
+        const int r = k / P, c = k - r * P;
+        // the row (and column) of g and its neighbour the ghost extrapolates from
+        const int ri = min(max(r - 1, 0), nx - 1), rn = r == 0 ? 1 : nx - 2;
+        const int ci = min(max(c - 1, 0), nq - 1), cn = c == 0 ? 1 : nq - 2;
+        const bool gr = r == 0 || r == nx + 1, gc = c == 0 || c == nq + 1;
+        double v = g[ri * nq + ci];
+        if (gr) v = 2.0 * v - g[rn * nq + ci];
+        if (gc) {
+            double w = g[ri * nq + cn];
+            if (gr) w = 2.0 * w - g[rn * nq + cn];
+            v = 2.0 * v - w;
+        }
+        t[k] = static_cast<T>(v);
+    }
+}
+
+// F_LO_PDF: the padded density grid follows the block's cells in shared
+// memory; every thread calls this after carve/stage.
 template <int FAM, int MODE, int PRIV>
 __device__ __forceinline__ const typename ModeTraits<MODE>::T *stage_pdf(unsigned char *raw, const SampleArgs &a,
                                                                           int d) {
     using T = typename ModeTraits<MODE>::T;
     if (FAM != F_LO_PDF) return nullptr;
     T *t = reinterpret_cast<T *>(raw + sample_smem_bytes<MODE, PRIV>(d, a.N));
-    for (int k = threadIdx.x; k < a.pdf_n; k += blockDim.x) t[k] = static_cast<T>(a.pdf[k]);
+    stage_grid(t, a.pdf, a.pdf_nx, a.pdf_nq);
     return t;
 }
 

@@ -22,7 +22,7 @@ __global__ void trace_kernel(const SampleArgs a, double inv_scale, int32_t *bins
     if (FAM == F_LO_PDF) {
         // the density grid in shared memory, in the path's precision
         T *t = reinterpret_cast<T *>(trace_smem);
-        for (int i = threadIdx.x; i < a.pdf_n; i += blockDim.x) t[i] = static_cast<T>(a.pdf[i]);
+        stage_grid(t, a.pdf, a.pdf_nx, a.pdf_nq);
         __syncthreads();
         fam.tbl = t;
     }
