@@ -219,3 +219,25 @@ def test_strat_checkpoint_keeps_the_setting():
     ra = V.vegas_iterate(a)
     rb = V.vegas_iterate(b)
     assert ra[0] == rb[0] and ra[1] == rb[1]
+
+
+def test_strat_largest_hypercube_count():
+    """The most hypercubes allowed, 2^31 of 2 samples (n = 2^32 + 12345 requested,
+    2^32 used): sample indices pass 2^32 inside the iteration.  Bins of the
+    first and last samples bit-exact against the oracle, the estimate within
+    5 sigma of the closed form."""
+    V = native()
+    d, N, n = 4, 50, (1 << 32) + 12345
+    ctx, p = _make(V, "gauss_sym", d, N, n, "fp32_acc64", -1)
+    Bt, P, used = V.vegas_get_strata(ctx)
+    assert (Bt, P, used) == (31, 2, 1 << 32)
+    e = O.uniform_edges(d, N)
+    for s0 in (0, used - 600):
+        bins, x, w = V.vegas_trace(ctx, 0, s0, 600)
+        bins = bins.cpu().numpy()
+        for k in range(0, 600, 7):
+            ob, _, _, _ = O.sample_strat(d, N, e, "gauss_sym", p, 0, 0, 0, Bt, P, s0 + k)
+            assert np.array_equal(bins[k], ob)
+    I, sigma, n_ok, _ = V.vegas_iterate(ctx)
+    assert n_ok == used
+    assert abs(I - math.erf(5.0) ** d) < 5 * sigma
