@@ -262,8 +262,17 @@ def _time_single(V, torch, family, params, d, N, n, prec, iters, warm=2, iid=0):
     kms = V.vegas_profile_read(ctx)
     res = V.vegas_result(ctx)
     V.vegas_destroy(ctx)
-    return {"samples_per_s": n * iters / (ms / 1e3), "ms_per_iter": ms / iters,
-            "kernel_ms": sum(kms) / max(1, len(kms)), "I": res["I"], "sigma": res["sigma"]}
+    k_ms = sum(kms) / max(1, len(kms))
+    out = {"samples_per_s": n * iters / (ms / 1e3), "ms_per_iter": ms / iters,
+           "kernel_ms": k_ms, "I": res["I"], "sigma": res["sigma"]}
+    if prec != "fp64":
+        # the sampling kernel against the issue bound of its family and d (the FP64
+        # path's bound is its FP64 pipe, which this operation model does not count)
+        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        bound = min(roofline_samples_per_s(ops_per_sample(family, d, prec), sms, 2070e6).values())
+        out["roofline"] = {"bound": "alu", "roofline_samples_per_s": bound,
+                           "frac": (n / (k_ms / 1e3)) / bound}
+    return out
 
 
 def _time_strat(V, torch, family, params, d, N, n, prec, iters=10, warm=5):

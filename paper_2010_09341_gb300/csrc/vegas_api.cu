@@ -408,6 +408,14 @@ vegas_status vegas_create_user(const vegas_config *cfg, const char *source, cons
 
 const char *vegas_jit_log(void) { return jit_last_log(); }
 
+// More blocks than fit the GPU at once run in waves: round their number up to
+// whole waves (each block then takes fewer samples), so that the last wave
+// does not leave most SMs idle.
+static long long whole_waves(long long blocks, long long resident) {
+    if (resident <= 0 || blocks <= resident) return blocks;
+    return (blocks + resident - 1) / resident * resident;
+}
+
 // Stratification in effect for n samples: 2^B hypercubes of P samples, with
 // B = the requested B (or, automatically, as many as leave P >= 2), never more
 // than leave P >= 2, 16 halvings per dimension or 2^31 hypercubes.
@@ -485,6 +493,7 @@ static vegas_status launch_sampling_strat(vegas_ctx *c, const Strata &st, long l
         const long long cap = block_samples_max(c->mode, c->priv ? 1 : 0, c->cfg.n_bins) / st.P;
         blocks = std::max(blocks, (count + cap - 1) / cap);
     }
+    blocks = whole_waves(blocks, c->max_blocks_strat);
     void *params[] = {&a};
     VEGAS_CK(cudaLaunchKernel(c->kfn_strat, dim3(static_cast<unsigned>(blocks)), dim3(c->threads), params,
                               c->smem, c->stream));
@@ -505,6 +514,7 @@ static vegas_status launch_sampling(vegas_ctx *c, long long s_begin, long long n
         const long long cap = block_samples_max(c->mode, c->priv ? 1 : 0, c->cfg.n_bins);
         blocks = std::max(blocks, (n + cap - 1) / cap);
     }
+    blocks = whole_waves(blocks, c->max_blocks);
     void *params[] = {&a};
     VEGAS_CK(cudaLaunchKernel(c->kfn, dim3(static_cast<unsigned>(blocks)), dim3(c->threads), params,
                               c->smem, c->stream));
