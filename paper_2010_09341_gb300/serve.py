@@ -99,6 +99,38 @@ class SamplePolicy:
         rel = res["sigma"] / abs(res["I"])
         return used * (rel / r.target_rel) ** 2 > self.give_up * r.budget
 
+    # -- the same rules over arrays (one entry per active integral) --------
+    @staticmethod
+    def _pow2_ceil_array(x):
+        # exponents above 62 would overflow int64; every cap applied afterwards is smaller
+        e = np.minimum(62.0, np.maximum(0.0, np.ceil(np.log2(np.maximum(1.0, x)))))
+        return np.left_shift(np.int64(1), e.astype(np.int64))
+
+    def next_n_array(self, budget, target, used, n_iter, I, sigma, n_active: int):
+        """next_n for every entry: int64 array."""
+        left = budget - used
+        warm = (n_iter < self.warm_iters) | (sigma <= 0) | (I == 0)
+        if not self.adaptive:
+            warm = np.ones_like(warm)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            rel = np.where(I != 0, sigma / np.abs(I), 0.0)
+        need_total = used * (rel / target) ** 2
+        more = np.maximum(0.0, need_total - used)
+        n = self._pow2_ceil_array(more / self.iters_to_target)
+        n_cap = max(self.n_max, _pow2_ceil(self.step_samples / max(1, n_active)) // 2)
+        adapt = np.maximum(2, np.minimum(np.minimum(np.maximum(self.n_first, n), n_cap), left))
+        first = np.maximum(2, np.minimum(self.n_first, left))
+        return np.where(warm, first, adapt).astype(np.int64)
+
+    def hopeless_array(self, budget, target, used, n_iter, I, sigma):
+        """hopeless for every entry: bool array."""
+        if self.give_up <= 0:
+            return np.zeros(len(used), dtype=bool)
+        ok = (n_iter >= self.give_up_after) & (sigma > 0) & (I != 0)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            rel = np.where(I != 0, sigma / np.abs(I), 0.0)
+        return ok & (used * (rel / target) ** 2 > self.give_up * budget)
+
 
 class Server:
     def __init__(self, max_slots: int = 1024, pool_bytes: int = 512 << 20,
@@ -117,6 +149,11 @@ class Server:
         self.queue = []       # arrived, not yet admitted (arrival order)
         self.steps = 0
         self.samples = 0
+        # per-slot state as arrays, for the vectorised step
+        self.used = np.zeros(max_slots, dtype=np.int64)
+        self.n_cur = np.zeros(max_slots, dtype=np.int64)
+        self.budget = np.zeros(max_slots, dtype=np.float64)
+        self.target = np.zeros(max_slots, dtype=np.float64)
 
     def _admit(self, now: float) -> None:
         while self.queue:
@@ -132,40 +169,58 @@ class Server:
                 raise
             r.admitted = now
             self.active[slot] = [r, 0, n0]
+            self.used[slot] = 0
+            self.n_cur[slot] = n0
+            self.budget[slot] = r.budget
+            self.target[slot] = r.target_rel
             self.queue.pop(0)
 
     def step(self, now_fn) -> list:
-        """One batched iteration of all active integrals; returns retired requests."""
+        """One batched iteration of all active integrals; returns retired requests.
+
+        The rules run over arrays of all active integrals at once (the
+        SamplePolicy array forms); only integrals that retire or change their
+        samples per iteration are touched one by one."""
         if not self.active:
             return []
         self.batch.step()
-        res = self.batch.wait()
+        a = self.batch.wait_array()
         self.steps += 1
         now = now_fn()
+        slots = a["slot"].astype(np.int64)
+        used = self.used[slots] + a["n"] + a["n_nonfinite"]
+        self.used[slots] = used
+        self.samples += int(self.n_cur[slots].sum())
+        I, sigma, m = a["I"], a["sigma"], a["n_iter"]
+        budget, target = self.budget[slots], self.target[slots]
+        conv = (m >= self.min_iters) & (sigma <= target * np.abs(I)) & (I != 0)
+        hopeless = ~conv & (used < budget) & self.policy.hopeless_array(budget, target, used, m, I, sigma)
+        done = conv | (used >= budget) | hopeless
         retired = []
-        for slot, rec in list(self.active.items()):
-            r, used, n = rec
-            out = res[slot]
-            used += out["n"] + out["n_nonfinite"]
-            self.samples += n
-            rec[1] = used
-            conv = (out["n_iter"] >= self.min_iters and out["sigma"] <= r.target_rel * abs(out["I"])
-                    and out["I"] != 0)
-            hopeless = not conv and used < r.budget and self.policy.hopeless(r, used, out)
-            if conv or used >= r.budget or hopeless:
-                r.done = now
-                r.converged = bool(conv)
-                r.gave_up = bool(hopeless)
-                r.result = dict(out)
-                r.result["samples"] = used
-                self.batch.remove(slot)
-                del self.active[slot]
-                retired.append(r)
-                continue
-            nn = self.policy.next_n(r, used, out, len(self.active))
-            if nn != n:
-                self.batch.set_events(slot, nn)
-                rec[2] = nn
+        for k in np.flatnonzero(done):
+            slot = int(slots[k])
+            r = self.active.pop(slot)[0]
+            r.done = now
+            r.converged = bool(conv[k])
+            r.gave_up = bool(hopeless[k])
+            r.result = {"t": int(a["t"][k]), "I_t": float(a["I_t"][k]), "sigma_t": float(a["sigma_t"][k]),
+                        "n": int(a["n"][k]), "n_nonfinite": int(a["n_nonfinite"][k]), "I": float(I[k]),
+                        "sigma": float(sigma[k]), "chi2_dof": float(a["chi2_dof"][k]), "n_iter": int(m[k]),
+                        "samples": int(used[k])}
+            self.batch.remove(slot)
+            retired.append(r)
+        keep = ~done
+        if keep.any():
+            nn = self.policy.next_n_array(budget[keep], target[keep], used[keep], m[keep], I[keep], sigma[keep],
+                                          len(self.active))
+            ks = slots[keep]
+            for slot, n_new in zip(ks[nn != self.n_cur[ks]], nn[nn != self.n_cur[ks]]):
+                self.batch.set_events(int(slot), int(n_new))
+            self.n_cur[ks] = nn
+            for slot, n_new in zip(ks, nn):
+                rec = self.active[int(slot)]
+                rec[1] = int(self.used[slot])
+                rec[2] = int(n_new)
         return retired
 
     def run(self, requests, time_limit: float = 60.0, realtime: bool = True):

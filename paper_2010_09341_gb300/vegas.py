@@ -441,6 +441,19 @@ class Batch:
                                 "n_iter": r.comb.n_iter}
         return out
 
+    # the layout of vegas_batch_result as a numpy record
+    RESULT_DTYPE = np.dtype([("slot", "<i4"), ("t", "<i4"), ("I_t", "<f8"), ("sigma_t", "<f8"),
+                             ("n", "<i8"), ("n_nonfinite", "<i8"), ("I", "<f8"), ("sigma", "<f8"),
+                             ("chi2_dof", "<f8"), ("n_iter", "<i4"), ("reserved", "<i4")])
+
+    def wait_array(self) -> np.ndarray:
+        """Results of the last step as a numpy record array (one entry per
+        integral stepped; fields as vegas_batch_result), a copy."""
+        cnt = ctypes.c_int32()
+        check(nat.load().vegas_batch_wait(self.handle, self._buf, self.max_slots, ctypes.byref(cnt)),
+              "vegas_batch_wait")
+        return np.frombuffer(self._buf, dtype=self.RESULT_DTYPE, count=cnt.value).copy()
+
     def grid(self, slot: int) -> np.ndarray:
         cfg = self.cfgs[int(slot)]
         e = np.zeros((cfg.n_dim, cfg.n_bins + 1), dtype=np.float64)

@@ -50,3 +50,35 @@ def test_give_up_rule():
     assert not p.hopeless(r, 10 ** 8, _res(8, 0.0, 1.0))
     # give_up <= 0 switches the rule off
     assert not SamplePolicy(give_up=0.0).hopeless(r, 10 ** 8, _res(8, 1.0, 1e-3))
+
+
+def test_array_forms_equal_the_scalar_rules():
+    """The server applies the rules to all integrals at once; on random states,
+    zero estimates and variances, exhausted budgets and early iterations they
+    give exactly the scalar rules' answers."""
+    rng = np.random.default_rng(7)
+    k = 4000
+    budget = rng.choice([10 ** 5, 10 ** 7, 10 ** 9], size=k).astype(np.float64)
+    target = 10.0 ** rng.uniform(-5, -3, size=k)
+    used = (budget * rng.uniform(0, 1.2, size=k)).astype(np.int64)
+    n_iter = rng.integers(0, 12, size=k).astype(np.int32)
+    I = rng.normal(0, 1, size=k)
+    I[rng.uniform(size=k) < 0.05] = 0.0
+    sigma = np.abs(I) * 10.0 ** rng.uniform(-6, 0, size=k)
+    sigma[rng.uniform(size=k) < 0.05] = 0.0
+    # projections beyond 2^63 samples: relative error above 10 against a 1e-5 target
+    sigma[:50] = 10.0 * np.abs(I[:50]) + 1.0
+    target[:50] = 1e-5
+    n_iter[:50] = 9
+    used[:50] = (budget[:50] * 0.9).astype(np.int64)
+    for pol in (SamplePolicy(), SamplePolicy(adaptive=False), SamplePolicy(give_up=0.0),
+                SamplePolicy(n_first=1 << 10, n_max=1 << 30, step_samples=1 << 31)):
+        for n_active in (1, 37, 5000):
+            nn = pol.next_n_array(budget, target, used, n_iter, I, sigma, n_active)
+            hh = pol.hopeless_array(budget, target, used, n_iter, I, sigma)
+            for i in list(range(50)) + list(range(50, k, 7)):
+                r = _req(target=float(target[i]), budget=int(budget[i]))
+                res = _res(int(n_iter[i]), float(I[i]), float(sigma[i]))
+                if used[i] < budget[i]:
+                    assert nn[i] == pol.next_n(r, int(used[i]), res, n_active), i
+                assert hh[i] == pol.hopeless(r, int(used[i]), res), i
