@@ -112,9 +112,11 @@ class SamplePolicy:
         warm = (n_iter < self.warm_iters) | (sigma <= 0) | (I == 0)
         if not self.adaptive:
             warm = np.ones_like(warm)
+        # entries that take the first-iterations rule (warm) may divide by zero
+        # here; their value is not used
         with np.errstate(divide="ignore", invalid="ignore"):
             rel = np.where(I != 0, sigma / np.abs(I), 0.0)
-        need_total = used * (rel / target) ** 2
+            need_total = used * (rel / target) ** 2
         more = np.maximum(0.0, need_total - used)
         n = self._pow2_ceil_array(more / self.iters_to_target)
         n_cap = max(self.n_max, _pow2_ceil(self.step_samples / max(1, n_active)) // 2)
@@ -129,7 +131,7 @@ class SamplePolicy:
         ok = (n_iter >= self.give_up_after) & (sigma > 0) & (I != 0)
         with np.errstate(divide="ignore", invalid="ignore"):
             rel = np.where(I != 0, sigma / np.abs(I), 0.0)
-        return ok & (used * (rel / target) ** 2 > self.give_up * budget)
+            return ok & (used * (rel / target) ** 2 > self.give_up * budget)
 
 
 class Server:
