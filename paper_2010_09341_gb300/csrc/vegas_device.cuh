@@ -139,7 +139,13 @@ __device__ __forceinline__ float fexp2(float x) {
     return y;
 }
 __device__ __forceinline__ double fexp2(double x) { return exp2(x); }
-__device__ __forceinline__ float flog2(float x) { return log2f(x); }
+// log2 x for the FP32 path: the hardware approximation (absolute error about
+// 2^-22), subnormal arguments flushed to zero.
+__device__ __forceinline__ float flog2(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 __device__ __forceinline__ double flog2(double x) { return log2(x); }
 // FP32 cosine for moderate arguments: reduce by 2 pi with a two-part constant
 // (Cody & Waite, "Software Manual for the Elementary Functions", 1980):
@@ -160,7 +166,14 @@ __device__ __forceinline__ float fcos(float x) {
 __device__ __forceinline__ double fcos(double x) { return cos(x); }
 __device__ __forceinline__ float frsqrt(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double frsqrt(double x) { return rsqrt(x); }
-__device__ __forceinline__ float frcp(float x) { return 1.0f / x; }
+// 1/x for the FP32 path: the hardware approximation (at most 1 ulp), results
+// below the normal range flushed to zero; an IEEE division would take a
+// multi-instruction sequence with a slow-path branch per sample.
+__device__ __forceinline__ float frcp(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 __device__ __forceinline__ double frcp(double x) { return 1.0 / x; }
 
 // Weights of the cubic through four equally spaced values f0..f3 at t in
