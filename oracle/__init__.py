@@ -89,6 +89,9 @@ def _load():
         lib.oracle_refine.restype = None
         lib.oracle_combine.argtypes = [i32, dp, dp, dp, dp, dp]
         lib.oracle_combine.restype = None
+        lib.oracle_histogram.argtypes = [i32, i32, dp, i32, dp, i32, u32, u32, u32, i32, i64, i64, i64,
+                                         i32, i32, ctypes.c_double, ctypes.c_double, dp]
+        lib.oracle_histogram.restype = None
         lib.oracle_set_pdf_grid.argtypes = [i32, i32, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                             ctypes.c_double, dp]
         lib.oracle_set_pdf_grid.restype = None
@@ -401,3 +404,32 @@ def set_pdf_grid(xg, u0, u1, v0, v1) -> None:
 
 def pdf_xg(x: float, q2: float) -> float:
     return float(_load().oracle_pdf_xg(x, q2))
+
+
+# --------------------------------------------------- observable histograms
+def histogram(d, N, edges, family, params, seed, integral_id, t, n, obs, nb, lo, hi, B=0, P=0,
+              threads=1):
+    """Observable histogram of the n samples of iteration t (stratified when P
+    > 0): (S1[nb + 2], S2[nb + 2]) with bin 0 below lo and bin nb + 1 at or
+    above hi.  Pieces run on host threads are added in thread order."""
+    lib = _load()
+    e = _f64(edges).reshape(d, N + 1)
+    p = _f64(params if len(params) else [0.0])
+    threads = max(1, min(int(threads), max(1, n)))
+    bounds = np.linspace(0, n, threads + 1).astype(np.int64)
+    outs = [np.zeros(2 * (nb + 2)) for _ in range(threads)]
+
+    def run(i):
+        lib.oracle_histogram(d, N, _dptr(e), FAMILIES[family], _dptr(p), len(params), seed,
+                             integral_id, t, B, P, int(bounds[i]), int(bounds[i + 1]), obs, nb, lo, hi,
+                             _dptr(outs[i]))
+
+    ths = [threading.Thread(target=run, args=(i,)) for i in range(threads)]
+    for th in ths:
+        th.start()
+    for th in ths:
+        th.join()
+    tot = np.zeros(2 * (nb + 2))
+    for o in outs:
+        tot += o
+    return tot[:nb + 2], tot[nb + 2:]

@@ -530,3 +530,48 @@ void oracle_strat_result(double S1, double Q, int64_t H, int64_t P, double *I, d
     *I = S1 / (Hd * Pd);
     *var = P > 1 ? Q / (Hd * Hd * Pd * (Pd - 1.0)) : 0.0;
 }
+
+/* ------------------------------------------------ observable histograms */
+/* The paper's generator chain ends in histogramming (Fig. 1): the samples'
+ * weights v = J f binned in an observable.  Observables: a coordinate x_k
+ * (obs = k >= 0), or for the LO toys sqrt(shat) in GeV (obs = -1) and
+ * cos(theta) = 2 x_3 - 1 (obs = -2).  Bin b in 1..nb holds the samples with
+ * lo + (b-1) w <= o < lo + b w, w = (hi - lo)/nb; bin 0 those below lo and bin
+ * nb + 1 those at or above hi.  out[b] += v, out[nb + 2 + b] += v^2; samples
+ * with a non-finite v are left out (a stratified iteration counts them as 0,
+ * which adds nothing). */
+static double observable(int obs, const double *x, const double *params) {
+    if (obs >= 0) return x[obs];
+    if (obs == -1) return sqrt(x[0] * x[1]) * params[0];
+    return 2.0 * x[2] - 1.0;
+}
+
+void oracle_histogram(int d, int N, const double *edges, int family, const double *params,
+                      int n_params, uint32_t seed, uint32_t integral_id, uint32_t t, int B, int64_t P,
+                      int64_t s_begin, int64_t s_end, int obs, int nb, double lo, double hi,
+                      double *out) {
+    int32_t bins[ORACLE_MAXD];
+    double x[ORACLE_MAXD];
+    double w = (hi - lo) / (double)nb;
+    for (int64_t s = s_begin; s < s_end; ++s) {
+        double J, f;
+        if (P > 0)
+            oracle_sample_strat(d, N, edges, family, params, n_params, seed, integral_id, t, B, P,
+                                (uint64_t)s, bins, x, &J, &f);
+        else
+            oracle_sample(d, N, edges, family, params, n_params, seed, integral_id, t, (uint64_t)s,
+                          bins, x, &J, &f);
+        double v = J * f;
+        if (!isfinite(v)) continue;
+        double o = observable(obs, x, params);
+        int b;
+        if (o < lo) b = 0;
+        else if (o >= hi) b = nb + 1;
+        else {
+            b = 1 + (int)floor((o - lo) / w);
+            if (b > nb) b = nb;
+        }
+        out[b] += v;
+        out[nb + 2 + b] += v * v;
+    }
+}

@@ -111,6 +111,17 @@ void oracle_iterate_strat(int d, int N, const double *edges, int family, const d
 /* Stratified estimate: I = S1/(H P), var = Q/(H^2 P (P-1)). */
 void oracle_strat_result(double S1, double Q, int64_t H, int64_t P, double *I, double *var);
 
+/* Observable histogram of samples [s_begin, s_end) of iteration t (P > 0:
+ * the stratified iteration of 2^B hypercubes of P samples, else plain):
+ * out[b] += v, out[nb + 2 + b] += v^2 for the bin b of the sample's observable
+ * (obs >= 0: x_obs; -1: sqrt(shat) = sqrt(x1 x2) params[0]; -2: 2 x3 - 1);
+ * bin 0 below lo, bins 1..nb of width (hi - lo)/nb, bin nb + 1 at or above hi.
+ * Non-finite v are left out.  out: 2 (nb + 2) values, accumulated into. */
+void oracle_histogram(int d, int N, const double *edges, int family, const double *params,
+                      int n_params, uint32_t seed, uint32_t integral_id, uint32_t t, int B, int64_t P,
+                      int64_t s_begin, int64_t s_end, int obs, int nb, double lo, double hi,
+                      double *out);
+
 /* Inverse-variance combination of m iteration results. */
 void oracle_combine(int m, const double *I, const double *sigma, double *Ibar, double *sbar,
                     double *chi2_dof);
