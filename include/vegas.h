@@ -249,6 +249,24 @@ vegas_status vegas_set_iteration(vegas_ctx *ctx, int32_t t);
 vegas_status vegas_trace(vegas_ctx *ctx, int32_t t, int64_t s_begin, int64_t count,
                          int32_t *dev_bins, double *dev_x, double *dev_w);
 
+/* Observable histogram of iteration t's weights, for the analysis step that
+ * follows integration in the paper's generator chain (Fig. 1: histogramming).
+ * Every sample iteration t would draw on the context's current grid (the
+ * stratified set when vegas_set_strata is on) is computed again, and its
+ * weight v = J f (unscaled; left out if not finite) is added to the bin of
+ * its observable o, in shared memory per block, with no traffic per sample:
+ *   observable >= 0 : o = x_observable (a coordinate, < n_dim);
+ *   -1 (LO families): o = sqrt(shat) = sqrt(x1 x2) sqrtS, in GeV;
+ *   -2 (LO families): o = cos(theta) = 2 x3 - 1.
+ * dev_out (device, FP64, 2 (nbins + 2) values, zeroed by the call): dev_out[b]
+ * = sum of v and dev_out[nbins + 2 + b] = sum of v^2 over the samples of bin b,
+ * with bin 0 below lo, bin 1 + floor((o - lo)/w) (w = (hi - lo)/nbins, at most
+ * nbins) up to hi and bin nbins + 1 at or above hi.  dev_out[b] / n is bin b's
+ * part of the iteration's estimate (n = the samples the iteration uses).  Does
+ * not change the context's state.  1 <= nbins <= 1024.  Asynchronous. */
+vegas_status vegas_histogram(vegas_ctx *ctx, int32_t t, int32_t observable, int32_t nbins, double lo, double hi,
+                             double *dev_out);
+
 /* Stratified + importance hybrid: the combined mode of Lepage's VEGAS (Cornell
  * CLNS-80/447, 1980; the method the paper takes as VegasFlow's, Sec. 1), in
  * which y-space is also cut into equal hypercubes that each receive the same

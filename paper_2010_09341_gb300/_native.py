@@ -92,6 +92,8 @@ _SIGS = {
                                          ctypes.POINTER(ctypes.c_double), ctypes.c_int32, _P, _P,
                                          ctypes.c_size_t, ctypes.POINTER(_P)]),
     "vegas_jit_log": (ctypes.c_char_p, []),
+    "vegas_histogram": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                       ctypes.c_double, _P]),
     "vegas_set_pdf_grid": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_double, ctypes.c_double]),
     "vegas_get_strata": (ctypes.c_int, [_P, _P, _P, _P]),

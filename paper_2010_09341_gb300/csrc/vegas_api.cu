@@ -765,9 +765,35 @@ vegas_status vegas_trace(vegas_ctx *c, int32_t t, int64_t s_begin, int64_t count
         fill_strata(a, sg, c->cfg.n_dim, nullptr);
     }
     if (c->family == VEGAS_F_USER)
-        VEGAS_CK(launch_trace_fn(c->jit.trace, a, 1.0 / c->scale, bins, x, w, c->stream));
+        VEGAS_CK(launch_trace_fn(c->jit.trace, a, 1.0 / c->scale, bins, x, w, nullptr, c->stream));
     else
         VEGAS_CK(launch_trace(a, c->family, c->mode, 1.0 / c->scale, bins, x, w, c->stream));
+    return VEGAS_OK;
+}
+
+vegas_status vegas_histogram(vegas_ctx *c, int32_t t, int32_t observable, int32_t nbins, double lo, double hi,
+                             double *dev_out) {
+    if (!c || t < 0 || nbins < 1 || nbins > 1024 || !(hi > lo) || !std::isfinite(lo) || !std::isfinite(hi) ||
+        !dev_out || (reinterpret_cast<uintptr_t>(dev_out) % alignof(double)) != 0)
+        return VEGAS_EINVAL;
+    const bool lo_family = c->family == VEGAS_F_LO || c->family == VEGAS_F_LO_PDF;
+    if (observable >= c->cfg.n_dim || observable < -2 || (observable < 0 && !lo_family)) return VEGAS_EINVAL;
+    if (c->family == VEGAS_F_LO_PDF && !c->pdf) return VEGAS_EINVAL;
+    const Strata sg = strata_for(c->strat_req, c->cfg.n_dim, c->cfg.n_events);
+    const long long n = sg.P > 0 ? sg.H * sg.P : c->cfg.n_events;
+    SampleArgs a = make_args(c, 0, n, t);
+    if (sg.P > 0) fill_strata(a, sg, c->cfg.n_dim, nullptr);
+    HistArgs h;
+    h.out = dev_out;
+    h.nb = nbins;
+    h.obs = observable;
+    h.lo = lo;
+    h.hi = hi;
+    h.w = (hi - lo) / static_cast<double>(nbins);
+    h.sqrt_s = lo_family ? c->params[0] : 0.0;
+    VEGAS_CK(cudaMemsetAsync(dev_out, 0, sizeof(double) * 2 * (nbins + 2), c->stream));
+    const void *fn = c->family == VEGAS_F_USER ? c->jit.trace : trace_kernel_for(c->family, c->mode, c->cfg.n_dim);
+    VEGAS_CK(launch_trace_fn(fn, a, 1.0 / c->scale, nullptr, nullptr, nullptr, &h, c->stream));
     return VEGAS_OK;
 }
 

@@ -6,6 +6,9 @@
 // it (a rebinned edge is a difference of running sums; chi^2 is a sum of
 // squared deviations), and they touch O(d N) values, so their cost is
 // launch latency, not arithmetic.
+#include <algorithm>
+#include <cstring>
+
 #include "vegas_kernels.cuh"
 #include "vegas_refine.cuh"
 #include "vegas_trace.cuh"
@@ -224,20 +227,38 @@ cudaError_t launch_trace(const SampleArgs &a, int fam, int mode, double inv_scal
     // only changes how sums are kept, which the trace does not do.
     if (mode == ACC_F64) fn = trace_pick_fam<ACC_F64>(fam, tier);
     else fn = trace_pick_fam<ACC_F32_KAHAN>(fam, tier);
-    return launch_trace_fn(fn, a, inv_scale, bins, x, w, stream);
+    return launch_trace_fn(fn, a, inv_scale, bins, x, w, nullptr, stream);
+}
+
+const void *trace_kernel_for(int fam, int mode, int d) {
+    const int tier = tier_of(d);
+    return mode == ACC_F64 ? trace_pick_fam<ACC_F64>(fam, tier) : trace_pick_fam<ACC_F32_KAHAN>(fam, tier);
 }
 
 cudaError_t launch_trace_fn(const void *fn, const SampleArgs &a, double inv_scale, int32_t *bins,
-                            double *x, double *w, cudaStream_t stream) {
+                            double *x, double *w, const HistArgs *hist, cudaStream_t stream) {
     if (!fn) return cudaErrorInvalidValue;
     if (a.n <= 0) return cudaSuccess;
     const unsigned threads = 256;
-    const unsigned blocks = static_cast<unsigned>((a.n + threads - 1) / threads);
+    long long blocks = (a.n + threads - 1) / threads;
+    HistArgs h;
+    memset(&h, 0, sizeof(h));
+    if (hist) {
+        h = *hist;
+        blocks = std::min(blocks, 2048LL);  // grid-stride: one histogram flush per block
+    }
     SampleArgs args = a;
-    void *params[] = {&args, &inv_scale, &bins, &x, &w};
-    // a density grid is staged, padded, in shared memory (at most kMaxPdfValues FP64 values: 48 KB)
-    const size_t smem = a.pdf ? static_cast<size_t>(a.pdf_nx + 2) * (a.pdf_nq + 2) * sizeof(double) : 0;
-    return cudaLaunchKernel(fn, dim3(blocks), dim3(threads), params, smem, stream);
+    void *params[] = {&args, &inv_scale, &bins, &x, &w, &h};
+    // shared memory: a density grid, padded (at most kMaxPdfValues FP64 values: 48 KB), then the
+    // block's histogram (at most 2 (1024 + 2) FP64 values)
+    size_t smem = a.pdf ? (static_cast<size_t>(a.pdf_nx + 2) * (a.pdf_nq + 2) * sizeof(double) + 15) / 16 * 16 : 0;
+    if (hist) smem += static_cast<size_t>(2 * (h.nb + 2)) * sizeof(double);
+    if (smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+    }
+    return cudaLaunchKernel(fn, dim3(static_cast<unsigned>(blocks)), dim3(threads), params, smem, stream);
 }
 
 // --------------------------------------------------------------- Philox

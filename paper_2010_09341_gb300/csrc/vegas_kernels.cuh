@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include "vegas_sample.cuh"
+#include "vegas_trace.cuh"
 
 namespace vegas {
 
@@ -94,9 +95,12 @@ cudaError_t launch_table_from_edges(const double *edges, void *table, int mode, 
 cudaError_t launch_trace(const SampleArgs &a, int fam, int mode, double inv_scale, int32_t *bins,
                          double *x, double *w, cudaStream_t stream);
 
-// The same with the trace kernel given (a run-time compiled user integrand's).
+// The same with the trace kernel given (a run-time compiled user integrand's);
+// with hist, the samples' weights are also binned in an observable (HistArgs).
 cudaError_t launch_trace_fn(const void *fn, const SampleArgs &a, double inv_scale, int32_t *bins,
-                            double *x, double *w, cudaStream_t stream);
+                            double *x, double *w, const HistArgs *hist, cudaStream_t stream);
+// The built-in trace kernel of (family, mode, d); null if none.
+const void *trace_kernel_for(int fam, int mode, int d);
 
 // Largest density grid of the F_LO_PDF family, counted with its padding,
 // (nx + 2)(nq + 2) values: 48 KB of FP64.

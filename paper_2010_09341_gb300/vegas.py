@@ -240,6 +240,17 @@ def vegas_set_strata(ctx: Context, B: int) -> None:
     check(nat.load().vegas_set_strata(ctx.handle, int(B)), "vegas_set_strata")
 
 
+def vegas_histogram(ctx: Context, t: int, observable: int, nbins: int, lo: float, hi: float):
+    """Observable histogram of iteration t's weights: (sum v, sum v^2) per bin as
+    float64 CUDA tensors of nbins + 2 (bin 0 below lo, the last at or above hi).
+    observable: a coordinate index, or -1 (sqrt(shat)) / -2 (cos theta) for the
+    LO families."""
+    out = torch.empty(2 * (nbins + 2), dtype=torch.float64, device="cuda")
+    check(nat.load().vegas_histogram(ctx.handle, int(t), int(observable), int(nbins), float(lo), float(hi),
+                                     ctypes.c_void_p(out.data_ptr())), "vegas_histogram")
+    return out[:nbins + 2], out[nbins + 2:]
+
+
 def vegas_set_pdf_grid(ctx: Context, xg: torch.Tensor, u0: float, u1: float, v0: float,
                        v1: float) -> None:
     """Density grid of an "lo_pdf" context: xg (nx, nq) float64 CUDA tensor of
