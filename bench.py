@@ -33,6 +33,7 @@ METRIC = "Vegas samples/s (% of roofline)"
 UNIT = "samples/s"
 D, NBINS, NEVENTS, ALPHA = 8, 50, 10_000_000, 1.5
 PRECISION = "fp32_acc64"
+PROFILE_EVERY = 4             # timed steps per step with kernel events
 WORKLOAD = "d=8 Gaussian a=0.1 + d=8 Genz oscillatory (c~U(0,1) seed 1), 50 bins, 1e7 samples/iter each, FP32 sampling, FP64 accumulators"
 
 # Unit counts used for the issue roofline (per SM per clock); the measured
@@ -551,14 +552,17 @@ def main():
     l2_flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     def step():
+        # both integrals: each one's sampling launch, then one launch for both
+        # iteration results and refinements
+        V.vegas_step_many(ctxs)
+
+    def profile(on):
         for c in ctxs:
-            V.vegas_step(c, sync=False)  # iterate + refine
+            V.vegas_profile(c, on)
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    for c in ctxs:
-        V.vegas_profile(c, True)
 
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
@@ -570,9 +574,17 @@ def main():
     torch.cuda.synchronize()
     for k in range(args.steps):
         l2_flush.zero_()  # L2 flush between steps, outside the step events
+        # CUDA events around the sampling launches of every PROFILE_EVERY-th
+        # step give the kernel durations (an event pair between two launches
+        # costs the step about 2 us)
+        prof = k % PROFILE_EVERY == 0
+        if prof:
+            profile(True)
         ev[k][0].record(stream)
         step()
         ev[k][1].record(stream)
+        if prof:
+            profile(False)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -580,8 +592,6 @@ def main():
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
     kern_ms = {c.family: V.vegas_profile_read(c) for c in ctxs}
-    for c in ctxs:
-        V.vegas_profile(c, False)
     t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -708,11 +718,12 @@ def main():
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "samples_per_step": samples_per_step,
                        "bins": NBINS, "dims": D, "precision": PRECISION,
-                       "step": "one iteration (sample, then finalize + refine in one launch) of both integrals",
+                       "step": "one iteration of both integrals (vegas_step_many): each one's sampling launch, then one finalize + refine launch for both",
+                       "kernel_timing": "CUDA events around the sampling launches of every %dth timed step" % PROFILE_EVERY,
                        "l2": "flushed between steps (256 MiB write outside the step events); the kernel reads no HBM inputs",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "extra": extra,
-            "gpu_launches": args.steps * 2 * len(ctxs),
+            "gpu_launches": args.steps * (len(ctxs) + 1),
             "clocks": clk,
         }
         print(json.dumps(out))

@@ -212,6 +212,20 @@ vegas_status vegas_finalize(vegas_ctx *ctx, vegas_iter_result *out);
  * but the last).  Same results as the two calls. */
 vegas_status vegas_step(vegas_ctx *ctx, vegas_iter_result *out);
 
+/* One vegas_step (sampling, iteration result, refinement; Sec. 2 and 3) of
+ * each of n independent integrals, 1 <= n <= VEGAS_MAX_STEP_MANY: their
+ * sampling launches in the given order, then ONE launch for all n iteration
+ * results and refinements (d_k + 1 blocks for context k), so that a set of
+ * integrals advanced together pays one small launch per iteration, not n.
+ * ctxs: n distinct contexts (host array, read during the call) that share one
+ * stream.  Asynchronous: read the results with vegas_result / vegas_run's
+ * records.  Each context's results equal those of vegas_step on it.
+ * Errors: VEGAS_EINVAL for a NULL array or context, n out of range, a context
+ * given twice, contexts on different streams, or a density-grid context
+ * without its grid (nothing is launched then); a launch error as vegas_step. */
+#define VEGAS_MAX_STEP_MANY 8
+vegas_status vegas_step_many(vegas_ctx *const *ctxs, int32_t n);
+
 /* Refine the grid from the last iteration's histograms (asynchronous). */
 vegas_status vegas_refine(vegas_ctx *ctx);
 

@@ -76,6 +76,7 @@ _SIGS = {
                                           ctypes.POINTER(_P)]),
     "vegas_finalize": (ctypes.c_int, [_P, ctypes.POINTER(VegasIterResult)]),
     "vegas_step": (ctypes.c_int, [_P, ctypes.POINTER(VegasIterResult)]),
+    "vegas_step_many": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32]),
     "vegas_refine": (ctypes.c_int, [_P]),
     "vegas_result": (ctypes.c_int, [_P, ctypes.POINTER(VegasResult)]),
     "vegas_run": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(VegasIterResult),

@@ -495,8 +495,8 @@ static vegas_status launch_sampling_strat(vegas_ctx *c, const Strata &st, long l
     }
     blocks = whole_waves(blocks, c->max_blocks_strat);
     void *params[] = {&a};
-    VEGAS_CK(cudaLaunchKernel(c->kfn_strat, dim3(static_cast<unsigned>(blocks)), dim3(c->threads), params,
-                              c->smem, c->stream));
+    VEGAS_CK(launch_programmatic(c->kfn_strat, dim3(static_cast<unsigned>(blocks)), dim3(c->threads), params,
+                                 c->smem, c->stream));
     return VEGAS_OK;
 }
 
@@ -516,8 +516,8 @@ static vegas_status launch_sampling(vegas_ctx *c, long long s_begin, long long n
     }
     blocks = whole_waves(blocks, c->max_blocks);
     void *params[] = {&a};
-    VEGAS_CK(cudaLaunchKernel(c->kfn, dim3(static_cast<unsigned>(blocks)), dim3(c->threads), params,
-                              c->smem, c->stream));
+    VEGAS_CK(launch_programmatic(c->kfn, dim3(static_cast<unsigned>(blocks)), dim3(c->threads), params,
+                                 c->smem, c->stream));
     return VEGAS_OK;
 }
 
@@ -611,13 +611,45 @@ vegas_status vegas_iterate(vegas_ctx *c, vegas_iter_result *out) {
     return finalize_iteration(c, out);
 }
 
+static RefineJob refine_job(vegas_ctx *c) {
+    RefineJob r;
+    r.f = finalize_args(c);
+    r.edges = c->edges;
+    r.table = c->table;
+    r.mode = c->mode;
+    r.d = c->cfg.n_dim;
+    r.N = c->cfg.n_bins;
+    r.smooth = c->cfg.smooth;
+    r.alpha = c->cfg.alpha;
+    return r;
+}
+
 vegas_status vegas_step(vegas_ctx *c, vegas_iter_result *out) {
     if (!c) return VEGAS_EINVAL;
     const vegas_status st = sample_samples(c, 0, c->cfg.n_events);
     if (st != VEGAS_OK) return st;
-    VEGAS_CK(launch_finalize_refine(finalize_args(c), c->edges, c->table, c->mode, c->cfg.n_dim,
-                                    c->cfg.n_bins, c->cfg.alpha, c->cfg.smooth, c->stream));
+    const RefineJob r = refine_job(c);
+    VEGAS_CK(launch_finalize_refine(&r, 1, c->stream));
     return after_finalize(c, out);
+}
+
+vegas_status vegas_step_many(vegas_ctx *const *ctxs, int32_t n) {
+    if (!ctxs || n < 1 || n > VEGAS_MAX_STEP_MANY) return VEGAS_EINVAL;
+    for (int k = 0; k < n; ++k) {
+        if (!ctxs[k] || ctxs[k]->stream != ctxs[0]->stream) return VEGAS_EINVAL;
+        for (int i = 0; i < k; ++i)
+            if (ctxs[i] == ctxs[k]) return VEGAS_EINVAL;
+        if (ctxs[k]->family == VEGAS_F_LO_PDF && !ctxs[k]->pdf) return VEGAS_EINVAL;
+    }
+    RefineJob jobs[VEGAS_MAX_STEP_MANY];
+    for (int k = 0; k < n; ++k) {
+        const vegas_status st = sample_samples(ctxs[k], 0, ctxs[k]->cfg.n_events);
+        if (st != VEGAS_OK) return st;
+        jobs[k] = refine_job(ctxs[k]);
+    }
+    VEGAS_CK(launch_finalize_refine(jobs, n, ctxs[0]->stream));
+    for (int k = 0; k < n; ++k) after_finalize(ctxs[k], nullptr);
+    return VEGAS_OK;
 }
 
 vegas_status vegas_sample_shard(vegas_ctx *c, int64_t s_begin, int64_t count) {

@@ -140,33 +140,66 @@ refine_kernel(const double *last, double *edges, void *table, int mode, int N, d
                  smooth, rs);
 }
 
-// Finalize and refinement of one iteration in one launch (d + 1 blocks):
-// block j < d refines dimension j from its accumulator row (refinement only
+// Finalize and refinement of one iteration of each of js.n integrals in one
+// launch (d_k + 1 blocks for integral k, in order): block j < d_k refines
+// dimension j of integral k from its accumulator row (refinement only
 // normalises the histogram, so the row's scale does not matter) and then
-// moves the row to `last`; block d forms the iteration result.
-__global__ void __launch_bounds__(kRefineThreads)
-finalize_refine_kernel(const FinalizeArgs f, double *edges, void *table, int mode, int d, int N,
-                       double alpha, int smooth) {
+// moves the row to `last`; block d_k forms integral k's iteration result.
+__global__ void __launch_bounds__(kRefineThreads) finalize_refine_kernel(const RefineJobs js) {
     extern __shared__ double rs[];
-    const int j = blockIdx.x;
-    if (j == d) {
-        if (threadIdx.x == 0) finalize_stats(f);
+    pdl_begin();
+    int j = blockIdx.x, k = 0;
+    while (k + 1 < js.n && j > js.job[k].d) {
+        j -= js.job[k].d + 1;
+        ++k;
+    }
+    const RefineJob &r = js.job[k];
+    if (j == r.d) {
+        if (threadIdx.x == 0) finalize_stats(r.f);
         return;
     }
-    const size_t entry = mode == ACC_F64 ? sizeof(double2) : sizeof(float2);
-    refine_block(f.acc + 2 + static_cast<size_t>(j) * N, edges + static_cast<size_t>(j) * (N + 1),
-                 static_cast<char *>(table) + entry * static_cast<size_t>(j) * N, mode, N, alpha,
-                 smooth, rs);
+    const int N = r.N;
+    const size_t entry = r.mode == ACC_F64 ? sizeof(double2) : sizeof(float2);
+    refine_block(r.f.acc + 2 + static_cast<size_t>(j) * N, r.edges + static_cast<size_t>(j) * (N + 1),
+                 static_cast<char *>(r.table) + entry * static_cast<size_t>(j) * N, r.mode, N, r.alpha,
+                 r.smooth, rs);
     __syncthreads();
-    move_rows(f, 2 + j * N, 2 + (j + 1) * N);
+    move_rows(r.f, 2 + j * N, 2 + (j + 1) * N);
 }
 
-cudaError_t launch_finalize_refine(const FinalizeArgs &f, double *edges, void *table, int mode,
-                                   int d, int N, double alpha, int smooth, cudaStream_t stream) {
-    const size_t smem = static_cast<size_t>(4 * N + 2) * sizeof(double);
-    finalize_refine_kernel<<<d + 1, kRefineThreads, smem, stream>>>(f, edges, table, mode, d, N, alpha,
-                                                                    smooth);
+cudaError_t launch_finalize_refine(const RefineJob *jobs, int n, cudaStream_t stream) {
+    if (n < 1 || n > kMaxRefineJobs) return cudaErrorInvalidValue;
+    RefineJobs js;
+    js.n = n;
+    int blocks = 0, maxN = 0;
+    for (int k = 0; k < n; ++k) {
+        js.job[k] = jobs[k];
+        blocks += jobs[k].d + 1;
+        maxN = std::max(maxN, jobs[k].N);
+    }
+    const size_t smem = static_cast<size_t>(4 * maxN + 2) * sizeof(double);
+    // An ordinary launch: its few FP64-bound blocks then start on idle SMs,
+    // one per SM.  Launched early (programmatic), they would take the first
+    // SMs that the sampling kernel's tail frees, several to an SM, and share
+    // its FP64 units.  Its pdl_begin still lets the next sampling launch start
+    // early.
+    finalize_refine_kernel<<<blocks, kRefineThreads, smem, stream>>>(js);
     return cudaGetLastError();
+}
+
+cudaError_t launch_programmatic(const void *fn, dim3 grid, dim3 block, void **params, size_t smem,
+                                cudaStream_t stream) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, fn, params);
 }
 
 cudaError_t launch_refine(const double *last, double *edges, void *table, int mode, int d, int N,

@@ -120,6 +120,7 @@ batch_sample_kernel_t(const BatchArgs ba) {
     FamConsts<T> &fc_s = batch_fc<T>();
     __shared__ long long s_tile;
     __shared__ int s_item;
+    __shared__ T s_scal[2];
     const PlanHeader hdr = *ba.hdr;
     BS bs;
     ThreadSums<MODE> ts;
@@ -155,7 +156,7 @@ batch_sample_kernel_t(const BatchArgs ba) {
         const int item = s_item;
         if (item < 0) break;
         if (item != cur) {
-            if (cur >= 0) flush_block<MODE, PRIV>(bs, ts, rp.hs, sd->acc, &sd->nonfinite);
+            if (cur >= 0) flush_block<MODE, PRIV>(bs, ts, rp.hs, sd->acc, &sd->nonfinite, nullptr, true);
             sd = &ba.slots[ba.items[item]];
             fam = sd->family;
             rp.d = sd->d;
@@ -163,9 +164,11 @@ batch_sample_kernel_t(const BatchArgs ba) {
             rp.key0 = sd->key0;
             rp.key1 = sd->key1;
             rp.iter = static_cast<uint32_t>(sd->t);
-            rp.jinit = MODE == ACC_F64 ? static_cast<T>(sd->jinit64 * sd->jmul)
-                                       : static_cast<T>(static_cast<double>(sd->jinit32) * sd->jmul);
-            rp.n4 = static_cast<T>(sd->n4);
+            if (threadIdx.x == 0) {  // FP64 scalars once per block (read after the barrier below)
+                s_scal[0] = MODE == ACC_F64 ? static_cast<T>(sd->jinit64 * sd->jmul)
+                                            : static_cast<T>(static_cast<double>(sd->jinit32) * sd->jmul);
+                s_scal[1] = static_cast<T>(sd->n4);
+            }
             rp.hs = MODE != ACC_F64 ? sd->hscale : 0.f;
             rp.acc = sd->acc;
             n_cur = sd->n;
@@ -181,6 +184,8 @@ batch_sample_kernel_t(const BatchArgs ba) {
             bs.carve(smem_raw, rp.d * rp.N);
             bs.stage(sd->table);
             __syncthreads();
+            rp.jinit = s_scal[0];
+            rp.n4 = s_scal[1];
             cur = item;
         }
         long long s0 = (tile - ba.tile_prefix[item]) * static_cast<long long>(hdr.tile_samples);
@@ -201,7 +206,7 @@ batch_sample_kernel_t(const BatchArgs ba) {
         }
         __syncthreads();  // s_tile / s_item are rewritten by the next claim
     }
-    if (cur >= 0) flush_block<MODE, PRIV>(bs, ts, rp.hs, sd->acc, &sd->nonfinite);
+    if (cur >= 0) flush_block<MODE, PRIV>(bs, ts, rp.hs, sd->acc, &sd->nonfinite, nullptr, true);
 }
 
 }  // namespace vegas

@@ -31,6 +31,19 @@ template <class T> __device__ T user_integrand(const T *x, int d, const T *p);
 
 namespace vegas {
 
+// ------------------------------------------------- programmatic launch
+// The sampling kernels are launched with programmatic stream serialisation:
+// such a launch may be scheduled once every block of the kernel before it has
+// passed pdl_begin (or exited), and its blocks wait in pdl_begin until that
+// grid has completed and its writes are visible.  So the next kernel's launch
+// and block dispatch overlap this one's tail.  A kernel that calls pdl_begin
+// reads nothing an earlier launch wrote before it; launched without the
+// attribute, the wait returns at once.
+__device__ __forceinline__ void pdl_begin() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // ---------------------------------------------------------------- Philox
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as
 // easy as 1, 2, 3", SC'11): ten rounds of two 32x32->64 multiplies and

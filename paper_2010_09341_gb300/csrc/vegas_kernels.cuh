@@ -78,9 +78,27 @@ struct FinalizeArgs {
     double *q;
 };
 cudaError_t launch_finalize(const FinalizeArgs &f, cudaStream_t stream);
-// Finalize and refinement in one launch (vegas_step).
-cudaError_t launch_finalize_refine(const FinalizeArgs &f, double *edges, void *table, int mode,
-                                   int d, int N, double alpha, int smooth, cudaStream_t stream);
+// Finalize and refinement of one integral's iteration: its FP64 edges and
+// sampling table (of `mode`), d dimensions of N bins, damping alpha.
+struct RefineJob {
+    FinalizeArgs f;
+    double *edges;
+    void *table;
+    int mode, d, N, smooth;
+    double alpha;
+};
+constexpr int kMaxRefineJobs = 8;
+struct RefineJobs {
+    RefineJob job[kMaxRefineJobs];
+    int n;
+};
+// Finalize and refinement of n <= kMaxRefineJobs integrals in one launch
+// (vegas_step, vegas_step_many).
+cudaError_t launch_finalize_refine(const RefineJob *jobs, int n, cudaStream_t stream);
+// A launch with programmatic stream serialisation (the kernel calls
+// pdl_begin before it reads anything an earlier launch wrote).
+cudaError_t launch_programmatic(const void *fn, dim3 grid, dim3 block, void **params, size_t smem,
+                                cudaStream_t stream);
 
 // Refine every dimension from the histograms in last[2..] and write the new
 // FP64 edges and the sampling table of the given mode.

@@ -92,7 +92,8 @@ template <> __device__ __forceinline__ const FamConsts<float> &consts<float>(con
 // (below), so that no cell can reach 2^32.  With S = 0 (first
 // iteration) the lane-private cells hold FP32 and take every value.  Zero
 // weights touch no cell.
-constexpr float kFineScale = 65536.0f;    // 2^16
+constexpr int kFineShift = 16;
+constexpr float kFineScale = 65536.0f;    // 2^kFineShift
 constexpr float kFineInv = 1.0f / 65536.0f;
 constexpr float kFixedMax = 8388608.0f;   // 2^23
 
@@ -471,17 +472,23 @@ __device__ __forceinline__ void sample_range(const BlockState<MODE, PRIV> &bs,
 // with a barrier (every thread's samples are in) and ends with one (the
 // shared cells may be reused).  Resets ts.
 // q (stratified launches, else null): FP64 accumulator of the hypercube m2 sums.
+// table_free: the caller reads the staged table no more (the end of a launch,
+// or a re-stage next), so its shared memory may hold the block's partial sums.
 template <int MODE, int PRIV>
 __device__ __forceinline__ void flush_block(const BlockState<MODE, PRIV> &bs, ThreadSums<MODE> &ts,
                                             float hs, double *acc, unsigned long long *n_nonfinite,
-                                            double *q = nullptr) {
+                                            double *q = nullptr, bool table_free = false) {
     using BS = BlockState<MODE, PRIV>;
     using H = typename BS::H;
+    using T2 = typename BS::T2;
     constexpr int HP = BS::HP;
+    constexpr int TP = BS::TP;
     __shared__ double red1[32], red2[32], redq[32];
     __shared__ unsigned int rednf[32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nwarps = blockDim.x >> 5;
+    __shared__ double inv_s[2];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nthr = blockDim.x, nwarps = nthr >> 5;
+    const bool fixed = hs > 0.f;
     double b1, b2;
     if (MODE == ACC_F32_KAHAN) {
         b1 = static_cast<double>(ts.s1f) - static_cast<double>(ts.c1f);
@@ -490,50 +497,85 @@ __device__ __forceinline__ void flush_block(const BlockState<MODE, PRIV> &bs, Th
         b1 = ts.s1d;
         b2 = ts.s2d;
     }
-    b1 = warp_sum(b1);
-    b2 = warp_sum(b2);
-    const double bq = q ? warp_sum(ts.qd) : 0.0;
+    double bq = ts.qd;
     const unsigned int nf = __reduce_add_sync(0xFFFFFFFFu, ts.nonfinite);
     ts = ThreadSums<MODE>();
-    __syncthreads();
-    if (lane == 0) {
-        red1[warp] = b1;
-        red2[warp] = b2;
-        redq[warp] = bq;
-        rednf[warp] = nf;
+    // A warp's FP64 instruction holds its scheduler's FP64 unit for about 76
+    // cycles on this GPU, and every block flushes at the same moment at the end
+    // of a launch.  So the FP64 scalars are formed once per block, and, where the
+    // table copies are no longer needed, the block sums take a shared-memory
+    // tree (each level half the warps of the one before: 40 FP64 warp
+    // instructions for two sums of 512) instead of a shuffle tree in every warp
+    // (170).
+    const int nsum = q ? 3 : 2;
+    const bool tree = table_free && nthr >= 64 && (nthr & (nthr - 1)) == 0 &&
+                      static_cast<size_t>(bs.cells) * TP * sizeof(T2) >=
+                          static_cast<size_t>(nsum) * nthr * sizeof(double);
+    __syncthreads();  // every thread's samples are in
+    if (tid == 0) {
+        inv_s[0] = fixed ? 1.0 / static_cast<double>(hs) : 0.0;
+        inv_s[1] = inv_s[0] * static_cast<double>(kFineInv);
     }
-    __syncthreads();
-    if (warp == 0) {
-        double x1 = lane < nwarps ? red1[lane] : 0.0;
-        double x2 = lane < nwarps ? red2[lane] : 0.0;
-        unsigned int xn = lane < nwarps ? rednf[lane] : 0u;
-        x1 = warp_sum(x1);
-        x2 = warp_sum(x2);
-        xn = __reduce_add_sync(0xFFFFFFFFu, xn);
-        if (q) {
-            const double xq = warp_sum(lane < nwarps ? redq[lane] : 0.0);
-            if (lane == 0) atomicAdd(q, xq);
+    if (lane == 0) rednf[warp] = nf;
+    if (tree) {
+        double *part = reinterpret_cast<double *>(bs.tab);
+        part[tid] = b1;
+        part[nthr + tid] = b2;
+        if (q) part[2 * nthr + tid] = bq;
+        __syncthreads();
+        for (int h = nthr >> 1; h >= 32; h >>= 1) {
+            const int lh = __ffs(h) - 1;
+            for (int t = tid; t < nsum * h; t += nthr) {
+                double *p = part + (t >> lh) * nthr + (t & (h - 1));
+                p[0] += p[h];
+            }
+            __syncthreads();
         }
+        if (warp < nsum) {
+            const double x = warp_sum(part[warp * nthr + lane]);
+            if (lane == 0) atomicAdd(warp == 2 ? q : acc + warp, x);
+        }
+    } else {
+        b1 = warp_sum(b1);
+        b2 = warp_sum(b2);
+        if (q) bq = warp_sum(bq);
         if (lane == 0) {
-            atomicAdd(acc + 0, x1);
-            atomicAdd(acc + 1, x2);
-            if (xn) atomicAdd(n_nonfinite, static_cast<unsigned long long>(xn));
+            red1[warp] = b1;
+            red2[warp] = b2;
+            redq[warp] = bq;
         }
+        __syncthreads();
+        if (warp == 0) {
+            const double x1 = warp_sum(lane < nwarps ? red1[lane] : 0.0);
+            const double x2 = warp_sum(lane < nwarps ? red2[lane] : 0.0);
+            if (q) {
+                const double xq = warp_sum(lane < nwarps ? redq[lane] : 0.0);
+                if (lane == 0) atomicAdd(q, xq);
+            }
+            if (lane == 0) {
+                atomicAdd(acc + 0, x1);
+                atomicAdd(acc + 1, x2);
+            }
+        }
+    }
+    if (warp == nwarps - 1) {
+        const unsigned int xn = __reduce_add_sync(0xFFFFFFFFu, lane < nwarps ? rednf[lane] : 0u);
+        if (lane == 0 && xn) atomicAdd(n_nonfinite, static_cast<unsigned long long>(xn));
     }
     // One thread per cell sums the cell's HP copies, reading them from copy
     // c mod HP on so that the lanes of a warp touch distinct banks.
-    // Fixed-point copies (and the fine cell) are summed exactly as integers
-    // and scaled once; floating-point copies pairwise.
-    const bool fixed = hs > 0.f;
-    const double inv_hs = fixed ? 1.0 / static_cast<double>(hs) : 0.0;
-    for (int c = threadIdx.x; c < bs.cells; c += blockDim.x) {
+    // Fixed-point copies and the fine cell are summed exactly as one integer
+    // (the coarse cells count units of 1/hs, the fine cell units of 2^-16/hs;
+    // below 2^53 + 2^32) and scaled once; floating-point copies pairwise.
+    const double inv_fine = inv_s[1];
+    for (int c = tid; c < bs.cells; c += nthr) {
         double h;
         if (MODE != ACC_F64 && fixed) {
             const unsigned int *hu = reinterpret_cast<const unsigned int *>(bs.hist) + c * HP;
-            unsigned long long q = 0;
+            unsigned long long qs = 0;
 #pragma unroll
-            for (int k = 0; k < HP; ++k) q += hu[(k + c) & (HP - 1)];
-            h = static_cast<double>(q) * inv_hs + static_cast<double>(bs.fine[c]) * (inv_hs * kFineInv);
+            for (int k = 0; k < HP; ++k) qs += hu[(k + c) & (HP - 1)];
+            h = static_cast<double>((qs << kFineShift) + bs.fine[c]) * inv_fine;
         } else {
             // pairwise: the rounding of a tree of log2(HP) levels
             const H *hc = bs.hist + c * HP;
@@ -551,11 +593,22 @@ __device__ __forceinline__ void flush_block(const BlockState<MODE, PRIV> &bs, Th
     __syncthreads();
 }
 
+// The iteration's scalars every thread needs, the v-rescaled Jacobian factor
+// and N^4, formed by thread 0 (FP64 arithmetic issues at 1.68 lanes per clock
+// per SM here): scal[0..1] after the caller's next barrier.
+template <class T> __device__ __forceinline__ void block_scalars(const SampleArgs &a, T *scal) {
+    if (threadIdx.x == 0) {
+        scal[0] = static_cast<T>(a.jinit * (a.jmul ? *a.jmul : 1.0));
+        scal[1] = static_cast<T>(a.nblk4);
+    }
+}
+
 // One integral, samples [a.s_begin, a.s_begin + a.n): each block takes a
 // contiguous range of them.
 template <int FAM, int MODE, int MAXD, bool EXACT, bool PRIV>
 __global__ void __launch_bounds__(512)
 vegas_sample_kernel(const SampleArgs a) {
+    pdl_begin();
     using BS = BlockState<MODE, PRIV>;
     using T = typename BS::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -570,11 +623,13 @@ vegas_sample_kernel(const SampleArgs a) {
     rp.key0 = a.key0;
     rp.key1 = a.key1;
     rp.iter = a.iter;
-    rp.jinit = static_cast<T>(a.jinit * (a.jmul ? *a.jmul : 1.0));
-    rp.n4 = static_cast<T>(a.nblk4);
+    __shared__ T scal[2];
+    block_scalars(a, scal);
     rp.hs = (MODE != ACC_F64) ? *a.hscale : 0.f;
     rp.acc = a.acc;
     __syncthreads();
+    rp.jinit = scal[0];
+    rp.n4 = scal[1];
 
     const long long per = (a.n + gridDim.x - 1) / gridDim.x;
     const long long lo = static_cast<long long>(blockIdx.x) * per;
@@ -584,7 +639,7 @@ vegas_sample_kernel(const SampleArgs a) {
         sample_range<FAM, MODE, MAXD, EXACT, PRIV>(bs, rp, consts<T>(a), ts,
                                                    static_cast<unsigned long long>(a.s_begin + lo),
                                                    static_cast<int>(hi - lo));
-    flush_block<MODE, PRIV>(bs, ts, rp.hs, a.acc, a.n_nonfinite);
+    flush_block<MODE, PRIV>(bs, ts, rp.hs, a.acc, a.n_nonfinite, nullptr, true);
 }
 
 }  // namespace vegas

@@ -127,6 +127,7 @@ __device__ __forceinline__ void sample_range_strat(const BlockState<MODE, PRIV> 
 template <int FAM, int MODE, int MAXD, bool EXACT, bool PRIV>
 __global__ void __launch_bounds__(512, MAXD > 8 ? 1 : 2)
 vegas_sample_strat_kernel(const SampleArgs a) {
+    pdl_begin();
     using BS = BlockState<MODE, PRIV>;
     using T = typename BS::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -141,11 +142,13 @@ vegas_sample_strat_kernel(const SampleArgs a) {
     rp.key0 = a.key0;
     rp.key1 = a.key1;
     rp.iter = a.iter;
-    rp.jinit = static_cast<T>(a.jinit * (a.jmul ? *a.jmul : 1.0));
-    rp.n4 = static_cast<T>(a.nblk4);
+    __shared__ T scal[2];
+    block_scalars(a, scal);
     rp.hs = (MODE != ACC_F64) ? *a.hscale : 0.f;
     rp.acc = a.acc;
     __syncthreads();
+    rp.jinit = scal[0];
+    rp.n4 = scal[1];
 
     const long long per = (a.n + gridDim.x - 1) / gridDim.x;
     const long long lo = static_cast<long long>(blockIdx.x) * per;
@@ -155,7 +158,7 @@ vegas_sample_strat_kernel(const SampleArgs a) {
         sample_range_strat<FAM, MODE, MAXD, EXACT, PRIV>(bs, rp, consts<T>(a), a.st, ts,
                                                          static_cast<uint32_t>(a.s_begin + lo),
                                                          static_cast<int>(hi - lo));
-    flush_block<MODE, PRIV>(bs, ts, rp.hs, a.acc, a.n_nonfinite, a.st.q);
+    flush_block<MODE, PRIV>(bs, ts, rp.hs, a.acc, a.n_nonfinite, a.st.q, true);
 }
 
 }  // namespace vegas

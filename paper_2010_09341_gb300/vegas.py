@@ -126,6 +126,16 @@ def vegas_step(ctx: Context, sync: bool = True):
     return r.I, r.sigma, r.n, r.n_nonfinite
 
 
+MAX_STEP_MANY = 8
+
+
+def vegas_step_many(ctxs) -> None:
+    """One vegas_step of each context (distinct, on one stream), with all their
+    iteration results and refinements in one launch (asynchronous)."""
+    arr = (nat._P * len(ctxs))(*[c.handle for c in ctxs])
+    check(nat.load().vegas_step_many(arr, len(ctxs)), "vegas_step_many")
+
+
 def vegas_sample_shard(ctx: Context, s_begin: int, count: int) -> None:
     check(nat.load().vegas_sample_shard(ctx.handle, int(s_begin), int(count)), "vegas_sample_shard")
 
