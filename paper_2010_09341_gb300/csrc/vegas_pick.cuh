@@ -10,70 +10,85 @@ namespace vegas {
 
 template <int MODE, int FAM, int MAXD, bool EXACT>
 static const void *pick_priv(bool priv) {
-    if (EXACT) return reinterpret_cast<const void *>(&vegas_sample_kernel<FAM, MODE, MAXD, true, true>);
-    return priv ? reinterpret_cast<const void *>(&vegas_sample_kernel<FAM, MODE, MAXD, false, true>)
-                : reinterpret_cast<const void *>(&vegas_sample_kernel<FAM, MODE, MAXD, false, false>);
+    if constexpr (EXACT) {
+        return reinterpret_cast<const void *>(&vegas_sample_kernel<FAM, MODE, MAXD, true, true>);
+    } else {
+        return priv ? reinterpret_cast<const void *>(&vegas_sample_kernel<FAM, MODE, MAXD, false, true>)
+                    : reinterpret_cast<const void *>(&vegas_sample_kernel<FAM, MODE, MAXD, false, false>);
+    }
 }
 
 // Exact-dimension kernels (no per-dimension guards) for d <= 8 with the
-// lane-private layout; generic kernels with a run-time d otherwise.
+// lane-private layout; generic kernels with a run-time d otherwise.  Only the
+// kernels a branch can return are instantiated (constexpr branches).
 template <int MODE, int FAM>
 static const void *pick_family(int d, bool priv) {
     constexpr bool kExact = MODE != ACC_F64;  // the FP64 path is FP64-pipe bound either way
-    if (FAM == F_LO || FAM == F_LO_PDF) {
+    if constexpr (FAM == F_LO || FAM == F_LO_PDF) {
         if (d != 3) return nullptr;
-        return (kExact && priv) ? pick_priv<MODE, FAM, 3, true>(true) : pick_priv<MODE, FAM, 4, false>(priv);
-    }
-    if (kExact && priv) {
-        switch (d) {
-        case 1: return pick_priv<MODE, FAM, 1, true>(true);
-        case 2: return pick_priv<MODE, FAM, 2, true>(true);
-        case 3: return pick_priv<MODE, FAM, 3, true>(true);
-        case 4: return pick_priv<MODE, FAM, 4, true>(true);
-        case 5: return pick_priv<MODE, FAM, 5, true>(true);
-        case 6: return pick_priv<MODE, FAM, 6, true>(true);
-        case 7: return pick_priv<MODE, FAM, 7, true>(true);
-        case 8: return pick_priv<MODE, FAM, 8, true>(true);
-        default: break;
+        if constexpr (kExact) {
+            if (priv) return pick_priv<MODE, FAM, 3, true>(true);
         }
+        return pick_priv<MODE, FAM, 4, false>(priv);
+    } else {
+        if constexpr (kExact) {
+            if (priv) switch (d) {
+            case 1: return pick_priv<MODE, FAM, 1, true>(true);
+            case 2: return pick_priv<MODE, FAM, 2, true>(true);
+            case 3: return pick_priv<MODE, FAM, 3, true>(true);
+            case 4: return pick_priv<MODE, FAM, 4, true>(true);
+            case 5: return pick_priv<MODE, FAM, 5, true>(true);
+            case 6: return pick_priv<MODE, FAM, 6, true>(true);
+            case 7: return pick_priv<MODE, FAM, 7, true>(true);
+            case 8: return pick_priv<MODE, FAM, 8, true>(true);
+            default: break;
+            }
+        }
+        if (d <= 8) return pick_priv<MODE, FAM, 8, false>(priv);
+        if (d <= 16) return pick_priv<MODE, FAM, 16, false>(priv);
+        return pick_priv<MODE, FAM, 32, false>(priv);
     }
-    if (d <= 8) return pick_priv<MODE, FAM, 8, false>(priv);
-    if (d <= 16) return pick_priv<MODE, FAM, 16, false>(priv);
-    return pick_priv<MODE, FAM, 32, false>(priv);
 }
 
 // Stratified kernels: as above, exact-dimension kernels for d <= 8 in the
 // FP32 modes with the lane-private layout, generic tiers otherwise.
 template <int MODE, int FAM, int MAXD, bool EXACT>
 static const void *pick_strat_priv(bool priv) {
-    if (EXACT) return reinterpret_cast<const void *>(&vegas_sample_strat_kernel<FAM, MODE, MAXD, true, true>);
-    return priv ? reinterpret_cast<const void *>(&vegas_sample_strat_kernel<FAM, MODE, MAXD, false, true>)
-                : reinterpret_cast<const void *>(&vegas_sample_strat_kernel<FAM, MODE, MAXD, false, false>);
+    if constexpr (EXACT) {
+        return reinterpret_cast<const void *>(&vegas_sample_strat_kernel<FAM, MODE, MAXD, true, true>);
+    } else {
+        return priv ? reinterpret_cast<const void *>(&vegas_sample_strat_kernel<FAM, MODE, MAXD, false, true>)
+                    : reinterpret_cast<const void *>(&vegas_sample_strat_kernel<FAM, MODE, MAXD, false, false>);
+    }
 }
 
 template <int MODE, int FAM>
 static const void *pick_strat(int d, bool priv) {
     constexpr bool kExact = MODE != ACC_F64;
-    if (FAM == F_LO || FAM == F_LO_PDF) {
+    if constexpr (FAM == F_LO || FAM == F_LO_PDF) {
         if (d != 3) return nullptr;
-        return (kExact && priv) ? pick_strat_priv<MODE, FAM, 3, true>(true) : pick_strat_priv<MODE, FAM, 4, false>(priv);
-    }
-    if (kExact && priv) {
-        switch (d) {
-        case 1: return pick_strat_priv<MODE, FAM, 1, true>(true);
-        case 2: return pick_strat_priv<MODE, FAM, 2, true>(true);
-        case 3: return pick_strat_priv<MODE, FAM, 3, true>(true);
-        case 4: return pick_strat_priv<MODE, FAM, 4, true>(true);
-        case 5: return pick_strat_priv<MODE, FAM, 5, true>(true);
-        case 6: return pick_strat_priv<MODE, FAM, 6, true>(true);
-        case 7: return pick_strat_priv<MODE, FAM, 7, true>(true);
-        case 8: return pick_strat_priv<MODE, FAM, 8, true>(true);
-        default: break;
+        if constexpr (kExact) {
+            if (priv) return pick_strat_priv<MODE, FAM, 3, true>(true);
         }
+        return pick_strat_priv<MODE, FAM, 4, false>(priv);
+    } else {
+        if constexpr (kExact) {
+            if (priv) switch (d) {
+            case 1: return pick_strat_priv<MODE, FAM, 1, true>(true);
+            case 2: return pick_strat_priv<MODE, FAM, 2, true>(true);
+            case 3: return pick_strat_priv<MODE, FAM, 3, true>(true);
+            case 4: return pick_strat_priv<MODE, FAM, 4, true>(true);
+            case 5: return pick_strat_priv<MODE, FAM, 5, true>(true);
+            case 6: return pick_strat_priv<MODE, FAM, 6, true>(true);
+            case 7: return pick_strat_priv<MODE, FAM, 7, true>(true);
+            case 8: return pick_strat_priv<MODE, FAM, 8, true>(true);
+            default: break;
+            }
+        }
+        if (d <= 8) return pick_strat_priv<MODE, FAM, 8, false>(priv);
+        if (d <= 16) return pick_strat_priv<MODE, FAM, 16, false>(priv);
+        return pick_strat_priv<MODE, FAM, 32, false>(priv);
     }
-    if (d <= 8) return pick_strat_priv<MODE, FAM, 8, false>(priv);
-    if (d <= 16) return pick_strat_priv<MODE, FAM, 16, false>(priv);
-    return pick_strat_priv<MODE, FAM, 32, false>(priv);
 }
 
 }  // namespace vegas

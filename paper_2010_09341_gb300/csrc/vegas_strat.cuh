@@ -24,11 +24,11 @@ namespace vegas {
 // partial sums of v, v^2 (FP32_SUM64) and m2 are kept in FP32 and added in
 // FP64 once a thread has taken kChunk samples since the last addition.
 template <int FAM, int MODE, int MAXD, bool EXACT, int PRIV>
-__device__ __forceinline__ void sample_range_strat(const BlockState<MODE, PRIV> &bs,
-                                                   const RangeParams<typename ModeTraits<MODE>::T> &rp,
-                                                   const FamConsts<typename ModeTraits<MODE>::T> &fc,
-                                                   const StratArgs &st, ThreadSums<MODE> &ts, uint32_t h0,
-                                                   int cnt) {
+__device__ __forceinline__ void sample_range_strat_any(const BlockState<MODE, PRIV> &bs,
+                                                       const RangeParams<typename ModeTraits<MODE>::T> &rp,
+                                                       const FamConsts<typename ModeTraits<MODE>::T> &fc,
+                                                       const StratArgs &st, ThreadSums<MODE> &ts, uint32_t h0,
+                                                       int cnt) {
     using BS = BlockState<MODE, PRIV>;
     using T = typename BS::T;
     using T2 = typename BS::T2;
@@ -118,6 +118,131 @@ __device__ __forceinline__ void sample_range_strat(const BlockState<MODE, PRIV> 
         if (MODE == ACC_F64 || since >= kChunk) flush_partials();
     }
     flush_partials();
+}
+
+// The same for P <= kChunk in the exact-dimension kernels, with the FP64
+// additions of the FP32 partials at the end of each group of ceil(kChunk / P)
+// hypercubes (the same points as above), not behind a test inside the loop:
+// the compiler predicates a short conditional block, and a predicated-off FP64
+// instruction still holds the FP64 unit for its ~76 cycles on this GPU.
+template <int FAM, int MODE, int MAXD, bool EXACT, int PRIV>
+__device__ __forceinline__ void sample_range_strat_grouped(const BlockState<MODE, PRIV> &bs,
+                                                     const RangeParams<typename ModeTraits<MODE>::T> &rp,
+                                                     const FamConsts<typename ModeTraits<MODE>::T> &fc,
+                                                     const StratArgs &st, ThreadSums<MODE> &ts, uint32_t h0,
+                                                     int cnt) {
+    using BS = BlockState<MODE, PRIV>;
+    using T = typename BS::T;
+    using T2 = typename BS::T2;
+    using H = typename BS::H;
+    constexpr int TP = BS::TP;
+    constexpr int HP = BS::HP;
+    const int lane = threadIdx.x & 31;
+    const T2 *tab_l = bs.tab + (lane % TP);
+    H *hist_l = bs.hist + (lane % HP);
+    const float hs = rp.hs;
+    const bool fixed = hs > 0.f;
+    const uint32_t P = st.P;
+    const T invP = T(1) / static_cast<T>(P);
+    constexpr uint32_t kChunk = 8;
+    // generic tiers: two samples' cells in 16-bit halves (d N <= 32768), which
+    // keeps them in registers; the exact-dimension kernels have room for both
+    constexpr bool kPack = !EXACT;
+    float p1 = 0.f, p2 = 0.f;   // FP32_SUM64 partial sums of v, v^2
+    T qt = T(0);                // partial sum of m2 (FP32 modes)
+    auto add_vv = [&]() {       // the FP32 partials of v, v^2 into FP64
+        if (MODE == ACC_F32_SUM64) {
+            ts.s1d += static_cast<double>(p1);
+            ts.s2d += static_cast<double>(p2);
+            p1 = 0.f;
+            p2 = 0.f;
+        }
+    };
+    auto add_q = [&]() {
+        ts.qd += static_cast<double>(qt);
+        qt = T(0);
+    };
+    auto add_sums = [&](T v, T v2) {
+        if (MODE == ACC_F32_KAHAN) {
+            kahan_add(ts, static_cast<float>(v), static_cast<float>(v2));
+        } else if (MODE == ACC_F32_SUM64) {
+            p1 += static_cast<float>(v);
+            p2 += static_cast<float>(v2);
+        } else {
+            const double vd = static_cast<double>(v);
+            ts.s1d += vd;
+            ts.s2d = __fma_rn(vd, vd, ts.s2d);
+        }
+    };
+    // samples [pb, pe) of hypercube h (first sample index sb), into A, B
+    auto run = [&](uint32_t h, unsigned long long sb, uint32_t pb, uint32_t pe, T &c, T &a, T &b) {
+        uint32_t p = pb;
+        for (; p + 1 < pe; p += 2) {
+            SampleCells<MAXD, kPack> ca, cb;
+            const T va = map_sample<FAM, MODE, MAXD, EXACT, PRIV, kPack, true>(tab_l, rp, fc, &st, h, sb + p, ca,
+                                                                               ts.nonfinite);
+            const T vb = map_sample<FAM, MODE, MAXD, EXACT, PRIV, kPack, true>(tab_l, rp, fc, &st, h, sb + p + 1,
+                                                                               cb, ts.nonfinite);
+            const T va2 = va * va, vb2 = vb * vb;
+            add_sums(va, va2);
+            add_sums(vb, vb2);
+            if (p == 0) c = va;
+            const T da = va - c, db = vb - c;
+            a += da + db;
+            b = ffma(da, da, ffma(db, db, b));
+            hist_add<MODE, PRIV, MAXD, EXACT, kPack>(bs, hist_l, rp, ca, va2, fixed, hs);
+            hist_add<MODE, PRIV, MAXD, EXACT, kPack>(bs, hist_l, rp, cb, vb2, fixed, hs);
+        }
+        if (p < pe) {
+            SampleCells<MAXD, kPack> ca;
+            const T va = map_sample<FAM, MODE, MAXD, EXACT, PRIV, kPack, true>(tab_l, rp, fc, &st, h, sb + p, ca,
+                                                                               ts.nonfinite);
+            const T va2 = va * va;
+            add_sums(va, va2);
+            if (p == 0) c = va;
+            const T da = va - c;
+            a += da;
+            b = ffma(da, da, b);
+            hist_add<MODE, PRIV, MAXD, EXACT, kPack>(bs, hist_l, rp, ca, va2, fixed, hs);
+        }
+    };
+    auto finish = [&](T a, T b) {
+        const T m2 = b - a * a * invP;
+        qt += m2 > T(0) ? m2 : T(0);
+    };
+    // P <= kChunk: the FP32 partials go into FP64 after each group of
+    // ceil(kChunk / P) hypercubes (one hypercube in the FP64 mode)
+    const int G = MODE == ACC_F64 ? 1 : static_cast<int>((kChunk + P - 1) / P);
+    const int step = blockDim.x;
+    for (int k0 = threadIdx.x; k0 < cnt; k0 += G * step) {
+        const int kend = min(cnt, k0 + G * step);
+        for (int k = k0; k < kend; k += step) {
+            const uint32_t h = h0 + static_cast<uint32_t>(k);
+            const unsigned long long sb = static_cast<unsigned long long>(h) * P;
+            T c = T(0), a = T(0), b = T(0);
+            run(h, sb, 0u, P, c, a, b);
+            finish(a, b);
+        }
+        add_vv();
+        add_q();
+    }
+}
+
+template <int FAM, int MODE, int MAXD, bool EXACT, int PRIV>
+__device__ __forceinline__ void sample_range_strat(const BlockState<MODE, PRIV> &bs,
+                                                   const RangeParams<typename ModeTraits<MODE>::T> &rp,
+                                                   const FamConsts<typename ModeTraits<MODE>::T> &fc,
+                                                   const StratArgs &st, ThreadSums<MODE> &ts, uint32_t h0,
+                                                   int cnt) {
+    // the generic tiers keep one copy of the sample loop (a second one would
+    // push the 32-dimension tier past its 128 registers)
+    if constexpr (EXACT) {
+        if (st.P <= 8u) {
+            sample_range_strat_grouped<FAM, MODE, MAXD, EXACT, PRIV>(bs, rp, fc, st, ts, h0, cnt);
+            return;
+        }
+    }
+    sample_range_strat_any<FAM, MODE, MAXD, EXACT, PRIV>(bs, rp, fc, st, ts, h0, cnt);
 }
 
 // Stratified form: hypercubes [a.s_begin, a.s_begin + a.n) of P = a.st.P
