@@ -65,3 +65,19 @@ def test_workspace_bytes_validates_config(lib):
 def test_strerror(lib):
     assert lib.vegas_strerror(0) == b"ok"
     assert b"invalid" in lib.vegas_strerror(1)
+
+
+def test_step_many_rejects_bad_arguments_before_any_launch(lib):
+    """vegas_step_many validates on the host: a NULL array, a count out of
+    [1, VEGAS_MAX_STEP_MANY] and NULL contexts return VEGAS_EINVAL (no device
+    call is reached, so this runs without a GPU)."""
+    import ctypes
+    from paper_2010_09341_gb300 import _native as nat
+    P = ctypes.c_void_p
+    assert lib.vegas_step_many(None, 1) == nat.VEGAS_EINVAL
+    two = (P * 2)(None, None)
+    assert lib.vegas_step_many(two, 2) == nat.VEGAS_EINVAL
+    nine = (P * 9)()
+    assert lib.vegas_step_many(nine, 9) == nat.VEGAS_EINVAL
+    assert lib.vegas_step_many(two, 0) == nat.VEGAS_EINVAL
+    assert lib.vegas_step_many(two, -1) == nat.VEGAS_EINVAL
