@@ -212,14 +212,16 @@ vegas_status vegas_finalize(vegas_ctx *ctx, vegas_iter_result *out);
  * but the last).  Same results as the two calls. */
 vegas_status vegas_step(vegas_ctx *ctx, vegas_iter_result *out);
 
-/* One vegas_step (sampling, iteration result, refinement; Sec. 2 and 3) of
+/* One vegas_step (sampling, iteration result and refinement: the iteration of
+ * Sec. 1, whose result informs the next grid, Sec. 3.2) of
  * each of n independent integrals, 1 <= n <= VEGAS_MAX_STEP_MANY: their
  * sampling launches in the given order, then ONE launch for all n iteration
  * results and refinements (d_k + 1 blocks for context k), so that a set of
  * integrals advanced together pays one small launch per iteration, not n.
  * ctxs: n distinct contexts (host array, read during the call) that share one
  * stream.  Asynchronous: read the results with vegas_result / vegas_run's
- * records.  Each context's results equal those of vegas_step on it.
+ * records.  Each context's results are those of vegas_step on it, up to the
+ * order of the FP64 atomic additions of its block sums (which no launch fixes).
  * Errors: VEGAS_EINVAL for a NULL array or context, n out of range, a context
  * given twice, contexts on different streams, or a density-grid context
  * without its grid (nothing is launched then); a launch error as vegas_step. */
