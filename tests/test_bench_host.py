@@ -1,0 +1,62 @@
+"""CPU checks of bench.py's host-side arithmetic: the counted operations and
+the issue roofline of the sampling kernel, and the profile-hash gate of
+`roofline.traffic`.  No GPU.
+"""
+import os
+import shutil
+
+import pytest
+
+import bench
+
+
+def test_counted_operations_of_the_headline_integrals():
+    """The counts the roofline is built on, at d = 8 with FP32 sampling and FP64
+    sums: 196.5 (Gaussian) and 192.5 (oscillatory) operations, of which 48 are
+    32x32->64 multiplies (2 Philox calls x 20, plus one per dimension)."""
+    g = bench.ops_per_sample("gauss_sym", 8, "fp32_acc64")
+    o = bench.ops_per_sample("genz_osc", 8, "fp32_acc64")
+    assert g["total"] == 196.5 and o["total"] == 192.5
+    assert g["mulwide"] == o["mulwide"] == 48
+    assert g["fp64"] == 0.5
+    # one more Philox call per 4 dimensions, 10 + per-dimension integrand ops per dimension
+    g9 = bench.ops_per_sample("gauss_sym", 9, "fp32_acc64")
+    assert g9["mulwide"] == 60 + 9
+    assert g9["total"] - g["total"] == 40 + (10 + 2)
+
+
+def test_issue_roofline_at_152_sms_and_2070_mhz():
+    """(196.5 - 48) + 4 x 48 = 340.5 issue cycles per sample: 152 x 2.07e9 x 128 / 340.5
+    = 118.28 G samples/s; the FP64 and MUFU bounds are far above it."""
+    b = bench.roofline_samples_per_s(bench.ops_per_sample("gauss_sym", 8, "fp32_acc64"), 152, 2.07e9)
+    assert b["issue"] == pytest.approx(152 * 2.07e9 * 128 / 340.5, rel=1e-12)
+    assert b["issue"] == pytest.approx(118.28e9, rel=1e-4)
+    assert min(b, key=b.get) == "issue"
+    assert b["fp64"] > 10 * b["issue"] and b["mufu"] > 10 * b["issue"]
+
+
+def _copy_tree(tmp_path):
+    root = tmp_path / "repo"
+    (root / "profiles").mkdir(parents=True)
+    src = root / "paper_2010_09341_gb300" / "csrc"
+    src.mkdir(parents=True)
+    shutil.copy(os.path.join(bench.ROOT, "profiles", "sample_kernel_d8_gauss.md"), root / "profiles")
+    for f in ("vegas_device.cuh", "vegas_sample.cuh"):
+        shutil.copy(os.path.join(bench.ROOT, "paper_2010_09341_gb300", "csrc", f), src / f)
+    return root, src
+
+
+def test_traffic_is_reported_only_for_the_profiled_sources(tmp_path, monkeypatch):
+    """roofline.traffic comes from the committed ncu summary only while the
+    kernel sources hash to the profiled ones; any edit of them turns it to null."""
+    root, src = _copy_tree(tmp_path)
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    first = bench._traffic_from_profile()
+    if first is None:
+        pytest.skip("the committed sources differ from the profiled ones")
+    assert first > 0
+    with open(src / "vegas_sample.cuh", "a") as f:
+        f.write("\n// edited\n")
+    assert bench._traffic_from_profile() is None
+    os.remove(root / "profiles" / "sample_kernel_d8_gauss.md")
+    assert bench._traffic_from_profile() is None
