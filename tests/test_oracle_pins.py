@@ -367,3 +367,23 @@ def test_oracle_reproduces_golden_fixture_bitwise():
     assert [[float(I).hex(), float(s).hex()] for I, s in r["iters"]] == g["iters"]
     assert float(r["I"]).hex() == g["I"] and float(r["sigma"]).hex() == g["sigma"]
     assert hashlib.sha256(r["edges"].astype("<f8").tobytes()).hexdigest() == g["edges_sha256"]
+
+
+def test_oracle_reproduces_path_fixtures_bitwise():
+    """tests/golden/paths_oracle.json (tests/golden/make_golden.py, oracle only):
+    the stratified run, the LO toy on a density grid and an observable
+    histogram reproduce exactly on this machine, so that any change of the
+    oracle's arithmetic on those paths shows."""
+    import json
+    import os
+    import sys
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    sys.path.insert(0, here)
+    try:
+        import make_golden as MG
+    finally:
+        sys.path.remove(here)
+    g = json.load(open(os.path.join(here, "paths_oracle.json")))
+    r = MG.paths()
+    for key in ("strat", "lo_pdf", "histogram"):
+        assert r[key] == g[key], key
