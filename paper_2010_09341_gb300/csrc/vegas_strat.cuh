@@ -124,7 +124,7 @@ __device__ __forceinline__ void sample_range_strat_any(const BlockState<MODE, PR
 // additions of the FP32 partials at the end of each group of ceil(kChunk / P)
 // hypercubes (the same points as above), not behind a test inside the loop:
 // the compiler predicates a short conditional block, and a predicated-off FP64
-// instruction still holds the FP64 unit for its ~76 cycles on this GPU.
+// instruction still holds the FP64 unit for its ~76 cycles on GB300.
 template <int FAM, int MODE, int MAXD, bool EXACT, int PRIV>
 __device__ __forceinline__ void sample_range_strat_grouped(const BlockState<MODE, PRIV> &bs,
                                                      const RangeParams<typename ModeTraits<MODE>::T> &rp,
