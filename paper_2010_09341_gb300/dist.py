@@ -10,7 +10,8 @@ grid is refined (Sec. 3.1, Sec. 3.2).  The union of the shards is exactly the
 single-device iteration.
 
 The orchestration here works on any object with the shard interface
-(``sample_shard``, ``accumulators``, ``finalize``, ``refine``);
+(``sample_shard``, ``accumulators``, ``finalize``, ``refine``, and optionally
+``exchange_begin`` / ``exchange_end``, called around the collective);
 :class:`GpuShard` adapts a C-ABI context.  Independent integrals need no
 exchange: they run as replicas (one set per rank).
 """
@@ -45,6 +46,16 @@ class GpuShard:
     def accumulators(self):
         return self.V.vegas_accumulators(self.ctx)
 
+    def exchange_begin(self) -> None:
+        # The accumulators are written on the context's stream, which need not
+        # be the stream the collective orders itself after.
+        self.ctx.stream.synchronize()
+
+    def exchange_end(self) -> None:
+        # The collective wrote the summed accumulators in the order of the
+        # current stream; finalize reads them on the context's stream.
+        self.ctx.stream.wait_stream(torch.cuda.current_stream(self.ctx.stream.device))
+
     def finalize(self):
         return self.V.vegas_finalize(self.ctx, sync=True)
 
@@ -60,10 +71,14 @@ def sharded_iterate(shard, group=None):
     s0, count = shard_range(shard.n_events, rank, world)
     shard.sample_shard(s0, count)
     sums, nonfinite = shard.accumulators()
-    if sums.is_cuda:
-        torch.cuda.current_stream().synchronize()
+    begin = getattr(shard, "exchange_begin", None)
+    if begin is not None:
+        begin()
     dist.all_reduce(sums, op=dist.ReduceOp.SUM, group=group)
     dist.all_reduce(nonfinite, op=dist.ReduceOp.SUM, group=group)
+    end = getattr(shard, "exchange_end", None)
+    if end is not None:
+        end()
     return shard.finalize()
 
 

@@ -29,8 +29,10 @@ class OracleShard:
         self.t = 0
         self.sums = torch.zeros(2 + d * N, dtype=torch.float64)
         self.nonfinite = torch.zeros(1, dtype=torch.int64)
+        self.log = []
 
     def sample_shard(self, s0, count):
+        self.log.append("sample")
         acc = O.iterate(self.d, self.N, self.edges, self.family, self.params, self.seed, self.iid,
                         self.t, self.n_events, s_begin=s0, s_end=s0 + count)
         self.sums.zero_()
@@ -42,7 +44,16 @@ class OracleShard:
     def accumulators(self):
         return self.sums, self.nonfinite
 
+    def exchange_begin(self):
+        self.log.append("begin")
+        self.pre = float(self.sums[0])
+
+    def exchange_end(self):
+        # the collective has summed the accumulators by now
+        self.log.append("end" if float(self.sums[0]) != self.pre else "end-unsummed")
+
     def finalize(self):
+        self.log.append("finalize")
         ne = self.n_events - int(self.nonfinite[0])
         I, var = O.iteration_result(float(self.sums[0]), float(self.sums[1]), ne)
         self.t += 1
@@ -69,7 +80,7 @@ def _worker(rank, world, port, q):
         sh = OracleShard("genz_gauss", d, N, n, p, seed=3, iid=5)
         its = D.sharded_run(sh, 3)
         slow = D.max_over_ranks(1.0 + rank)
-        q.put((rank, its, sh.edges, slow))
+        q.put((rank, its, sh.edges, slow, sh.log))
     finally:
         dist.destroy_process_group()
 
@@ -90,8 +101,10 @@ def test_sharded_run_equals_single_rank():
     d, N, n = 4, 20, 20_003
     p = W.genz_params("genz_gauss", d, seed=9)
     ref = O.integrate(d, N, "genz_gauss", p, n, 3, seed=3, integral_id=5)
-    for rank, its, edges, slow in out:
+    for rank, its, edges, slow, log in out:
         assert slow == 2.0  # the slowest rank's value on every rank
+        # the exchange hooks bracket the collective of every iteration
+        assert log == ["sample", "begin", "end", "finalize"] * 3
         for (I, s, ne, nf), (Io, so) in zip(its, ref["iters"]):
             assert abs(I - Io) <= 1e-12 * abs(Io)
             assert abs(s - so) <= 1e-9 * so
