@@ -21,7 +21,8 @@ constexpr int kThreads = 1024;
 
 enum Kind : int {
     K_FFMA, K_IADD, K_LOP3, K_IMAD, K_MULHI, K_MULWIDE_XOR, K_MULWIDE_XOR_2FFMA, K_FFMA_LOP3,
-    K_ATOMS_U32, K_ATOMS_F32, K_ATOMS_F64, K_DFMA, K_EX2, K_EXP64, K_COUNT
+    K_ATOMS_U32, K_ATOMS_F32, K_ATOMS_F64, K_DFMA, K_EX2, K_EXP64, K_I2F, K_I2F_2FFMA, K_SHF,
+    K_ATOMS_U64, K_MATCH_ANY, K_COUNT
 };
 
 template <int V>
@@ -29,18 +30,22 @@ __global__ void __launch_bounds__(kThreads) chains(unsigned long long *cycles, u
     __shared__ unsigned cells_u[32 * 8];
     __shared__ float cells_f[32 * 8];
     __shared__ double cells_d[32 * 8];
+    __shared__ unsigned long long cells_q[32 * 8];
     const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
     const unsigned lane = threadIdx.x & 31;
     if (threadIdx.x < 32 * 8) {
         cells_u[threadIdx.x] = 0u;
         cells_f[threadIdx.x] = 0.f;
         cells_d[threadIdx.x] = 0.0;
+        cells_q[threadIdx.x] = 0ull;
     }
     unsigned x[8];
     float f[8];
     double g[8];
+    float g2f[8];
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
+        g2f[c] = 1.0f + c * 1e-4f;
         x[c] = t * 2654435761u + c * 977u + seed;
         f[c] = 1.0f + (t & 7) * 1e-3f + c * 1e-4f;
         g[c] = 1.0 + c * 1e-4;
@@ -85,6 +90,21 @@ __global__ void __launch_bounds__(kThreads) chains(unsigned long long *cycles, u
                 asm volatile("fma.rn.f64 %0, %0, 0d3FEFFFFFDE7210BE, 0d3E7AD7F29ABCAF48;" : "+d"(g[c]));
             } else if (V == K_EX2) {
                 asm volatile("ex2.approx.ftz.f32 %0, %0;" : "+f"(f[c]));
+            } else if (V == K_I2F || V == K_I2F_2FFMA) {
+                // the float's own bits converted as an unsigned integer: a chain of conversions
+                asm volatile("{ .reg .u32 b; mov.b32 b, %0; cvt.rn.f32.u32 %0, b; }" : "+f"(f[c]));
+                if (V == K_I2F_2FFMA) {
+                    asm volatile("fma.rn.f32 %0, %0, 0f3F7FFFEF, 0f33D6BF95;" : "+f"(g2f[c]));
+                    asm volatile("fma.rn.f32 %0, %0, 0f3F7FFFEF, 0f33D6BF95;" : "+f"(g2f[c]));
+                }
+            } else if (V == K_SHF) {
+                asm volatile("shf.r.clamp.b32 %0, %0, 0x7F, 9;" : "+r"(x[c]));
+            } else if (V == K_ATOMS_U64) {
+                atomicAdd(&cells_q[c * 32 + lane], static_cast<unsigned long long>(x[c]));
+            } else if (V == K_MATCH_ANY) {
+                unsigned m;
+                asm volatile("match.any.sync.b32 %0, %1, 0xFFFFFFFF;" : "=r"(m) : "r"(x[c]));
+                x[c] ^= m;
             }
         }
     }
@@ -92,9 +112,11 @@ __global__ void __launch_bounds__(kThreads) chains(unsigned long long *cycles, u
     __syncthreads();
     unsigned r = 0;
 #pragma unroll
-    for (int c = 0; c < 8; ++c) r += x[c] + __float_as_uint(f[c]) + static_cast<unsigned>(g[c] * 1e3);
+    for (int c = 0; c < 8; ++c)
+        r += x[c] + __float_as_uint(f[c]) + __float_as_uint(g2f[c]) + static_cast<unsigned>(g[c] * 1e3);
     if (threadIdx.x < 32 * 8)
-        r += cells_u[threadIdx.x] + __float_as_uint(cells_f[threadIdx.x]) + static_cast<unsigned>(cells_d[threadIdx.x]);
+        r += cells_u[threadIdx.x] + __float_as_uint(cells_f[threadIdx.x]) + static_cast<unsigned>(cells_d[threadIdx.x]) +
+             static_cast<unsigned>(cells_q[threadIdx.x]);
     sink[t] = r;
     if (threadIdx.x == 0) cycles[blockIdx.x] = c1 - c0;
 }
@@ -132,6 +154,11 @@ int main() {
         {"dfma", 1, chains<K_DFMA>},
         {"ex2.approx", 1, chains<K_EX2>},
         {"exp (double, one call)", 1, chains<K_EXP64>},
+        {"cvt.rn.f32.u32", 1, chains<K_I2F>},
+        {"cvt.rn.f32.u32 + 2 ffma", 3, chains<K_I2F_2FFMA>},
+        {"shf.r (funnel shift)", 1, chains<K_SHF>},
+        {"shared atomic add u64", 1, chains<K_ATOMS_U64>},
+        {"match.any.sync.b32", 2, chains<K_MATCH_ANY>},
     };
     unsigned long long *h = new unsigned long long[blocks];
     int rc = 0;
