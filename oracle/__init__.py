@@ -80,6 +80,8 @@ def _load():
         lib.oracle_sample.argtypes = [i32, i32, dp, i32, dp, i32, u32, u32, u32, u64,
                                       ip, dp, dp, dp]
         lib.oracle_sample.restype = None
+        lib.oracle_trace.argtypes = [i32, i32, dp, i32, dp, i32, u32, u32, u32, u64, i64, ip, dp, dp]
+        lib.oracle_trace.restype = None
         lib.oracle_iterate.argtypes = [i32, i32, dp, i32, dp, i32, u32, u32, u32, i64, i64,
                                        dp, dp, dp, lp, lp]
         lib.oracle_iterate.restype = None
@@ -177,6 +179,34 @@ def sample(d, N, edges, family, params, seed, integral_id, t, s):
                       integral_id, t, s, bins.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                       _dptr(x), ctypes.byref(J), ctypes.byref(f))
     return bins, x, J.value, f.value
+
+
+def trace(d, N, edges, family, params, seed, integral_id, t, s_begin, count, threads=1):
+    """Samples s_begin .. s_begin + count - 1: (bins[count, d] int32, x[count, d], v[count])
+    with v = J f; ``threads`` > 1 splits the range over host threads."""
+    lib = _load()
+    e = _f64(edges).reshape(d, N + 1)
+    p = _f64(params if len(params) else [0.0])
+    bins = np.zeros((count, d), dtype=np.int32)
+    x = np.zeros((count, d), dtype=np.float64)
+    v = np.zeros(count, dtype=np.float64)
+    threads = max(1, min(int(threads), max(1, count)))
+    bounds = np.linspace(0, count, threads + 1).astype(np.int64)
+
+    def run(a, b):
+        if b <= a:
+            return
+        lib.oracle_trace(d, N, _dptr(e), FAMILIES[family], _dptr(p), len(params), seed, integral_id, t,
+                         int(s_begin + a), int(b - a),
+                         bins[a:b].ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _dptr(x[a:b]),
+                         _dptr(v[a:b]))
+
+    ths = [threading.Thread(target=run, args=(int(bounds[i]), int(bounds[i + 1]))) for i in range(threads)]
+    for th in ths:
+        th.start()
+    for th in ths:
+        th.join()
+    return bins, x, v
 
 
 def iterate(d, N, edges, family, params, seed, integral_id, t, n, s_begin=0, s_end=None,

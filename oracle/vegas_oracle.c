@@ -295,6 +295,18 @@ void oracle_sample(int d, int N, const double *edges, int family, const double *
     *f = oracle_integrand(family, d, params, n_params, x);
 }
 
+
+void oracle_trace(int d, int N, const double *edges, int family, const double *params,
+                  int n_params, uint32_t seed, uint32_t integral_id, uint32_t t,
+                  uint64_t s_begin, int64_t count, int32_t *bins, double *x, double *v) {
+    for (int64_t k = 0; k < count; ++k) {
+        double J, f;
+        oracle_sample(d, N, edges, family, params, n_params, seed, integral_id, t, s_begin + (uint64_t)k,
+                      bins + (size_t)k * (size_t)d, x + (size_t)k * (size_t)d, &J, &f);
+        v[k] = J * f;
+    }
+}
+
 void oracle_iterate(int d, int N, const double *edges, int family, const double *params,
                     int n_params, uint32_t seed, uint32_t integral_id, uint32_t t,
                     int64_t s_begin, int64_t s_end, double *S1, double *S2, double *hist,

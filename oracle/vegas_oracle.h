@@ -70,6 +70,12 @@ void oracle_sample(int d, int N, const double *edges, int family, const double *
                    int n_params, uint32_t seed, uint32_t integral_id, uint32_t t,
                    uint64_t s, int32_t *bins, double *x, double *J, double *f);
 
+/* Samples s_begin .. s_begin + count - 1 of iteration t, one oracle_sample
+ * each: bins[k*d + j], x[k*d + j] and v[k] = J f. */
+void oracle_trace(int d, int N, const double *edges, int family, const double *params,
+                  int n_params, uint32_t seed, uint32_t integral_id, uint32_t t,
+                  uint64_t s_begin, int64_t count, int32_t *bins, double *x, double *v);
+
 /* Accumulate samples s in [s_begin, s_end) of iteration t into
  * *S1 += v, *S2 += v^2, hist[j*N + i_j] += v^2 (v = J f).  Non-finite v are
  * counted in *n_nonfinite and skipped.  cnt (may be NULL) gets per-bin

@@ -387,3 +387,21 @@ def test_oracle_reproduces_path_fixtures_bitwise():
     r = MG.paths()
     for key in ("strat", "lo_pdf", "histogram"):
         assert r[key] == g[key], key
+
+
+def test_trace_is_sample_by_sample_and_sums_to_iterate():
+    """oracle.trace runs oracle_sample per sample (host threads): the same
+    bins, points and weights, and its weights add up to the iteration sums."""
+    d, N = 5, 30
+    p = W.genz_params("genz_gauss", d, seed=4)
+    rng = np.random.default_rng(5)
+    inner = np.sort(rng.uniform(0, 1, size=(d, N - 1)), axis=1)
+    e = np.concatenate([np.zeros((d, 1)), inner, np.ones((d, 1))], axis=1)
+    s0, cnt = (1 << 32) - 300, 2000
+    bins, x, v = O.trace(d, N, e, "genz_gauss", p, 3, 7, 2, s0, cnt, threads=3)
+    for k in (0, 1, 299, 300, 1999):
+        ob, ox, J, f = O.sample(d, N, e, "genz_gauss", p, 3, 7, 2, s0 + k)
+        assert np.array_equal(bins[k], ob) and np.array_equal(x[k], ox) and v[k] == J * f
+    acc = O.iterate(d, N, e, "genz_gauss", p, 3, 7, 2, cnt, s_begin=s0, s_end=s0 + cnt)
+    assert abs(v.sum() - acc["S1"]) <= 1e-13 * abs(acc["S1"])
+    assert abs((v * v).sum() - acc["S2"]) <= 1e-13 * acc["S2"]
