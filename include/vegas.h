@@ -56,13 +56,20 @@ typedef enum {
 } vegas_status;
 
 /* Arithmetic of the sampling path.
- *   VEGAS_FP64       : uniforms, grid map, Jacobian, integrand and all sums in FP64.
- *   VEGAS_FP32_ACC64 : map, Jacobian and integrand in FP32; per-thread sums of
- *                      v and v^2 in FP64; histograms in FP64 shared memory.
- *   VEGAS_FP32_KAHAN : map, Jacobian and integrand in FP32; per-thread sums of
- *                      v and v^2 Kahan-compensated FP32; histograms in FP32
- *                      shared memory (bounded depth per cell) promoted to FP64
- *                      once per block.
+ *   VEGAS_FP64       : uniforms, grid map, Jacobian, integrand and all sums in
+ *                      FP64; histograms in FP64 shared-memory cells.
+ *   VEGAS_FP32_ACC64 : map, Jacobian and integrand in FP32 (the in-bin
+ *                      position is the 32-bit low word rounded to FP32, not
+ *                      truncated); per-thread FP32 partial sums of v and v^2
+ *                      over 8 samples, added into FP64.
+ *   VEGAS_FP32_KAHAN : as FP32_ACC64, with the per-thread sums of v and v^2
+ *                      Kahan-compensated FP32.
+ * Histograms in both FP32 modes: in an iteration after a settled one (its
+ * mean v^2 at most 1024 times its squared mean v), 32-bit fixed-point integer
+ * cells in shared memory, each v^2 rounded to 2^-19 of the previous
+ * iteration's mean v^2 (values below 2^-18 of it to 2^-34 of it, never to 0;
+ * values above 32 times it straight to FP64); otherwise FP32 cells.  Either
+ * is added into FP64 once per block.  The histograms drive only refinement.
  * Refinement and the combination of iterations are FP64 in every mode. */
 typedef enum {
     VEGAS_FP64 = 0,
@@ -136,7 +143,8 @@ typedef struct {
     double I;               /* combined estimate over all iterations so far   */
     double sigma;           /* combined standard error                        */
     double chi2_dof;        /* chi^2 per degree of freedom (0 for one iteration) */
-    int32_t n_iter;         /* iterations combined                            */
+    int32_t n_iter;         /* iterations run, including any left out because
+                               they had no finite value                       */
     int32_t reserved;
 } vegas_result_t;
 
@@ -183,7 +191,17 @@ const char *vegas_jit_log(void);
 /* Run one iteration on the current grid: sample, accumulate S1, S2 and the
  * histograms, then form I_t, sigma_t and update the combination on the
  * device.  Asynchronous if out == NULL; otherwise synchronises the stream and
- * fills *out.  ENONFINITE (with *out filled) if no sample had a finite weight. */
+ * fills *out.  NaN or infinite values of J f are counted in n_nonfinite and
+ * left out of the sums and of n (stratified iterations: counted as 0, n keeps
+ * every sample).  ENONFINITE (with *out filled) if no sample had a finite
+ * weight: that iteration has no estimate and is left out of the combination,
+ * and a refinement after it keeps the grid (its histograms are zero).
+ * The combination: Ibar = sum w_t I_t / sum w_t, w_t = 1/sigma_t^2,
+ * sigma = (sum w_t)^-1/2, chi^2/dof = sum w_t (I_t - Ibar)^2 / (m - 1) over the
+ * m combined iterations, kept as running sums about the first iteration's
+ * estimate (no cancellation when the iterations agree to many digits); if any
+ * iteration has sigma_t = 0 (exact), the mean of those is the result with
+ * sigma 0. */
 vegas_status vegas_iterate(vegas_ctx *ctx, vegas_iter_result *out);
 
 /* Sharded iteration: one integral's samples split over several devices or
@@ -333,8 +351,10 @@ vegas_status vegas_set_pdf_grid(vegas_ctx *ctx, const double *dev_xg, int32_t nx
                                 double u1, double v0, double v1);
 
 /* Checkpoint: a byte blob holding config, parameters, FP64 grid, iteration
- * counter and per-iteration results.  export with buf == NULL sets *size.
- * import restores them into a context created with the same configuration. */
+ * counter, per-iteration results and the running combination (format 4).
+ * export with buf == NULL sets *size.  import restores them into a context
+ * created with the same configuration, family and parameters (EINVAL
+ * otherwise, and for a blob of another format). */
 vegas_status vegas_export_state(vegas_ctx *ctx, void *buf, size_t *size);
 vegas_status vegas_import_state(vegas_ctx *ctx, const void *buf, size_t size);
 
@@ -361,9 +381,11 @@ vegas_status vegas_philox(const uint32_t *dev_ctr, const uint32_t *dev_key, uint
  * It computes what vegas_iterate's sampling does for iteration t (the Philox
  * counter word) of the given configuration and integrand on the grid
  * dev_edges (device, d rows of N+1 FP64 edges, read only), and writes
- * dev_sums (device, 2 + d*N FP64: S1, S2, h_0[0..N-1], ...), in the layout of
- * vegas_get_sums.  Asynchronous on stream; nothing is reported back except
- * the status.
+ * dev_sums (device, 3 + d*N FP64: S1, S2, h_0[0..N-1], ..., in the layout of
+ * vegas_get_sums, then the number of samples whose J f was NaN or infinite,
+ * which S1, S2 and the histograms leave out: I = S1 / (n_events - that
+ * count)).  Asynchronous on stream; nothing else is reported back except the
+ * status.
  *   - EINVAL for an invalid configuration or integrand, and when
  *     n_dim * n_bins exceeds 4096 (vegas_last_error_string says so).
  *   - The first call on each device looks up the scratch array's device
@@ -396,8 +418,8 @@ vegas_status vegas_profile_read(vegas_ctx *ctx, float *ms_out, int32_t cap, int3
  * Sample s of a slot in iteration t draws the same Philox words as in a
  * single-integral context with the same seed and integral_id, so each slot's
  * iteration estimates equal its estimates alone up to summation order.  The
- * combination across iterations uses running sums (inverse-variance weights,
- * chi^2 from sum w I^2 - I sum w I).
+ * combination across iterations is vegas_iterate's (running sums about the
+ * first estimate; iterations without a finite value left out).
  *
  * The workspace (caller-allocated, 256-byte aligned) holds the step plan,
  * the per-slot state table and a pool from which each added integral takes

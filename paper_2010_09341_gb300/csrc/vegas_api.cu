@@ -181,6 +181,51 @@ bool prepare_family(int family, int d, const double *p, FamilyConsts &fc, double
     return true;
 }
 
+// The FP32 paths work in the coordinate X = 2^32 x (the sampling table holds
+// (2^32 e, w); Prec<float>::coord in the kernels).  Their constants are the
+// family's FP64 constants with that power of two folded in where the formula
+// meets x (p_j / 2^32 beside x, q_j 2^32 subtracted from it, s0 / 2^64 for a
+// product or square of two coordinates, log2 offsets + 32), rounded to FP32.
+// kappa: the constant factor by which the FP32 kernel's value of the integrand
+// differs from f (SUM adds X: 2^32; the LO toy's rsqrt(x1 x2) becomes
+// rsqrt(X1 X2): 2^-32; the density-grid toy divides by x1 x2 as well: 2^-64);
+// the FP32 initial weight is divided by it.  User integrands see x itself.
+void fp32_consts(int family, int d, const FamilyConsts &fc, FamConsts<float> &out, double &kappa) {
+    const double S = 4294967296.0, iS = 1.0 / S;
+    FamilyConsts t = fc;
+    kappa = 1.0;
+    switch (family) {
+    case VEGAS_F_SUM: kappa = S; break;
+    case VEGAS_F_GAUSS_SYM: t.s[0] = fc.s[0] * iS * iS; break;
+    case VEGAS_F_GENZ_OSC:
+    case VEGAS_F_GENZ_CORNER:
+        for (int j = 0; j < d; ++j) t.p[j] = fc.p[j] * iS;
+        break;
+    case VEGAS_F_GENZ_GAUSS:
+    case VEGAS_F_GENZ_PROD:
+        for (int j = 0; j < d; ++j) {
+            t.p[j] = fc.p[j] * iS;
+            t.q[j] = fc.q[j] * S;
+        }
+        break;
+    case VEGAS_F_LO:
+        t.s[0] = fc.s[0] * iS * iS;
+        kappa = iS;
+        break;
+    case VEGAS_F_LO_PDF:
+        t.s[0] = fc.s[0] * iS * iS;
+        t.p[0] = fc.p[0] + 32.0;  // log2 X of the first knot
+        kappa = iS * iS;
+        break;
+    default: break;  // CONST; USER (x unscaled in the kernel)
+    }
+    for (int k = 0; k < 32; ++k) {
+        out.p[k] = static_cast<float>(t.p[k]);
+        out.q[k] = static_cast<float>(t.q[k]);
+    }
+    for (int k = 0; k < 8; ++k) out.s[k] = static_cast<float>(t.s[k]);
+}
+
 }  // namespace
 
 struct vegas_ctx {
@@ -358,8 +403,14 @@ static vegas_status create_impl(const vegas_config *cfg, const vegas_integrand *
     // divides it out exactly.
     c->scale = std::ldexp(1.0, -static_cast<int>(std::lround(std::log2(fmax))));
     const double Nd = static_cast<double>(N);
-    if (mode == ACC_F64) c->jinit = norm * c->scale * std::pow(Nd, d);
-    else c->jinit = norm * c->scale * std::pow(Nd, d % 4);
+    if (mode == ACC_F64) {
+        c->jinit = norm * c->scale * std::pow(Nd, d);
+    } else {
+        FamConsts<float> unused;
+        double kappa = 1.0;
+        fp32_consts(itg->family, d, fc, unused, kappa);
+        c->jinit = norm * c->scale * std::pow(Nd, d % 4) / kappa;
+    }
     c->nblk4 = Nd * Nd * Nd * Nd;
     c->kfn = fn;
     c->smem = smem;
@@ -451,7 +502,7 @@ static void fill_strata(SampleArgs &a, const Strata &st, int d, double *q) {
 }
 
 static SampleArgs make_args(const vegas_ctx *c, long long s_begin, long long n, int t) {
-    SampleArgs a;
+    SampleArgs a{};
     a.table = c->table;
     a.acc = c->acc;
     a.n_nonfinite = c->nonfinite;
@@ -467,11 +518,8 @@ static SampleArgs make_args(const vegas_ctx *c, long long s_begin, long long n, 
     a.jmul = c->jmul + (c->n_done & 1);
     a.hscale = c->hscale;
     a.fc64 = c->fc;
-    for (int k = 0; k < 32; ++k) {
-        a.fc32.p[k] = static_cast<float>(c->fc.p[k]);
-        a.fc32.q[k] = static_cast<float>(c->fc.q[k]);
-    }
-    for (int k = 0; k < 8; ++k) a.fc32.s[k] = static_cast<float>(c->fc.s[k]);
+    double kappa;
+    fp32_consts(c->family, c->cfg.n_dim, c->fc, a.fc32, kappa);
     memset(&a.st, 0, sizeof(a.st));
     a.pdf = c->pdf;
     a.pdf_nx = c->pdf_nx;
@@ -594,7 +642,11 @@ static vegas_status after_finalize(vegas_ctx *c, vegas_iter_result *out) {
     out->sigma = r.sigma;
     out->n = r.n;
     out->n_nonfinite = r.n_nonfinite;
-    return r.n <= 0 ? VEGAS_ENONFINITE : VEGAS_OK;
+    // no finite value: plain iterations count only finite samples in n,
+    // stratified ones count every sample (a non-finite value as 0)
+    const bool strat = strata_for(c->strat_req, c->cfg.n_dim, c->cfg.n_events).P > 0;
+    const bool none = strat ? r.n_nonfinite >= r.n : r.n <= 0;
+    return none ? VEGAS_ENONFINITE : VEGAS_OK;
 }
 
 // Iteration result from the accumulators (n_events samples in all) and the
@@ -951,7 +1003,7 @@ vegas_status vegas_export_state(vegas_ctx *c, void *buf, size_t *size) {
                              c->stream));
     VEGAS_CK(cudaStreamSynchronize(c->stream));
     h.magic = kMagic;
-    h.version = 3;
+    h.version = 4;
     h.cfg = c->cfg;
     h.family = c->family;
     h.n_params = static_cast<int32_t>(c->params.size());
@@ -983,7 +1035,7 @@ vegas_status vegas_import_state(vegas_ctx *c, const void *buf, size_t size) {
     BlobHeader h;
     memcpy(&h, p, sizeof(h));
     p += sizeof(h);
-    if (h.magic != kMagic || h.version != 3) return VEGAS_EINVAL;
+    if (h.magic != kMagic || h.version != 4) return VEGAS_EINVAL;
     const vegas_config &a = h.cfg, &b = c->cfg;
     if (a.n_dim != b.n_dim || a.n_bins != b.n_bins || a.n_events != b.n_events ||
         a.seed != b.seed || a.integral_id != b.integral_id || a.precision != b.precision ||
@@ -1056,6 +1108,9 @@ namespace vegas {
 bool host_prepare_family(int family, int d, const double *p, FamilyConsts &fc, double &norm, double &fmax) {
     return prepare_family(family, d, p, fc, norm, fmax);
 }
+void host_fp32_consts(int family, int d, const FamilyConsts &fc, FamConsts<float> &out, double &kappa) {
+    fp32_consts(family, d, fc, out, kappa);
+}
 int host_n_params(int family, int d) { return n_params_for(family, d); }
 }  // namespace vegas
 
@@ -1079,10 +1134,12 @@ constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 char *g_noalloc_ptr[kMaxDevices] = {};
 
-__global__ void noalloc_unscale_kernel(const double *acc, double *out, int total, double inv1,
-                                       double inv2) {
+// out[0 .. total-1]: the sums unscaled; out[total]: the non-finite count.
+__global__ void noalloc_unscale_kernel(const double *acc, const unsigned long long *nonfinite, double *out,
+                                       int total, double inv1, double inv2) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c < total) out[c] = acc[c] * (c == 0 ? inv1 : inv2);
+    else if (c == total) out[c] = static_cast<double>(*nonfinite);
 }
 
 // Device address of the scratch array on the current device, looked up once
@@ -1158,7 +1215,7 @@ extern "C" vegas_status vegas_iterate_noalloc(const vegas_config *cfg, const veg
 
     const double scale = std::ldexp(1.0, -static_cast<int>(std::lround(std::log2(fmax))));
     const double Nd = static_cast<double>(N);
-    SampleArgs a;
+    SampleArgs a{};
     a.table = table;
     a.acc = acc;
     a.n_nonfinite = nonfinite;
@@ -1167,32 +1224,35 @@ extern "C" vegas_status vegas_iterate_noalloc(const vegas_config *cfg, const veg
     a.key0 = cfg->seed;
     a.key1 = cfg->integral_id;
     a.iter = static_cast<uint32_t>(t);
-    a.jinit = mode == ACC_F64 ? norm * scale * std::pow(Nd, d) : norm * scale * std::pow(Nd, d % 4);
+    double kappa = 1.0;
+    fp32_consts(itg->family, d, fc, a.fc32, kappa);
+    a.jinit = mode == ACC_F64 ? norm * scale * std::pow(Nd, d) : norm * scale * std::pow(Nd, d % 4) / kappa;
     a.nblk4 = Nd * Nd * Nd * Nd;
     a.jmul = nullptr;
     a.hscale = hscale;
     a.fc64 = fc;
-    for (int k = 0; k < 32; ++k) {
-        a.fc32.p[k] = static_cast<float>(fc.p[k]);
-        a.fc32.q[k] = static_cast<float>(fc.q[k]);
-    }
-    for (int k = 0; k < 8; ++k) a.fc32.s[k] = static_cast<float>(fc.s[k]);
     const long long n = cfg->n_events;
     const long long lim = cfg->events_limit > 0 ? cfg->events_limit : n;
     for (long long s0 = 0; s0 < n; s0 += lim) {
         a.s_begin = s0;
         a.n = std::min(lim, n - s0);
-        const long long want = (a.n + threads * 4LL - 1) / (threads * 4LL);
-        long long blocks = std::max(1LL, std::min<long long>(static_cast<long long>(occ) * di.sms, want));
+        // the grid of launch_sampling: 4 samples per thread at least in the
+        // FP32 modes, 1 in FP64 (every SM's FP64 pipe should contribute), the
+        // fixed-point cells' capacity, whole waves
+        const long long per_thread = mode == ACC_F64 ? 1 : 4;
+        const long long resident = static_cast<long long>(occ) * di.sms;
+        const long long want = (a.n + threads * per_thread - 1) / (threads * per_thread);
+        long long blocks = std::max(1LL, std::min<long long>(resident, want));
         if (mode != ACC_F64) {
             const long long cap = block_samples_max(mode, priv ? 1 : 0, N);
             blocks = std::max(blocks, (a.n + cap - 1) / cap);
         }
+        blocks = whole_waves(blocks, resident);
         void *params[] = {&a};
         VEGAS_CK(cudaLaunchKernel(fn, dim3(static_cast<unsigned>(blocks)), dim3(threads), params, smem, s));
     }
     const int total = 2 + d * N;
-    noalloc_unscale_kernel<<<(total + 255) / 256, 256, 0, s>>>(acc, dev_sums, total, 1.0 / scale,
+    noalloc_unscale_kernel<<<(total + 256) / 256, 256, 0, s>>>(acc, nonfinite, dev_sums, total, 1.0 / scale,
                                                                1.0 / (scale * scale));
     VEGAS_CK(cudaGetLastError());
     return VEGAS_OK;

@@ -17,12 +17,10 @@ namespace vegas {
 
 // ------------------------------------------------------------- finalize
 // Iteration estimate (Lepage 1978): I = S1/n, sigma^2 = (S2/n - I^2)/(n-1).
-// Combination over iterations, kept as running FP64 sums of w = 1/sigma^2,
-// w I and w I^2 over the iterations with a finite weight:
-//   I = sum w I / sum w,  sigma = (sum w)^-1/2,
-//   chi^2/dof = (sum w I^2 - I sum w I) / (m - 1)   (clamped at 0).
-// Iterations with zero variance are exact: if any exist, their plain mean is
-// the result with sigma 0.  O(1) whatever the number of iterations so far.
+// Iteration result (Lepage): I = S1/n, sigma^2 = (S2/n - I^2)/(n - 1) over
+// the n samples with a finite value (stratified: every sample, a non-finite
+// value counted as 0), then the running combination (comb_add).  An
+// iteration without a finite value has no estimate: status 6, left out.
 //
 // The v-rescale is double-buffered by record parity: iteration `rec` was
 // sampled with jmul[rec & 1] and the next one uses jmul[(rec + 1) & 1], so
@@ -72,39 +70,12 @@ __device__ void finalize_stats(const FinalizeArgs &f) {
         r.sigma = 0.0;
     }
     f.iters[f.rec % kIterRing] = r;
+    // no finite value among the f.n samples drawn: no estimate
+    const bool combined = nf < f.n;
     CombState st = *f.cs;
-    st.n_done += 1;
-    if (ne > 0) {
-        st.m += 1;
-        if (r.sigma == 0.0) {
-            st.nzero += 1;
-            st.zsum += r.I;
-        } else {
-            const double w = 1.0 / (r.sigma * r.sigma);
-            st.wsum += w;
-            st.wisum += w * r.I;
-            st.wi2sum += w * r.I * r.I;
-        }
-    }
+    comb_add(st, r.I, r.sigma, combined);
     *f.cs = st;
-    CombRec out;
-    out.n_iter = st.n_done;
-    out.status = ne <= 0 ? 6 : 0;
-    if (st.nzero > 0) {
-        out.I = st.zsum / st.nzero;
-        out.sigma = 0.0;
-        out.chi2_dof = 0.0;
-    } else if (st.wsum > 0.0) {
-        out.I = st.wisum / st.wsum;
-        out.sigma = 1.0 / sqrt(st.wsum);
-        const double chi = st.wi2sum - out.I * st.wisum;
-        out.chi2_dof = st.m > 1 ? fmax(chi, 0.0) / static_cast<double>(st.m - 1) : 0.0;
-    } else {
-        out.I = 0.0;
-        out.sigma = 0.0;
-        out.chi2_dof = 0.0;
-    }
-    *f.comb = out;
+    *f.comb = comb_result(st, combined);
 }
 
 // Histogram rows of one iteration: last = acc * inv^2, acc = 0, for the

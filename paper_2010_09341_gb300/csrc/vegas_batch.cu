@@ -39,11 +39,8 @@ size_t batch_sample_smem(int mode, int layout, int max_cells) { return sample_sm
 // ------------------------------------------------------------- kernels
 // Iteration result and running combination of every item's slot (one block
 // per item, grid-stride), then the accumulators move to `last` and clear.
-// The running combination keeps sum w, sum w I, sum w I^2 with w = 1/sigma^2:
-//   I = sum w I / sum w,  sigma = (sum w)^-1/2,
-//   chi^2/dof = (sum w I^2 - I sum w I) / (m - 1);
-// iterations with zero variance are exact and, if any, their plain mean is
-// the result with sigma 0.  Also writes the next iteration's fixed-point
+// The running combination is comb_add's (shifted sums; iterations without a
+// finite value left out).  Also writes the next iteration's fixed-point
 // histogram scale and resets the tile counter for the next step.
 __global__ void __launch_bounds__(128)
 batch_finalize_kernel(const BatchArgs ba) {
@@ -79,35 +76,9 @@ batch_finalize_kernel(const BatchArgs ba) {
                 r.I = ne == 1 ? sd.acc[0] * inv1 : 0.0;
                 r.sigma = 0.0;
             }
-            if (ne > 0) {
-                sd.m += 1;
-                if (r.sigma == 0.0) {
-                    sd.nzero += 1;
-                    sd.zsum += r.I;
-                } else {
-                    const double w = 1.0 / (r.sigma * r.sigma);
-                    sd.wsum += w;
-                    sd.wisum += w * r.I;
-                    sd.wi2sum += w * r.I * r.I;
-                }
-            }
-            CombRec c;
-            c.n_iter = sd.m;
-            c.status = ne <= 0 ? 6 : 0;
-            if (sd.nzero > 0) {
-                c.I = sd.zsum / sd.nzero;
-                c.sigma = 0.0;
-                c.chi2_dof = 0.0;
-            } else if (sd.wsum > 0.0) {
-                c.I = sd.wisum / sd.wsum;
-                c.sigma = 1.0 / sqrt(sd.wsum);
-                const double chi = sd.wi2sum - c.I * sd.wisum;
-                c.chi2_dof = sd.m > 1 ? fmax(chi, 0.0) / static_cast<double>(sd.m - 1) : 0.0;
-            } else {
-                c.I = 0.0;
-                c.sigma = 0.0;
-                c.chi2_dof = 0.0;
-            }
+            const bool combined = ne > 0;
+            comb_add(sd.cs, r.I, r.sigma, combined);
+            const CombRec c = comb_result(sd.cs, combined);
             sd.last_it = r;
             sd.comb = c;
             BatchResult br;
@@ -460,6 +431,7 @@ int prec_mode(int precision) {
 // Host-side helpers of vegas_api.cu (family constants, parameter counts).
 namespace vegas {
 bool host_prepare_family(int family, int d, const double *p, FamilyConsts &fc, double &norm, double &fmax);
+void host_fp32_consts(int family, int d, const FamilyConsts &fc, FamConsts<float> &out, double &kappa);
 int host_n_params(int family, int d);
 }
 
@@ -594,18 +566,15 @@ vegas_status vegas_batch_add(vegas_batch *b, const vegas_config *cfg, const vega
     sd.key1 = cfg->integral_id;
     const double scale = std::ldexp(1.0, -static_cast<int>(std::lround(std::log2(fmax))));
     const double Nd = static_cast<double>(N);
+    double kappa = 1.0;
+    host_fp32_consts(itg->family, d, fc, sd.fc32, kappa);
     sd.jinit64 = norm * scale * std::pow(Nd, d);
-    sd.jinit32 = static_cast<float>(norm * scale * std::pow(Nd, d % 4));
+    sd.jinit32 = static_cast<float>(norm * scale * std::pow(Nd, d % 4) / kappa);
     sd.n4 = static_cast<float>(Nd * Nd * Nd * Nd);
     sd.alpha = cfg->alpha;
     sd.inv_scale = 1.0 / scale;
     sd.jmul = 1.0;
     sd.fc64 = fc;
-    for (int k = 0; k < 32; ++k) {
-        sd.fc32.p[k] = static_cast<float>(fc.p[k]);
-        sd.fc32.q[k] = static_cast<float>(fc.q[k]);
-    }
-    for (int k = 0; k < 8; ++k) sd.fc32.s[k] = static_cast<float>(fc.s[k]);
     sd.edges = reinterpret_cast<double *>(base);
     sd.table = base + up(sizeof(double) * d * (N + 1));
     sd.acc = reinterpret_cast<double *>(static_cast<char *>(sd.table) + up(16 * cells));

@@ -34,9 +34,7 @@ struct SlotDev {
     unsigned long long nonfinite;
     float hscale;
     int t;                    // Philox iteration word of the next iteration
-    int m;                    // iterations combined
-    int nzero;                // iterations with zero variance
-    double wsum, wisum, wi2sum, zsum;
+    CombState cs;             // running combination (comb_add)
     IterRec last_it;
     CombRec comb;
 };

@@ -73,9 +73,8 @@ __device__ __forceinline__ uint32_t word(const uint4 &r, int k) {
 // ------------------------------------------------------------ bin split
 // y N with y = r 2^-32 is split with one 32x32->64 integer multiply: the high
 // word is the bin, the low word the in-bin position.  Bins are therefore the
-// same integers in every precision.  The in-bin position is returned as a
-// number m in [1, 2) whose mantissa holds the low word's top bits, so that
-// x = (e - w) + w m with a single fused multiply-add.
+// same integers in every precision.  The in-bin position becomes x with a
+// single fused multiply-add from the bin's table entry (Prec<T>::coord).
 struct Split {
     uint32_t bin;
     uint32_t lo;
@@ -86,10 +85,15 @@ __device__ __forceinline__ Split split_bin(uint32_t r, uint32_t N) {
     return Split{static_cast<uint32_t>(t >> 32), static_cast<uint32_t>(t)};
 }
 
-// FP32: m = 1 + (lo >> 9) 2^-23, exact.  One funnel shift of the 64-bit
-// pair (0x7F : lo) right by 9 gives (lo >> 9) | (0x7F << 23), the bits of m.
-__device__ __forceinline__ float unit_mantissa_f32(uint32_t lo) {
-    return __uint_as_float(__funnelshift_r(lo, 0x7Fu, 9));
+// FP32: the low word rounded to the nearest float (one conversion, relative
+// error at most 2^-24, the same issue cost as a funnel shift on this GPU).
+// Truncating it to a 23-bit fraction instead would leave an error of up to
+// 2^-23 of the bin width, which is a large relative error for points near a
+// bin's lower end at 0 (x << w), where integrands such as x^-1/2 live.
+__device__ __forceinline__ float low_word_f32(uint32_t lo) {
+    float f;
+    asm("cvt.rn.f32.u32 %0, %1;" : "=f"(f) : "r"(lo));
+    return f;
 }
 
 // FP64: m = 1 + lo 2^-32, exact (all 32 bits fit in the 52-bit mantissa).
@@ -97,14 +101,29 @@ __device__ __forceinline__ double unit_mantissa_f64(uint32_t lo) {
     return __hiloint2double(static_cast<int>(0x3FF00000u | (lo >> 12)), static_cast<int>(lo << 20));
 }
 
+// Coordinates and table entries per precision.
+//   FP64: entry (e - w, w) of a bin [e, e + w); x = (e - w) + w m, m = 1 + lo 2^-32.
+//   FP32: the path works in X = 2^32 x (kXS): entry (2^32 e, w);
+//         X = 2^32 e + w float(lo).  The power of two is folded into each
+//         family's FP32 constants (and, where it remains a constant factor of
+//         f, into the initial weight), so the integrands cost what they cost
+//         in x.  Every sample's X carries a relative error of a few 2^-24.
 template <class T> struct Prec;
 template <> struct Prec<float> {
     using T2 = float2;
-    __device__ static __forceinline__ float mant(uint32_t lo) { return unit_mantissa_f32(lo); }
+    static constexpr float kXS = 4294967296.0f;            // 2^32
+    static constexpr float kInvXS = 2.3283064365386963e-10f;  // 2^-32
+    __device__ static __forceinline__ float coord(float2 ent, uint32_t lo) {
+        return __fmaf_rn(ent.y, low_word_f32(lo), ent.x);
+    }
 };
 template <> struct Prec<double> {
     using T2 = double2;
-    __device__ static __forceinline__ double mant(uint32_t lo) { return unit_mantissa_f64(lo); }
+    static constexpr double kXS = 1.0;
+    static constexpr double kInvXS = 1.0;
+    __device__ static __forceinline__ double coord(double2 ent, uint32_t lo) {
+        return __fma_rn(ent.y, unit_mantissa_f64(lo), ent.x);
+    }
 };
 
 // ----------------------------------------------------------- integrands
@@ -233,10 +252,15 @@ __device__ __forceinline__ T grid_xg(const T *tbl, int pitch, int iu, const Cubi
     return ffma(wu.w3, acc[3], ffma(wu.w2, acc[2], ffma(wu.w1, acc[1], wu.w0 * acc[0])));
 }
 
-// The integrand is split into a per-dimension update (called as each x_j is
-// produced) and a final step.  Normalisation constants that do not depend on
-// x (the Gaussian's (a sqrt(pi))^-d, the product-peak's scale) are folded into
-// the initial weight on the host, so the kernels return f up to that factor.
+// The integrand is split into a per-dimension update (called as each
+// coordinate is produced) and a final step.  Normalisation constants that do
+// not depend on x (the Gaussian's (a sqrt(pi))^-d, the product-peak's scale)
+// are folded into the initial weight on the host, so the kernels return f up
+// to that factor.  The coordinate passed in is X = S x with S = Prec<T>::kXS
+// (2^32 in FP32, 1 in FP64); the FP32 constants are prepared for it on the
+// host (p_j / S, q_j S, s0 / S^2 where the formula below has them), and a
+// power of S left over as a factor of f (SUM: S; LO: 1/S; LO_PDF: 1/S^2) is
+// divided out of the initial weight.
 //
 //   CONST        acc unused                        f = 1
 //   SUM          acc += x                          f = acc
@@ -248,6 +272,7 @@ __device__ __forceinline__ T grid_xg(const T *tbl, int pitch, int iu, const Cubi
 //   LO           x kept in registers               f from s0..s6
 //   USER         x kept in registers               f = user_integrand(x, d, p), p = the
 //                                                  parameters in p[], q[], s[] in order
+//                                                  (x unscaled: x = X / S)
 template <int FAM, class T, int MAXD> struct Integrand {
     using C = FamConsts<T>;
     T acc;
@@ -267,7 +292,7 @@ template <int FAM, class T, int MAXD> struct Integrand {
         if (FAM == F_SUM) {
             acc += x;
         } else if (FAM == F_GAUSS_SYM) {
-            const T t = x - T(0.5);
+            const T t = x - T(0.5) * Prec<T>::kXS;
             acc = ffma(t, t, acc);
         } else if (FAM == F_GENZ_OSC || FAM == F_GENZ_CORNER) {
             acc = ffma(fc.p[j], x, acc);
@@ -284,7 +309,7 @@ template <int FAM, class T, int MAXD> struct Integrand {
             else if (j == 1) x1 = x;
             else if (j == 2) x2 = x;
         } else if (FAM == F_USER) {
-            xs[FAM == F_USER ? j : 0] = x;
+            xs[FAM == F_USER ? j : 0] = x * Prec<T>::kInvXS;
             nd = j + 1;
         }
     }
@@ -304,9 +329,9 @@ template <int FAM, class T, int MAXD> struct Integrand {
             // p[0..5] the grid (grid_xg), the constant 2 norm in the initial weight
             const T s1 = fc.s[1], s2 = fc.s[2], s3 = fc.s[3], s4 = fc.s[4], s5 = fc.s[5];
             const T shat = x0 * x1 * s0;
-            const T c = ffma(T(2), x2, T(-1));
+            const T c = ffma(T(2) * Prec<T>::kInvXS, x2, T(-1));
             const bool in = (shat >= s4) && (shat <= s5) && (fabs_t(c) < s3);
-            // p[0..5]: log2 x of the first knot, knots per unit of log2 x, the
+            // p[0..5]: log2 X of the first knot, knots per unit of log2 x, the
             // same for log2 Q^2, nx, nq; the scale's weights serve both densities
             const int nx = static_cast<int>(fc.p[4]), nq = static_cast<int>(fc.p[5]);
             T tv, t1, t2;
@@ -327,9 +352,9 @@ template <int FAM, class T, int MAXD> struct Integrand {
             // in the initial weight.
             const T s1 = fc.s[1], s2 = fc.s[2], s3 = fc.s[3], s4 = fc.s[4], s5 = fc.s[5];
             const T shat = x0 * x1 * s0;
-            const T c = ffma(T(2), x2, T(-1));
+            const T c = ffma(T(2) * Prec<T>::kInvXS, x2, T(-1));
             const bool in = (shat >= s4) && (shat <= s5) && (fabs_t(c) < s3);
-            const T om0 = T(1) - x0, om1 = T(1) - x1;
+            const T om0 = ffma(-Prec<T>::kInvXS, x0, T(1)), om1 = ffma(-Prec<T>::kInvXS, x1, T(1));
             const T g = om0 * om0 * om0 * om1 * om1 * om1 * frsqrt(x0 * x1);
             const T dm = shat - s1;
             const T den = ffma(dm, dm, s2) * shat;

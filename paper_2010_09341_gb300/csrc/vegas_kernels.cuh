@@ -19,13 +19,18 @@ struct IterRec {
     long long n_nonfinite;
 };
 
-// Running sums of the combination (finalize kernel).
+// Running sums of the combination (finalize kernels), taken about I0, the
+// estimate of the first combined iteration with a nonzero variance.
 struct CombState {
-    double wsum, wisum, wi2sum, zsum;
-    int m;        // iterations with a finite weight
-    int nzero;    // of which with zero variance
-    int n_done;   // all iterations finalized
-    int pad;
+    double wsum;    // sum of w = 1/sigma^2
+    double wdsum;   // sum of w (I - I0)
+    double wd2sum;  // sum of w (I - I0)^2
+    double zsum;    // sum of the zero-variance iterations' estimates
+    double i0;
+    int m;          // iterations combined (those with at least one finite value)
+    int nzero;      // of which with zero variance
+    int n_done;     // all iterations finalized
+    int have_i0;
 };
 
 // Iteration records are kept in a ring of this many entries.
@@ -39,6 +44,58 @@ struct CombRec {
     int n_iter;
     int status;             // 0 ok, 6 = every weight of the last iteration non-finite
 };
+
+// Inverse-variance combination of the iterations (Lepage; weights 1/sigma^2
+// of every iteration with a finite value, no warm-up discard), kept as
+// running sums about I0 so that chi^2 does not cancel when the iterations
+// agree to many digits (a one-pass sum w I^2 - Ibar sum w I loses all of
+// chi^2 once (Ibar/sigma)^2 nears 1/eps):
+//   Ibar = I0 + sum w (I - I0) / sum w,  sigma = (sum w)^-1/2,
+//   chi^2/dof = (sum w (I - I0)^2 - (sum w (I - I0))^2 / sum w) / (m - 1).
+// Iterations with zero variance are exact: if any, their plain mean is the
+// result, with sigma 0.  `combined`: false for an iteration without a finite
+// value, which has no estimate and is left out.
+__host__ __device__ inline void comb_add(CombState &st, double I, double sigma, bool combined) {
+    st.n_done += 1;
+    if (!combined) return;
+    st.m += 1;
+    if (sigma == 0.0) {
+        st.nzero += 1;
+        st.zsum += I;
+        return;
+    }
+    if (!st.have_i0) {
+        st.i0 = I;
+        st.have_i0 = 1;
+    }
+    const double w = 1.0 / (sigma * sigma);
+    const double dI = I - st.i0;
+    st.wsum += w;
+    st.wdsum += w * dI;
+    st.wd2sum += w * dI * dI;
+}
+
+__host__ __device__ inline CombRec comb_result(const CombState &st, bool last_combined) {
+    CombRec out;
+    out.n_iter = st.n_done;
+    out.status = last_combined ? 0 : 6;
+    if (st.nzero > 0) {
+        out.I = st.zsum / st.nzero;
+        out.sigma = 0.0;
+        out.chi2_dof = 0.0;
+    } else if (st.wsum > 0.0) {
+        const double mean_d = st.wdsum / st.wsum;
+        out.I = st.i0 + mean_d;
+        out.sigma = 1.0 / sqrt(st.wsum);
+        const double chi = st.wd2sum - mean_d * st.wdsum;
+        out.chi2_dof = st.m > 1 ? fmax(chi, 0.0) / static_cast<double>(st.m - 1) : 0.0;
+    } else {
+        out.I = 0.0;
+        out.sigma = 0.0;
+        out.chi2_dof = 0.0;
+    }
+    return out;
+}
 
 // Sampling kernel for (accumulation mode, family, dimension, lane-private
 // layout); nullptr if the combination does not exist.

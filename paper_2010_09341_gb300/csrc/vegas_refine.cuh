@@ -13,14 +13,12 @@ namespace vegas {
 //            interpolated linearly inside the old bin; zero-weight bins are
 //            skipped and an edge on an old edge takes the lower bin.
 // A dimension whose weights sum to zero keeps its grid.
-template <class T2, class T>
-__device__ __forceinline__ void write_entry(void *table, int idx, double e, double w) {
-    reinterpret_cast<T2 *>(table)[idx] = T2{static_cast<T>(e - w), static_cast<T>(w)};
-}
-
+// Sampling-table entry of the bin [e, e + w) (the coordinate forms of
+// Prec<T>::coord): FP64 (e - w, w), x = (e - w) + w m with m in [1, 2);
+// FP32 (2^32 e, w), X = 2^32 x = 2^32 e + w float(lo).
 __device__ __forceinline__ void store_table(void *table, int mode, int idx, double e, double w) {
-    if (mode == ACC_F64) write_entry<double2, double>(table, idx, e, w);
-    else write_entry<float2, float>(table, idx, e, w);
+    if (mode == ACC_F64) reinterpret_cast<double2 *>(table)[idx] = double2{e - w, w};
+    else reinterpret_cast<float2 *>(table)[idx] = float2{static_cast<float>(e * 4294967296.0), static_cast<float>(w)};
 }
 
 constexpr int kRefineThreads = 128;

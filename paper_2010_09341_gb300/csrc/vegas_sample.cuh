@@ -4,12 +4,13 @@
 // takes a contiguous range, each thread every blockDim-th sample of it.
 // Per sample (VEGAS, Lepage 1978; the paper's method, Sec. 1):
 //   r   = Philox4x32-10 words (ceil(d/4) calls, registers only)
-//   i_j = bin of r_j, x_j = (e - w)_j[i_j] + w_j[i_j] m_j,  m_j in [1, 2)
+//   i_j = bin of r_j, x_j = e_j[i_j] + w_j[i_j] lo_j 2^-32  (lo_j: the low word
+//         of r_j N; FP32 works in X = 2^32 x, see Prec<T>::coord)
 //   J   = C prod_j w_j[i_j]            (C = N^d times constant factors of f)
 //   v   = J f(x);  S1 += v, S2 += v^2, h_j[i_j] += v^2
 //
 // Shared memory holds, per (dimension, bin) cell, TP copies of the table
-// entry (e - w, w) and HP copies of the histogram cell, so that the 32 lanes
+// entry (Prec<T>::coord) and HP copies of the histogram cell, so that the 32 lanes
 // of a warp read and update distinct banks whatever bins they draw
 // (lane-private copies).  Layouts (template parameter PRIV): 1 = TP and HP
 // copies as above, 2 = half as many (two lanes share a copy: some two-way
@@ -45,7 +46,7 @@ __device__ __forceinline__ uint32_t strat_word(uint32_t r, uint32_t h, uint32_t 
 }
 
 struct SampleArgs {
-    const void *table;        // [d][N] entries (e - w, w): double2 or float2
+    const void *table;        // [d][N] entries: double2 (e - w, w) or float2 (2^32 e, w)
     double *acc;              // [2 + d N] FP64 accumulators: S1, S2, histograms
     unsigned long long *n_nonfinite;
     long long s_begin;        // first sample index of this launch
@@ -58,7 +59,7 @@ struct SampleArgs {
     double nblk4;             // N^4 (FP32 path multiplies it in every 4 dims)
     const float *hscale;      // FP32 modes: fixed-point scale of v^2 (0: float cells)
     FamConsts<double> fc64;   // integrand constants, FP64 path
-    FamConsts<float> fc32;    // the same rounded to FP32, FP32 paths
+    FamConsts<float> fc32;    // the same for the FP32 paths' X = 2^32 x, rounded to FP32
     StratArgs st;             // stratified launches: s_begin, n count hypercubes
     const double *pdf;        // F_LO_PDF: the density grid, pdf_nx x pdf_nq FP64 values (device)
     int pdf_nx, pdf_nq;
@@ -330,8 +331,7 @@ __device__ __forceinline__ typename ModeTraits<MODE>::T map_sample(
                     const Split sp = split_bin(rw, static_cast<uint32_t>(N));
                     const uint32_t cell = static_cast<uint32_t>(j * N) + sp.bin;
                     const T2 ent = tab_l[cell * TP];
-                    const T m = Prec<T>::mant(sp.lo);
-                    const T x = ffma(ent.y, m, ent.x);
+                    const T x = Prec<T>::coord(ent, sp.lo);
                     J *= ent.y;
                     if (sizeof(T) == 4 && (j & 3) == 3) J *= rp.n4;
                     cellj.set(j, cell);

@@ -58,7 +58,7 @@ __global__ void trace_kernel(const SampleArgs a, double inv_scale, int32_t *bins
         const unsigned long long s = static_cast<unsigned long long>(a.s_begin + k);
         const uint32_t slo = static_cast<uint32_t>(s), shi = static_cast<uint32_t>(s >> 32);
         T J = static_cast<T>(a.jinit * jm);
-        T xo = T(0), x0 = T(0), x1 = T(0), x2 = T(0);
+        double xo = 0.0, x0 = 0.0, x1 = 0.0, x2 = 0.0;
         fam.begin(fc);
 #pragma unroll
         for (int q = 0; q < (MAXD + 3) / 4; ++q) {
@@ -75,17 +75,18 @@ __global__ void trace_kernel(const SampleArgs a, double inv_scale, int32_t *bins
                         const Split sp = split_bin(rw, static_cast<uint32_t>(N));
                         const uint32_t cell = static_cast<uint32_t>(j * N) + sp.bin;
                         const T2 ent = tab[cell];
-                        const T m = Prec<T>::mant(sp.lo);
-                        const T x = ffma(ent.y, m, ent.x);
+                        const T x = Prec<T>::coord(ent, sp.lo);
                         J *= ent.y;
                         if (sizeof(T) == 4 && (j & 3) == 3) J *= n4;
                         fam.dim(j, x, fc);
-                        if (j == h.obs) xo = x;
-                        if (j == 0) x0 = x;
-                        if (j == 1) x1 = x;
-                        if (j == 2) x2 = x;
+                        // the coordinate itself (FP32 works in 2^32 x; exact)
+                        const double xd = static_cast<double>(x) * Prec<T>::kInvXS;
+                        if (j == h.obs) xo = xd;
+                        if (j == 0) x0 = xd;
+                        if (j == 1) x1 = xd;
+                        if (j == 2) x2 = xd;
                         if (bins) bins[k * d + j] = static_cast<int32_t>(sp.bin);
-                        if (xs) xs[k * d + j] = static_cast<double>(x);
+                        if (xs) xs[k * d + j] = xd;
                     }
                 }
             }
@@ -96,9 +97,9 @@ __global__ void trace_kernel(const SampleArgs a, double inv_scale, int32_t *bins
         if (ws) ws[k] = vd;
         if (hs && isfinite(vd)) {
             double o;
-            if (h.obs >= 0) o = static_cast<double>(xo);
-            else if (h.obs == -1) o = sqrt(static_cast<double>(x0) * static_cast<double>(x1)) * h.sqrt_s;
-            else o = 2.0 * static_cast<double>(x2) - 1.0;
+            if (h.obs >= 0) o = xo;
+            else if (h.obs == -1) o = sqrt(x0 * x1) * h.sqrt_s;
+            else o = 2.0 * x2 - 1.0;
             int b;
             if (o < h.lo) b = 0;
             else if (o >= h.hi) b = h.nb + 1;

@@ -319,13 +319,14 @@ def vegas_iterate_noalloc(cfg: Config, family: str, params, t: int, edges: torch
     For callers that cannot allocate device memory at call time (a runtime
     that owns the device's memory through its own pool, a plugin that must not
     grow the footprint).  ``edges`` (d x (N+1) float64) and ``sums``
-    (2 + d*N float64) are the caller's CUDA tensors; scratch lives in a fixed
-    array inside the library (n_dim * n_bins <= 4096).  Calls that overlap on
-    the GPU race on that array.
+    (3 + d*N float64: S1, S2, the histograms, the non-finite count) are the
+    caller's CUDA tensors; scratch lives in a fixed array inside the library
+    (n_dim * n_bins <= 4096).  Calls that overlap on the GPU race on that array.
     """
     assert edges.is_cuda and sums.is_cuda
     assert edges.dtype == torch.float64 and sums.dtype == torch.float64
     assert edges.is_contiguous() and sums.is_contiguous()
+    assert edges.numel() == cfg.n_dim * (cfg.n_bins + 1) and sums.numel() >= 3 + cfg.n_dim * cfg.n_bins
     c = cfg.to_c()
     p = np.ascontiguousarray(np.asarray(params, dtype=np.float64))
     itg = nat.VegasIntegrand(nat.FAMILIES[family], int(cfg.n_dim),

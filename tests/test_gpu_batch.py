@@ -48,9 +48,8 @@ def test_batch_equals_alone(prec):
         r = V.vegas_run(ctx, steps)
         for t, ((tb, Ib, sb, Icb), (Ia, sa, _, _)) in enumerate(zip(got[k], r["iters"])):
             assert tb == t
-            tol = 1e-4 if fam == "lo" else 1e-5  # LO: hard cuts (see the single-path tests)
-            assert abs(Ib - Ia) <= tol * abs(Ia) + 1e-300, (fam, t, Ib, Ia)
-        assert abs(got[k][-1][3] - r["I"]) <= 1e-4 * abs(r["I"]) + 1e-300
+            assert abs(Ib - Ia) <= 1e-5 * abs(Ia) + 1e-300, (fam, t, Ib, Ia)
+        assert abs(got[k][-1][3] - r["I"]) <= 1e-5 * abs(r["I"]) + 1e-300
 
 
 def test_batch_iteration_parity_with_oracle():

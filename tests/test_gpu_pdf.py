@@ -2,10 +2,10 @@
 against the FP64 oracle's grid interpolation.
 
 Tolerances: bins bit-exact; FP64 per-sample values 1e-13 relative and
-iteration results 1e-12; FP32 as for the LO toy (hard cuts: a point within
-FP32 rounding of a cut edge may fall on the other side; the interpolation's
-cell index comes from an FP32 log2, which moves the point by ~1e-7 of a cell
-inside a C1 interpolant): per sample 2e-4, per iteration 1e-4.
+iteration results 1e-12; FP32 per iteration 1e-5 as for every family, per
+sample 2e-4 (the interpolation's cell index comes from an FP32 log2, which
+moves the point by ~1e-6 of a cell inside a C1 interpolant, on top of the LO
+toy's Breit-Wigner slope).
 """
 import math
 
@@ -18,7 +18,7 @@ from paper_2010_09341_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-TOL_IT = {"fp64": 1e-12, "fp32_acc64": 1e-4, "fp32_kahan": 1e-4}
+TOL_IT = {"fp64": 1e-12, "fp32_acc64": 1e-5, "fp32_kahan": 1e-5}
 
 
 def _grid(nx=96, nq=48, b1=0.5):
@@ -175,4 +175,4 @@ def test_pdf_full_size_iteration_fp32_kahan():
     I, sigma, _, _ = V.vegas_iterate(ctx)
     acc = O.iterate(3, N, e, "lo_pdf", W.lo_params(), 0, 0, 2, n, threads=16)
     Io, var = O.iteration_result(acc["S1"], acc["S2"], n)
-    assert abs(I - Io) <= 1e-4 * abs(Io)
+    assert abs(I - Io) <= 1e-5 * abs(Io)

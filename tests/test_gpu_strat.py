@@ -18,7 +18,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from gpu_helpers import PRECS, TOL, native, params_for, random_grid
+from gpu_helpers import BIN_TOL, PRECS, TOL, assert_hist_close, native, params_for, random_grid
 
 pytestmark = pytest.mark.gpu
 
@@ -143,8 +143,7 @@ def test_strat_iteration_parity_on_shared_grid(family, d, N, n, B, prec, warm):
     assert n_nf == acc["n_nonfinite"]
     assert abs(I - Io) <= tol * abs(Io) + 1e-300, (I, Io)
     assert abs(S2 - acc["S2"]) <= tol * abs(acc["S2"]) + 1e-300
-    hs = acc["hist"].sum()
-    assert np.max(np.abs(h - acc["hist"])) <= tol * hs
+    assert_hist_close(h, acc["hist"], tol, BIN_TOL[prec])
     assert abs(sigma - math.sqrt(var)) <= SIGMA_TOL[prec] * math.sqrt(var), (sigma, math.sqrt(var))
 
 

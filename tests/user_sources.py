@@ -51,6 +51,30 @@ template <class T> __device__ T user_integrand(const T *x, int d, const T *p) {
 }
 """
 
+# NaN where x_0 < 2^-6, +Inf where x_1 > 1 - 2^-6, -Inf where
+# 1/2 <= x_2 < 1/2 + 2^-11 (d >= 3), else 1 + sum x_j^2.  The thresholds are
+# exact in FP32 and FP64, so both precisions see the same regions; the
+# non-finite values are formed at run time from x.
+NONFINITE = r"""
+template <class T> __device__ T user_integrand(const T *x, int d, const T *p) {
+    const T z = x[0] - x[0];
+    if (x[0] < T(0.015625)) return z / z;
+    if (x[1] > T(0.984375)) return T(1) / z;
+    if (x[2] >= T(0.5) && x[2] < T(0.50048828125)) return T(-1) / z;
+    T f = T(1);
+    for (int j = 0; j < d; ++j) f += x[j] * x[j];
+    return f;
+}
+"""
+
+# NaN everywhere
+ALL_NAN = r"""
+template <class T> __device__ T user_integrand(const T *x, int d, const T *p) {
+    const T z = x[0] - x[0];
+    return z / z;
+}
+"""
+
 BROKEN = r"""
 template <class T> __device__ T user_integrand(const T *x, int d, const T *p) {
     return this_is_not_defined(x[0]);
