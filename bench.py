@@ -62,18 +62,19 @@ def ops_per_sample(family: str, d: int, precision: str):
 
     Philox4x32-10: 10 rounds x (2 wide multiplies + 2 three-input xors) per
     4 words (round keys are per-thread constants).  Per dimension: 1 wide
-    multiply (bin split), 2 (mantissa build), 1 cell index, 1 table address,
-    1 table load, 1 FMA (x), 1 multiply (J), 1 histogram address, 1 shared
-    integer atomic, plus the integrand's per-dimension ops; J *= N^4 once per
-    4 dimensions.  Per sample: integrand finish, v = J f, v^2, non-finite test
+    multiply (bin split), 1 conversion of the in-bin position, 1 cell index,
+    1 table address, 1 table load, 1 FMA (x), 1 multiply (J), 1 histogram
+    address, 1 shared integer atomic, plus the integrand's per-dimension ops
+    (a family that takes x about a centre gets it from the table: the
+    symmetric Gaussian's (x - 1/2)^2 is one FMA); J *= N^4 once per 4
+    dimensions.  Per sample: integrand finish, v = J f, v^2, non-finite test
     (2), the fixed-point histogram value (scale, convert, clamp, range test:
     5), the two sums (FP32 partials + FP64 flush: 2 adds, 2 for the chunk
-    bookkeeping and 4 FP64 ops per 8 samples; Kahan: 8 FP32 ops; FP64:
-    convert + add + FMA), loop (3).
+    bookkeeping and 4 FP64 ops per 8 samples; Kahan: 8 FP32 ops), loop (3).
     Wide multiplies (32x32->64) also count on their own pipe: 20 per Philox
-    call plus one per dimension.
+    call plus one per dimension.  The FP64 path: fp64_ops_per_sample.
     """
-    per_dim_f = {"gauss_sym": 2, "genz_osc": 1, "genz_gauss": 3, "genz_prod": 4,
+    per_dim_f = {"gauss_sym": 1, "genz_osc": 1, "genz_gauss": 2, "genz_prod": 3,
                  "genz_corner": 1, "sum": 1, "const": 0, "lo": 0}[family]
     finish = {"gauss_sym": 2, "genz_osc": 6, "genz_gauss": 2, "genz_prod": 1,
               "genz_corner": 3, "sum": 0, "const": 0, "lo": 20}[family]
@@ -81,7 +82,7 @@ def ops_per_sample(family: str, d: int, precision: str):
             "genz_corner": 2, "sum": 0, "const": 0, "lo": 2}[family]
     calls = math.ceil(d / 4)
     philox = 40 * calls
-    per_dim = (10 + per_dim_f) * d + d // 4
+    per_dim = (9 + per_dim_f) * d + d // 4
     fp64 = 0
     hist = 5
     if precision == "fp32_kahan":
@@ -91,10 +92,31 @@ def ops_per_sample(family: str, d: int, precision: str):
         fp64 = 0.5
     else:
         acc = 3
-        fp64 = 3
         hist = 0
+        fp64 = fp64_ops_per_sample(family, d)
     total = philox + per_dim + finish + 2 + 2 + hist + acc + 3
     return {"total": total, "fp64": fp64, "mufu": mufu, "mulwide": 20 * calls + d}
+
+
+# Cost of one call of an FP64 library function in DFMA issue slots of the
+# FP64 pipe: its measured cycles per warp instruction over a DFMA's (76),
+# from paper_2010_09341_gb300/calib/pipe_costs.cu on one GB300.
+FP64_CALL_DFMA = {"exp2": 16.0, "cos": 16.0, "log2": 16.0, "rcp": 8.0}
+
+
+def fp64_ops_per_sample(family: str, d: int) -> float:
+    """FP64-pipe operations of one sample of the FP64 path (VEGAS_FP64): per
+    dimension the map FMA, the Jacobian multiply and the histogram add (the
+    shared FP64 atomic's add), plus the integrand's per-dimension ops; per
+    sample v = J f, v^2 and the sums of v and v^2 (4), and the integrand's
+    finish, library calls at their measured DFMA-equivalent cost."""
+    per_dim_f = {"gauss_sym": 1, "genz_osc": 1, "genz_gauss": 2, "genz_prod": 3,
+                 "genz_corner": 1, "sum": 1, "const": 0, "lo": 0}[family]
+    c = FP64_CALL_DFMA
+    finish = {"gauss_sym": 1 + c["exp2"], "genz_osc": c["cos"], "genz_gauss": 1 + c["exp2"],
+              "genz_prod": c["rcp"], "genz_corner": 1 + c["log2"] + c["exp2"], "sum": 0, "const": 0,
+              "lo": 14 + 2 * c["rcp"]}[family]
+    return (3 + per_dim_f) * d + 4 + finish
 
 
 def roofline_samples_per_s(ops, sms: int, clk_hz: float) -> dict:
@@ -108,7 +130,7 @@ def roofline_samples_per_s(ops, sms: int, clk_hz: float) -> dict:
     Half-rate integer operations (three-input logic, 32-bit multiply-add:
     2 cycles measured) are charged one slot, so the bound is optimistic for
     them.  The other pipes bound separately: FP64 at the nominal 1.25
-    TFLOP/s, MUFU 32 lanes/clk/SM.
+    TFLOP/s (2 FMA lanes/clk/SM), MUFU 32 lanes/clk/SM.
     """
     fp64_per_sm_clk = FP64_TFLOPS_NOMINAL * 1e12 / 2.0 / (sms * clk_hz)
     cycles = (ops["total"] - ops.get("mulwide", 0)) + MULWIDE_ISSUE_CYCLES * ops.get("mulwide", 0)
@@ -266,13 +288,15 @@ def _time_single(V, torch, family, params, d, N, n, prec, iters, warm=2, iid=0):
     k_ms = sum(kms) / max(1, len(kms))
     out = {"samples_per_s": n * iters / (ms / 1e3), "ms_per_iter": ms / iters,
            "kernel_ms": k_ms, "I": res["I"], "sigma": res["sigma"]}
-    if prec != "fp64":
-        # the sampling kernel against the issue bound of its family and d (the FP64
-        # path's bound is its FP64 pipe, which this operation model does not count)
-        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
-        bound = min(roofline_samples_per_s(ops_per_sample(family, d, prec), sms, 2070e6).values())
-        out["roofline"] = {"bound": "alu", "roofline_samples_per_s": bound,
-                           "frac": (n / (k_ms / 1e3)) / bound}
+    # the sampling kernel against the tightest bound of its family, d and
+    # precision: instruction issue in the FP32 modes, the FP64 pipe in FP64
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    bounds = roofline_samples_per_s(ops_per_sample(family, d, prec), sms, 2070e6)
+    pipe = min(bounds, key=bounds.get)
+    out["roofline"] = {"bound": "alu" if pipe == "issue" else pipe, "pipe": pipe,
+                       "roofline_samples_per_s": bounds[pipe], "frac": (n / (k_ms / 1e3)) / bounds[pipe]}
+    if prec == "fp64":
+        out["roofline"]["fp64_ops_per_sample"] = fp64_ops_per_sample(family, d)
     return out
 
 
@@ -493,7 +517,7 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the other workloads")
-    ap.add_argument("--only", choices=["batched", "serving", "lo", "config1", "strat", "user", "lo_pdf"],
+    ap.add_argument("--only", choices=["batched", "serving", "lo", "config1", "fp64", "strat", "user", "lo_pdf"],
                     default=None,
                     help="run just one of the other workloads and print its JSON (for profiling)")
     args = ap.parse_args()
@@ -519,6 +543,9 @@ def main():
         elif args.only == "config1":
             out = _time_single(V, torch, "gauss_sym", W.gauss_sym_params(0.1), 4, 50, 100_000, "fp64",
                                args.steps, warm=args.warmup)
+        elif args.only == "fp64":
+            out = {fam: _time_single(V, torch, fam, p, D, NBINS, NEVENTS, "fp64", args.steps, warm=args.warmup)
+                   for fam, p in _integrals()}
         elif args.only == "strat":
             out = {fam: _time_strat(V, torch, fam, p, D, NBINS, NEVENTS, PRECISION)
                    for fam, p in _integrals()}

@@ -22,7 +22,7 @@ constexpr int kThreads = 1024;
 enum Kind : int {
     K_FFMA, K_IADD, K_LOP3, K_IMAD, K_MULHI, K_MULWIDE_XOR, K_MULWIDE_XOR_2FFMA, K_FFMA_LOP3,
     K_ATOMS_U32, K_ATOMS_F32, K_ATOMS_F64, K_DFMA, K_EX2, K_EXP64, K_I2F, K_I2F_2FFMA, K_SHF,
-    K_ATOMS_U64, K_MATCH_ANY, K_COUNT
+    K_ATOMS_U64, K_MATCH_ANY, K_COS64, K_LOG2_64, K_EXP2_64, K_RCP64, K_COUNT
 };
 
 template <int V>
@@ -86,6 +86,14 @@ __global__ void __launch_bounds__(kThreads) chains(unsigned long long *cycles, u
                 atomicAdd(&cells_d[c * 32 + lane], g[c]);
             } else if (V == K_EXP64) {
                 g[c] = exp(-g[c]);  // stays in (0.3, 1]: converges to 0.567
+            } else if (V == K_EXP2_64) {
+                g[c] = exp2(-g[c]);  // stays in (0.5, 1]: converges to 0.64
+            } else if (V == K_COS64) {
+                g[c] = cos(g[c]);   // stays in [cos 1, 1]: converges to 0.739
+            } else if (V == K_RCP64) {
+                g[c] = 1.0 / (g[c] + 1.0);  // converges to 0.618
+            } else if (V == K_LOG2_64) {
+                g[c] = 1.0 + log2(g[c] + 1.0);  // stays in [1, 2]: converges to 2
             } else if (V == K_DFMA) {
                 asm volatile("fma.rn.f64 %0, %0, 0d3FEFFFFFDE7210BE, 0d3E7AD7F29ABCAF48;" : "+d"(g[c]));
             } else if (V == K_EX2) {
@@ -159,6 +167,10 @@ int main() {
         {"shf.r (funnel shift)", 1, chains<K_SHF>},
         {"shared atomic add u64", 1, chains<K_ATOMS_U64>},
         {"match.any.sync.b32", 2, chains<K_MATCH_ANY>},
+        {"exp2 (double, one call)", 1, chains<K_EXP2_64>},
+        {"cos (double, one call)", 1, chains<K_COS64>},
+        {"log2 (double, one call + 2 dadd)", 1, chains<K_LOG2_64>},
+        {"1/x (double, one division + dadd)", 1, chains<K_RCP64>},
     };
     unsigned long long *h = new unsigned long long[blocks];
     int rc = 0;

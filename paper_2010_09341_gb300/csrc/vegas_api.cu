@@ -36,7 +36,7 @@ constexpr size_t kAlign = 256;
 inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-    size_t edges, table, acc, last, nonfinite, hscale, jmul, iters, comb, cstate, q, total;
+    size_t edges, table, acc, last, nonfinite, hscale, jmul, iters, comb, cstate, q, center, total;
 };
 
 Layout layout_for(int d, int N) {
@@ -64,6 +64,8 @@ Layout layout_for(int d, int N) {
     off = align_up(off + sizeof(CombState));
     L.q = off;                                 // stratified: running and last sum of m2
     off = align_up(off + 2 * sizeof(double));
+    L.center = off;                            // the table's d centres (table_center)
+    off = align_up(off + sizeof(double) * d);
     L.total = off;
     return L;
 }
@@ -247,6 +249,7 @@ struct vegas_ctx {
     IterRec *iters;
     CombRec *comb;
     CombState *cstate;
+    double *center;   // d sampling-table centres (table_center)
     int t;          // Philox iteration word of the next iteration
     int n_done;     // iterations recorded in iters[]
     FamilyConsts fc;
@@ -395,6 +398,7 @@ static vegas_status create_impl(const vegas_config *cfg, const vegas_integrand *
     c->comb = reinterpret_cast<CombRec *>(c->ws + L.comb);
     c->cstate = reinterpret_cast<CombState *>(c->ws + L.cstate);
     c->q = reinterpret_cast<double *>(c->ws + L.q);
+    c->center = reinterpret_cast<double *>(c->ws + L.center);
     c->t = 0;
     c->n_done = 0;
     c->fc = fc;
@@ -429,7 +433,8 @@ static vegas_status create_impl(const vegas_config *cfg, const vegas_integrand *
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(c->jmul, kOnes, sizeof(kOnes), cudaMemcpyHostToDevice, c->stream);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(c->comb, 0, (L.cstate + sizeof(CombState)) - L.comb, c->stream);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(c->q, 0, 2 * sizeof(double), c->stream);
-    if (ce == cudaSuccess) ce = launch_table_from_edges(c->edges, c->table, mode, d, N, c->stream);
+    if (ce == cudaSuccess) ce = launch_set_centers(c->center, itg->family, d, fc, c->stream);
+    if (ce == cudaSuccess) ce = launch_table_from_edges(c->edges, c->table, c->center, mode, d, N, c->stream);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
     if (ce != cudaSuccess) {
         set_error("vegas_create", ce);
@@ -504,6 +509,7 @@ static void fill_strata(SampleArgs &a, const Strata &st, int d, double *q) {
 static SampleArgs make_args(const vegas_ctx *c, long long s_begin, long long n, int t) {
     SampleArgs a{};
     a.table = c->table;
+    a.center = c->center;
     a.acc = c->acc;
     a.n_nonfinite = c->nonfinite;
     a.s_begin = s_begin;
@@ -668,6 +674,7 @@ static RefineJob refine_job(vegas_ctx *c) {
     r.f = finalize_args(c);
     r.edges = c->edges;
     r.table = c->table;
+    r.center = c->center;
     r.mode = c->mode;
     r.d = c->cfg.n_dim;
     r.N = c->cfg.n_bins;
@@ -728,7 +735,7 @@ vegas_status vegas_finalize(vegas_ctx *c, vegas_iter_result *out) {
 vegas_status vegas_refine(vegas_ctx *c) {
     if (!c) return VEGAS_EINVAL;
     if (c->n_done == 0) return VEGAS_OK;  // nothing sampled yet: keep the grid
-    VEGAS_CK(launch_refine(c->last, c->edges, c->table, c->mode, c->cfg.n_dim, c->cfg.n_bins,
+    VEGAS_CK(launch_refine(c->last, c->edges, c->table, c->center, c->mode, c->cfg.n_dim, c->cfg.n_bins,
                            c->cfg.alpha, c->cfg.smooth, c->stream));
     return VEGAS_OK;
 }
@@ -801,7 +808,7 @@ vegas_status vegas_set_grid(vegas_ctx *c, const double *e) {
     }
     VEGAS_CK(cudaMemcpyAsync(c->edges, e, sizeof(double) * d * (N + 1), cudaMemcpyHostToDevice,
                              c->stream));
-    VEGAS_CK(launch_table_from_edges(c->edges, c->table, c->mode, d, N, c->stream));
+    VEGAS_CK(launch_table_from_edges(c->edges, c->table, c->center, c->mode, d, N, c->stream));
     VEGAS_CK(cudaStreamSynchronize(c->stream));
     return VEGAS_OK;
 }
@@ -1065,7 +1072,7 @@ vegas_status vegas_import_state(vegas_ctx *c, const void *buf, size_t size) {
     VEGAS_CK(cudaMemcpyAsync(c->hscale, &h.hscale, sizeof(float), cudaMemcpyHostToDevice, c->stream));
     VEGAS_CK(cudaMemcpyAsync(c->jmul + (h.n_done & 1), &h.jmul, sizeof(double), cudaMemcpyHostToDevice,
                              c->stream));
-    VEGAS_CK(launch_table_from_edges(c->edges, c->table, c->mode, d, N, c->stream));
+    VEGAS_CK(launch_table_from_edges(c->edges, c->table, c->center, c->mode, d, N, c->stream));
     VEGAS_CK(cudaStreamSynchronize(c->stream));
     c->t = h.t;
     c->n_done = h.n_done;
@@ -1125,7 +1132,8 @@ constexpr size_t kNaAcc = 0;                                                    
 constexpr size_t kNaNonfinite = (sizeof(double) * (2 + kNoallocMaxCells) + 255) / 256 * 256;
 constexpr size_t kNaHscale = kNaNonfinite + kAlign;                             // float, kept 0
 constexpr size_t kNaTable = kNaHscale + kAlign;                                 // cells x 16 bytes
-constexpr size_t kNaBytes = kNaTable + 16 * static_cast<size_t>(kNoallocMaxCells);
+constexpr size_t kNaCenter = kNaTable + 16 * static_cast<size_t>(kNoallocMaxCells);  // 32 doubles
+constexpr size_t kNaBytes = kNaCenter + sizeof(double) * VEGAS_MAX_DIM;
 
 // Shared by every call in the process, on every device that loads the library.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
@@ -1208,15 +1216,18 @@ extern "C" vegas_status vegas_iterate_noalloc(const vegas_config *cfg, const veg
     auto *nonfinite = reinterpret_cast<unsigned long long *>(scratch + kNaNonfinite);
     float *hscale = reinterpret_cast<float *>(scratch + kNaHscale);
     void *table = scratch + kNaTable;
+    double *center = reinterpret_cast<double *>(scratch + kNaCenter);
     // the array keeps the previous call's contents: clear the accumulators,
     // the non-finite counter and the histogram scale (0: FP32 cells)
     VEGAS_CK(cudaMemsetAsync(scratch, 0, kNaTable, s));
-    VEGAS_CK(launch_table_from_edges(dev_edges, table, mode, d, N, s));
+    VEGAS_CK(launch_set_centers(center, itg->family, d, fc, s));
+    VEGAS_CK(launch_table_from_edges(dev_edges, table, center, mode, d, N, s));
 
     const double scale = std::ldexp(1.0, -static_cast<int>(std::lround(std::log2(fmax))));
     const double Nd = static_cast<double>(N);
     SampleArgs a{};
     a.table = table;
+    a.center = center;
     a.acc = acc;
     a.n_nonfinite = nonfinite;
     a.d = d;

@@ -101,14 +101,14 @@ cudaError_t launch_finalize(const FinalizeArgs &f, cudaStream_t stream) {
 
 // --------------------------------------------------------------- refine
 __global__ void __launch_bounds__(kRefineThreads)
-refine_kernel(const double *last, double *edges, void *table, int mode, int N, double alpha,
-              int smooth) {
+refine_kernel(const double *last, double *edges, void *table, const double *center, int mode, int N,
+              double alpha, int smooth) {
     extern __shared__ double rs[];
     const int j = blockIdx.x;
     const size_t entry = mode == ACC_F64 ? sizeof(double2) : sizeof(float2);
     refine_block(last + 2 + static_cast<size_t>(j) * N, edges + static_cast<size_t>(j) * (N + 1),
                  static_cast<char *>(table) + entry * static_cast<size_t>(j) * N, mode, N, alpha,
-                 smooth, rs);
+                 smooth, center[j], rs);
 }
 
 // Finalize and refinement of one iteration of each of js.n integrals in one
@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(kRefineThreads) finalize_refine_kernel(const R
     const size_t entry = r.mode == ACC_F64 ? sizeof(double2) : sizeof(float2);
     refine_block(r.f.acc + 2 + static_cast<size_t>(j) * N, r.edges + static_cast<size_t>(j) * (N + 1),
                  static_cast<char *>(r.table) + entry * static_cast<size_t>(j) * N, r.mode, N, r.alpha,
-                 r.smooth, rs);
+                 r.smooth, r.center[j], rs);
     __syncthreads();
     move_rows(r.f, 2 + j * N, 2 + (j + 1) * N);
 }
@@ -173,25 +173,37 @@ cudaError_t launch_programmatic(const void *fn, dim3 grid, dim3 block, void **pa
     return cudaLaunchKernelExC(&cfg, fn, params);
 }
 
-cudaError_t launch_refine(const double *last, double *edges, void *table, int mode, int d, int N,
-                          double alpha, int smooth, cudaStream_t stream) {
+cudaError_t launch_refine(const double *last, double *edges, void *table, const double *center, int mode,
+                          int d, int N, double alpha, int smooth, cudaStream_t stream) {
     const size_t smem = static_cast<size_t>(4 * N + 2) * sizeof(double);
-    refine_kernel<<<d, kRefineThreads, smem, stream>>>(last, edges, table, mode, N, alpha, smooth);
+    refine_kernel<<<d, kRefineThreads, smem, stream>>>(last, edges, table, center, mode, N, alpha, smooth);
     return cudaGetLastError();
 }
 
-__global__ void table_kernel(const double *edges, void *table, int mode, int d, int N) {
+__global__ void table_kernel(const double *edges, void *table, const double *center, int mode, int d, int N) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= d * N) return;
     const int j = idx / N, k = idx - j * N;
     const double *e = edges + static_cast<size_t>(j) * (N + 1);
-    store_table(table, mode, idx, e[k], e[k + 1] - e[k]);
+    store_table(table, mode, idx, e[k], e[k + 1] - e[k], center[j]);
 }
 
-cudaError_t launch_table_from_edges(const double *edges, void *table, int mode, int d, int N,
-                                    cudaStream_t stream) {
+cudaError_t launch_table_from_edges(const double *edges, void *table, const double *center, int mode, int d,
+                                    int N, cudaStream_t stream) {
     const int total = d * N;
-    table_kernel<<<(total + 255) / 256, 256, 0, stream>>>(edges, table, mode, d, N);
+    table_kernel<<<(total + 255) / 256, 256, 0, stream>>>(edges, table, center, mode, d, N);
+    return cudaGetLastError();
+}
+
+__global__ void centers_kernel(double *dst, int d, const TableCenters c) {
+    const int j = threadIdx.x;
+    if (j < d) dst[j] = c.c[j];
+}
+
+cudaError_t launch_set_centers(double *dst, int family, int d, const FamConsts<double> &fc, cudaStream_t stream) {
+    TableCenters c;
+    for (int j = 0; j < 32; ++j) c.c[j] = j < d ? table_center(family, fc, j) : 0.0;
+    centers_kernel<<<1, 32, 0, stream>>>(dst, d, c);
     return cudaGetLastError();
 }
 

@@ -120,7 +120,7 @@ batch_refine_kernel(const BatchArgs ba) {
         const size_t entry = ba.mode == ACC_F64 ? sizeof(double2) : sizeof(float2);
         refine_block(sd.last + 2 + static_cast<size_t>(j) * N, sd.edges + static_cast<size_t>(j) * (N + 1),
                      static_cast<char *>(sd.table) + entry * static_cast<size_t>(j) * N, ba.mode, N,
-                     sd.alpha, sd.smooth, rs);
+                     sd.alpha, sd.smooth, sd.center[j], rs);
     }
 }
 
@@ -186,7 +186,8 @@ BatchLayout batch_layout(int max_slots) {
 
 size_t slot_pool_bytes(int d, int N) {
     const size_t cells = static_cast<size_t>(d) * N;
-    return up(sizeof(double) * d * (N + 1)) + up(16 * cells) + 2 * up(sizeof(double) * (2 + cells));
+    return up(sizeof(double) * d * (N + 1)) + up(16 * cells) + 2 * up(sizeof(double) * (2 + cells)) +
+           up(sizeof(double) * d);  // the table centres
 }
 
 // First-fit allocator over byte ranges of the device pool (host bookkeeping).
@@ -579,6 +580,7 @@ vegas_status vegas_batch_add(vegas_batch *b, const vegas_config *cfg, const vega
     sd.table = base + up(sizeof(double) * d * (N + 1));
     sd.acc = reinterpret_cast<double *>(static_cast<char *>(sd.table) + up(16 * cells));
     sd.last = reinterpret_cast<double *>(reinterpret_cast<char *>(sd.acc) + up(sizeof(double) * (2 + cells)));
+    sd.center = reinterpret_cast<double *>(reinterpret_cast<char *>(sd.last) + up(sizeof(double) * (2 + cells)));
     std::vector<double> e(static_cast<size_t>(d) * (N + 1));
     for (int j = 0; j < d; ++j)
         for (int k = 0; k <= N; ++k) e[static_cast<size_t>(j) * (N + 1) + k] = static_cast<double>(k) / N;
@@ -587,7 +589,8 @@ vegas_status vegas_batch_add(vegas_batch *b, const vegas_config *cfg, const vega
     if (ce == cudaSuccess)
         ce = cudaMemcpyAsync(sd.edges, e.data(), e.size() * sizeof(double), cudaMemcpyHostToDevice, b->stream);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(sd.acc, 0, 2 * up(sizeof(double) * (2 + cells)), b->stream);
-    if (ce == cudaSuccess) ce = launch_table_from_edges(sd.edges, sd.table, b->mode, d, N, b->stream);
+    if (ce == cudaSuccess) ce = launch_set_centers(sd.center, itg->family, d, fc, b->stream);
+    if (ce == cudaSuccess) ce = launch_table_from_edges(sd.edges, sd.table, sd.center, b->mode, d, N, b->stream);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(b->stream);  // host buffers go out of scope
     if (ce != cudaSuccess) {
         b->pool.release(off, need);

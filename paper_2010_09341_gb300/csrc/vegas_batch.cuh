@@ -30,6 +30,7 @@ struct SlotDev {
     void *table;              // d x N entries of the batch's mode
     double *acc;              // 2 + d N (scaled), zeroed after each finalize
     double *last;             // 2 + d N (unscaled) of the last iteration
+    double *center;           // d sampling-table centres (table_center)
     // updated by the kernels
     unsigned long long nonfinite;
     float hscale;

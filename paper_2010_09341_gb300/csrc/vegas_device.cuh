@@ -157,6 +157,14 @@ template <class T> struct FamConsts {
 };
 using FamilyConsts = FamConsts<double>;
 
+// Centre of dimension j's sampling-table coordinate (store_table): 1/2 for
+// GAUSS_SYM, the peak position q_j for GENZ_GAUSS and GENZ_PROD, else 0.
+__host__ __device__ inline double table_center(int family, const FamConsts<double> &fc, int j) {
+    if (family == F_GAUSS_SYM) return 0.5;
+    if (family == F_GENZ_GAUSS || family == F_GENZ_PROD) return fc.q[j];
+    return 0.0;
+}
+
 // Precision-typed helpers: the float versions must never promote to FP64
 // (GB300's FP64 pipe issues 2 operations per clock per SM).
 __device__ __forceinline__ float ffma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
@@ -256,11 +264,16 @@ __device__ __forceinline__ T grid_xg(const T *tbl, int pitch, int iu, const Cubi
 // coordinate is produced) and a final step.  Normalisation constants that do
 // not depend on x (the Gaussian's (a sqrt(pi))^-d, the product-peak's scale)
 // are folded into the initial weight on the host, so the kernels return f up
-// to that factor.  The coordinate passed in is X = S x with S = Prec<T>::kXS
+// to that factor.  The coordinate passed in is X = S (x - c) with S = Prec<T>::kXS
 // (2^32 in FP32, 1 in FP64); the FP32 constants are prepared for it on the
 // host (p_j / S, q_j S, s0 / S^2 where the formula below has them), and a
 // power of S left over as a factor of f (SUM: S; LO: 1/S; LO_PDF: 1/S^2) is
 // divided out of the initial weight.
+//
+// GAUSS_SYM, GENZ_GAUSS and GENZ_PROD take their coordinate relative to a
+// centre (1/2; the peak positions w_j = q_j) that the sampling table already
+// holds (table_center), so the subtraction costs nothing per sample; the
+// formulas below show it.
 //
 //   CONST        acc unused                        f = 1
 //   SUM          acc += x                          f = acc
@@ -292,17 +305,16 @@ template <int FAM, class T, int MAXD> struct Integrand {
         if (FAM == F_SUM) {
             acc += x;
         } else if (FAM == F_GAUSS_SYM) {
-            const T t = x - T(0.5) * Prec<T>::kXS;
-            acc = ffma(t, t, acc);
+            acc = ffma(x, x, acc);  // x - 1/2 (table centre)
         } else if (FAM == F_GENZ_OSC || FAM == F_GENZ_CORNER) {
             acc = ffma(fc.p[j], x, acc);
         } else if (FAM == F_GENZ_GAUSS) {
-            const T t = fc.p[j] * (x - fc.q[j]);
+            const T t = fc.p[j] * x;  // x - q_j (table centre)
             acc = ffma(t, t, acc);
         } else if (FAM == F_GENZ_PROD) {
             // (c^-2 + (x-w)^2) c^2 = 1 + (c (x-w))^2; the c^2 factors are in
             // the initial weight.  Multiply the denominators, invert once.
-            const T t = fc.p[j] * (x - fc.q[j]);
+            const T t = fc.p[j] * x;  // x - q_j (table centre)
             acc *= ffma(t, t, T(1));
         } else if (FAM == F_LO || FAM == F_LO_PDF) {
             if (j == 0) x0 = x;

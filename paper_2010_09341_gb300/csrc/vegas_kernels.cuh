@@ -141,6 +141,7 @@ struct RefineJob {
     FinalizeArgs f;
     double *edges;
     void *table;
+    const double *center;   // d table centres (table_center)
     int mode, d, N, smooth;
     double alpha;
 };
@@ -158,13 +159,21 @@ cudaError_t launch_programmatic(const void *fn, dim3 grid, dim3 block, void **pa
                                 cudaStream_t stream);
 
 // Refine every dimension from the histograms in last[2..] and write the new
-// FP64 edges and the sampling table of the given mode.
-cudaError_t launch_refine(const double *last, double *edges, void *table, int mode, int d, int N,
-                          double alpha, int smooth, cudaStream_t stream);
+// FP64 edges and the sampling table of the given mode (about the d centres).
+cudaError_t launch_refine(const double *last, double *edges, void *table, const double *center, int mode,
+                          int d, int N, double alpha, int smooth, cudaStream_t stream);
 
-// Build the sampling table of `mode` from FP64 edges.
-cudaError_t launch_table_from_edges(const double *edges, void *table, int mode, int d, int N,
-                                    cudaStream_t stream);
+// Build the sampling table of `mode` from FP64 edges, about the d centres
+// (device array, table_center).
+cudaError_t launch_table_from_edges(const double *edges, void *table, const double *center, int mode, int d,
+                                    int N, cudaStream_t stream);
+
+// The d table centres of a family (table_center), by value.
+struct TableCenters {
+    double c[32];
+};
+// Write the family's d table centres to the device array dst (no host copy).
+cudaError_t launch_set_centers(double *dst, int family, int d, const FamConsts<double> &fc, cudaStream_t stream);
 
 // Per-sample trace on the given table (same device arithmetic as sampling).
 cudaError_t launch_trace(const SampleArgs &a, int fam, int mode, double inv_scale, int32_t *bins,

@@ -13,22 +13,24 @@ namespace vegas {
 //            interpolated linearly inside the old bin; zero-weight bins are
 //            skipped and an edge on an old edge takes the lower bin.
 // A dimension whose weights sum to zero keeps its grid.
-// Sampling-table entry of the bin [e, e + w) (the coordinate forms of
-// Prec<T>::coord): FP64 (e - w, w), x = (e - w) + w m with m in [1, 2);
-// FP32 (2^32 e, w), X = 2^32 x = 2^32 e + w float(lo).
-__device__ __forceinline__ void store_table(void *table, int mode, int idx, double e, double w) {
-    if (mode == ACC_F64) reinterpret_cast<double2 *>(table)[idx] = double2{e - w, w};
-    else reinterpret_cast<float2 *>(table)[idx] = float2{static_cast<float>(e * 4294967296.0), static_cast<float>(w)};
+// Sampling-table entry of the bin [e, e + w) of a dimension whose integrand
+// takes its coordinate relative to the centre c (Prec<T>::coord gives x - c;
+// c = 0 for most families): FP64 (e - w - c, w), x - c = (e - w - c) + w m with
+// m in [1, 2); FP32 (2^32 (e - c), w), 2^32 (x - c) = 2^32 (e - c) + w float(lo).
+__device__ __forceinline__ void store_table(void *table, int mode, int idx, double e, double w, double c) {
+    if (mode == ACC_F64) reinterpret_cast<double2 *>(table)[idx] = double2{(e - c) - w, w};
+    else reinterpret_cast<float2 *>(table)[idx] = float2{static_cast<float>((e - c) * 4294967296.0), static_cast<float>(w)};
 }
 
 constexpr int kRefineThreads = 128;
 
 // Refines one dimension with the whole block (blockDim.x == kRefineThreads):
 // h = its N histogram values, e = its N+1 FP64 edges (updated in place),
-// table_row = its N sampling-table entries of `mode`; rs = 4N+2 doubles of
-// shared memory.  A dimension whose weights sum to zero keeps its grid.
+// table_row = its N sampling-table entries of `mode` about the centre c
+// (store_table); rs = 4N+2 doubles of shared memory.  A dimension whose
+// weights sum to zero keeps its grid.
 __device__ __forceinline__ void refine_block(const double *h, double *e, void *table_row, int mode, int N,
-                             double alpha, int smooth, double *rs) {
+                             double alpha, int smooth, double c, double *rs) {
     double *eo = rs;            // old edges, N+1
     double *rho = rs + (N + 1); // compressed weights, N
     double *cum = rho + N;      // inclusive running sum, N
@@ -130,7 +132,7 @@ __device__ __forceinline__ void refine_block(const double *h, double *e, void *t
     }
     __syncthreads();
     for (int k = tid; k <= N; k += blockDim.x) e[k] = en[k];
-    for (int k = tid; k < N; k += blockDim.x) store_table(table_row, mode, k, en[k], en[k + 1] - en[k]);
+    for (int k = tid; k < N; k += blockDim.x) store_table(table_row, mode, k, en[k], en[k + 1] - en[k], c);
 }
 
 

@@ -46,7 +46,8 @@ __device__ __forceinline__ uint32_t strat_word(uint32_t r, uint32_t h, uint32_t 
 }
 
 struct SampleArgs {
-    const void *table;        // [d][N] entries: double2 (e - w, w) or float2 (2^32 e, w)
+    const void *table;        // [d][N] entries about the centres (store_table): double2 or float2
+    const double *center;     // the d table centres (table_center; device)
     double *acc;              // [2 + d N] FP64 accumulators: S1, S2, histograms
     unsigned long long *n_nonfinite;
     long long s_begin;        // first sample index of this launch

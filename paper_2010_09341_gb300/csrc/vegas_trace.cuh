@@ -79,8 +79,9 @@ __global__ void trace_kernel(const SampleArgs a, double inv_scale, int32_t *bins
                         J *= ent.y;
                         if (sizeof(T) == 4 && (j & 3) == 3) J *= n4;
                         fam.dim(j, x, fc);
-                        // the coordinate itself (FP32 works in 2^32 x; exact)
-                        const double xd = static_cast<double>(x) * Prec<T>::kInvXS;
+                        // the coordinate itself (FP32 works in 2^32 (x - c), exactly
+                        // scaled; the table centre c added back in FP64)
+                        const double xd = static_cast<double>(x) * Prec<T>::kInvXS + a.center[j];
                         if (j == h.obs) xo = xd;
                         if (j == 0) x0 = xd;
                         if (j == 1) x1 = xd;

@@ -12,27 +12,44 @@ import bench
 
 def test_counted_operations_of_the_headline_integrals():
     """The counts the roofline is built on, at d = 8 with FP32 sampling and FP64
-    sums: 196.5 (Gaussian) and 192.5 (oscillatory) operations, of which 48 are
-    32x32->64 multiplies (2 Philox calls x 20, plus one per dimension)."""
+    sums: 180.5 (Gaussian) and 184.5 (oscillatory) operations, of which 48 are
+    32x32->64 multiplies (2 Philox calls x 20, plus one per dimension).  The
+    Gaussian's (x - 1/2)^2 is one FMA per dimension (its centre is in the
+    sampling table), the oscillatory sum one FMA."""
     g = bench.ops_per_sample("gauss_sym", 8, "fp32_acc64")
     o = bench.ops_per_sample("genz_osc", 8, "fp32_acc64")
-    assert g["total"] == 196.5 and o["total"] == 192.5
+    assert g["total"] == 180.5 and o["total"] == 184.5
     assert g["mulwide"] == o["mulwide"] == 48
     assert g["fp64"] == 0.5
-    # one more Philox call per 4 dimensions, 10 + per-dimension integrand ops per dimension
+    # one more Philox call per 4 dimensions, 9 + per-dimension integrand ops per dimension
     g9 = bench.ops_per_sample("gauss_sym", 9, "fp32_acc64")
     assert g9["mulwide"] == 60 + 9
-    assert g9["total"] - g["total"] == 40 + (10 + 2)
+    assert g9["total"] - g["total"] == 40 + (9 + 1)
 
 
 def test_issue_roofline_at_152_sms_and_2070_mhz():
-    """(196.5 - 48) + 4 x 48 = 340.5 issue cycles per sample: 152 x 2.07e9 x 128 / 340.5
-    = 118.28 G samples/s; the FP64 and MUFU bounds are far above it."""
+    """(180.5 - 48) + 4 x 48 = 324.5 issue cycles per sample: 152 x 2.07e9 x 128 / 324.5
+    = 124.11 G samples/s; the FP64 and MUFU bounds are far above it."""
     b = bench.roofline_samples_per_s(bench.ops_per_sample("gauss_sym", 8, "fp32_acc64"), 152, 2.07e9)
-    assert b["issue"] == pytest.approx(152 * 2.07e9 * 128 / 340.5, rel=1e-12)
-    assert b["issue"] == pytest.approx(118.28e9, rel=1e-4)
+    assert b["issue"] == pytest.approx(152 * 2.07e9 * 128 / 324.5, rel=1e-12)
+    assert b["issue"] == pytest.approx(124.11e9, rel=1e-4)
     assert min(b, key=b.get) == "issue"
     assert b["fp64"] > 10 * b["issue"] and b["mufu"] > 10 * b["issue"]
+
+
+def test_fp64_path_is_bound_by_its_fp64_pipe():
+    """The FP64 path at d = 8, symmetric Gaussian: per dimension the map FMA,
+    the Jacobian multiply, the histogram add and the integrand's FMA (4), per
+    sample v, v^2 and the two sums (4) and the exponential (one multiply and
+    one exp2 call at 16 DFMA-equivalents): 53 FP64 operations; at the nominal
+    1.25 TFLOP/s (0.625e12 FMA/s) 0.625e12 / 53 = 11.79 G samples/s, the
+    tightest bound."""
+    o = bench.ops_per_sample("gauss_sym", 8, "fp64")
+    assert o["fp64"] == 4 * 8 + 4 + 1 + bench.FP64_CALL_DFMA["exp2"] == 53
+    b = bench.roofline_samples_per_s(o, 152, 2.07e9)
+    assert min(b, key=b.get) == "fp64"
+    assert b["fp64"] == pytest.approx(152 * 2.07e9 * (1.25e12 / 2 / (152 * 2.07e9)) / 53, rel=1e-12)
+    assert b["fp64"] == pytest.approx(11.79e9, rel=1e-3)
 
 
 def _copy_tree(tmp_path):
