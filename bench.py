@@ -101,7 +101,7 @@ def ops_per_sample(family: str, d: int, precision: str):
 # Cost of one call of an FP64 library function in DFMA issue slots of the
 # FP64 pipe: its measured cycles per warp instruction over a DFMA's (76),
 # from paper_2010_09341_gb300/calib/pipe_costs.cu on one GB300.
-FP64_CALL_DFMA = {"exp2": 16.0, "cos": 16.0, "log2": 16.0, "rcp": 8.0}
+FP64_CALL_DFMA = {"exp2": 17.0, "cos": 17.5, "log2": 30.4, "rcp": 4.7}
 
 
 def fp64_ops_per_sample(family: str, d: int) -> float:
