@@ -34,7 +34,19 @@ UNIT = "samples/s"
 D, NBINS, NEVENTS, ALPHA = 8, 50, 10_000_000, 1.5
 PRECISION = "fp32_acc64"
 PROFILE_EVERY = 4             # timed steps per step with kernel events
-WORKLOAD = "d=8 Gaussian a=0.1 + d=8 Genz oscillatory (c~U(0,1) seed 1), 50 bins, 1e7 samples/iter each, FP32 sampling, FP64 accumulators"
+WORKLOAD = "d=8 Gaussian a=0.1 + d=8 Genz oscillatory (c~U(0,1) seed 1), 50 bins, 1e7 samples/iter each"
+
+# The workload's identity, the same in both arms (the arithmetic is in "dtype").
+CONFIG = {"workload": WORKLOAD, "integrals": 2, "dims": D, "bins": NBINS, "samples_per_iteration": NEVENTS}
+
+# Serving sweep: Poisson arrival rates and requests per rate (about two
+# seconds of arrivals each, at most 1e4: 1e4 requests at 10/s would arrive
+# over 1000 s).
+SERVING_RATES = (10.0, 100.0, 1000.0, 10000.0)
+
+
+def serving_requests(rate: float) -> int:
+    return int(min(10_000, max(20, round(2.0 * rate))))
 
 # Unit counts used for the issue roofline (per SM per clock); the measured
 # costs come from paper_2010_09341_gb300/calib/pipe_costs.cu.
@@ -251,8 +263,8 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * sum(per_step) / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "parallelism": "host threads",
-                   "sample": "each step: %d samples per integral, grid uniform"
+        "config": dict(CONFIG, parallelism="host threads (%d)" % threads),
+        "method": {"step": "each step: %d samples per integral of iteration t on the uniform grid"
                    % (n_total // (2 * args.steps))},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": "%d samples over %d steps (%.1f s)"
@@ -422,8 +434,12 @@ def _time_batched(V, torch, steps=8, warm=2):
     for _ in range(warm):
         b.step()
         b.wait()
-    cands = [16384, 32768, 65536, 131072, 262144, 524288]
-    best, ms = b.autotune(cands, reps=2)
+    # launch shapes: tile samples x threads per block x shared-memory layout
+    cands = [(t, th, lay) for t in (65536, 131072, 262144, 524288) for th in (512, 640, 768)
+             for lay in (1, 2)]
+    import tempfile
+    cache = os.path.join(tempfile.mkdtemp(prefix="vegas_tune_"), "tune.json")
+    shape, ms = b.autotune_shapes(cands, reps=2, cache=cache)
     b.step()
     b.wait()
     t0 = time.perf_counter()
@@ -451,8 +467,30 @@ def _time_batched(V, torch, steps=8, warm=2):
                                   "and the graph's plan upload and result download" % sms},
             "samples_per_s": n_total * steps / dt,
             "integral_iterations_per_s": 512 * steps / dt,
-            "tile_samples": best, "autotune_ms": dict(zip([str(c) for c in cands], ms)),
+            "shape": shape, "tile_samples": shape["tile_samples"],
+            "autotune_ms": {"%d/%d/%d" % c: round(m, 4) for c, m in zip(cands, ms) if m >= 0},
             "timing": "wall clock per step incl. graph launch and result download"}
+
+
+def _serving_compare(V, rate, n_requests, target, budget):
+    """The same Poisson request stream through the batched FP32-Kahan server
+    and through the plain FP64 single-integral form (one context at a time),
+    both with real-time arrivals and the same sample schedule and stopping
+    rules: integrals/s and latency of each."""
+    from paper_2010_09341_gb300 import serve as S
+    from paper_2010_09341_gb300 import workloads as W
+    stream = W.request_stream(rate=rate, n_requests=n_requests, seed=3)
+    srv = S.Server(max_slots=1024, pool_bytes=512 << 20)
+    st32 = srv.run(S.requests_from(stream, budget=budget, target=target), realtime=True, time_limit=120)
+    srv.batch.close()
+    st64 = S.serve_single_fp64(S.requests_from(stream, budget=budget, target=target), time_limit=120)
+    return {"rate_per_s": rate, "requests": n_requests, "target_rel": target, "budget": budget,
+            "arrival": "Poisson, real time, the same stream for both",
+            "batched_fp32_kahan": st32, "fp64_single": st64,
+            "integrals_per_s_ratio": (st32["integrals_per_s"] / st64["integrals_per_s"]
+                                      if st64["integrals_per_s"] else None),
+            "converged_per_s_ratio": (st32["converged_per_s"] / st64["converged_per_s"]
+                                      if st64["converged_per_s"] else None)}
 
 
 def _serving(V, rate, n_requests, target, budget, fp64_sample=0):
@@ -557,7 +595,10 @@ def main():
             out = _time_single(V, torch, "lo", W.lo_params(), 3, 100, 100_000_000, "fp32_kahan",
                                args.steps, warm=args.warmup)
         else:
-            out = _serving(V, rate=1000.0, n_requests=1000, target=1e-4, budget=10 ** 9, fp64_sample=100)
+            out = {("rate_%d" % int(r)): _serving(V, rate=r, n_requests=serving_requests(r), target=1e-4,
+                                                  budget=10 ** 9) for r in SERVING_RATES}
+            out["poisson_batched_vs_fp64"] = _serving_compare(V, rate=100.0, n_requests=100, target=1e-4,
+                                                              budget=10 ** 9)
         print(json.dumps({"only": args.only, **out}))
         return 0
     if world > 1:
@@ -725,17 +766,24 @@ def main():
                                                       100_000_000, "fp32_kahan", 10)
         extra["config3_lo_pdf_grid_fp32_kahan"] = _time_lo_pdf(V, torch)
         extra["config4_batched"] = _time_batched(V, torch)
-        extra["config5_serving_1e-4"] = _serving(V, rate=1000.0, n_requests=1000, target=1e-4,
-                                                 budget=10 ** 9, fp64_sample=100)
+        for rate in SERVING_RATES:
+            extra["config5_serving_rate_%d" % int(rate)] = _serving(
+                V, rate=rate, n_requests=serving_requests(rate), target=1e-4, budget=10 ** 9)
+        extra["config5_poisson_batched_vs_fp64"] = _serving_compare(V, rate=100.0, n_requests=100,
+                                                                    target=1e-4, budget=10 ** 9)
 
     # ---- CPU baseline: the oracle on this host's cores (rank 0, N = 1)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         threads = os.cpu_count() or 1
         rate, n, dt = oracle_samples_per_s(args.cpu_seconds, threads)
+        rate1, n1, dt1 = oracle_samples_per_s(min(3.0, args.cpu_seconds), 1)
         cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": "%d samples (half per integral), iteration 0 on the uniform grid, %.1f s"
-               % (n, dt)}
+               % (n, dt),
+               "single_thread": {"value": rate1, "unit": UNIT, "cores": 1,
+                                 "sample": "%d samples (half per integral), iteration 0 on the "
+                                           "uniform grid, %.1f s" % (n1, dt1)}}
 
     if rank == 0:
         out = {
@@ -743,12 +791,12 @@ def main():
             "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 accumulators)",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "samples_per_step": samples_per_step,
-                       "bins": NBINS, "dims": D, "precision": PRECISION,
+            "config": dict(CONFIG, **{
+                "l2": "flushed between steps (256 MiB write outside the step events); the kernel reads no HBM inputs",
+                "parallelism": "replicas" if world > 1 else "single GPU"}),
+            "method": {"precision": PRECISION, "samples_per_step": samples_per_step,
                        "step": "one iteration of both integrals (vegas_step_many): each one's sampling launch, then one finalize + refine launch for both",
-                       "kernel_timing": "CUDA events around the sampling launches of every %dth timed step" % PROFILE_EVERY,
-                       "l2": "flushed between steps (256 MiB write outside the step events); the kernel reads no HBM inputs",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+                       "kernel_timing": "CUDA events around the sampling launches of every %dth timed step" % PROFILE_EVERY},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "extra": extra,
             "gpu_launches": args.steps * (len(ctxs) + 1),
             "clocks": clk,

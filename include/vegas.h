@@ -461,6 +461,31 @@ vegas_status vegas_batch_set_events(vegas_batch *b, int32_t slot, int64_t n_even
  * discarded, slot state is unchanged), keeps the fastest and writes the
  * average times (ms) to ms_out (may be NULL). */
 vegas_status vegas_batch_set_tile(vegas_batch *b, int32_t tile_samples);
+
+/* Launch shape of the batch's persistent sampling kernel: tile_samples (as
+ * above), threads per block (a multiple of 32 in [128, 768]; one block per SM
+ * at most 768 threads because the out-of-line samplers keep up to 80
+ * registers a thread) and the shared-memory layout (1: lane-private copies of
+ * the table and histogram cells, 2: half as many, 0: one copy; -1: the most
+ * copies that fit the largest slot, the default).  set_shape synchronises;
+ * EINVAL if a value is out of range or the layout does not fit the largest
+ * slot (the shape is then unchanged).  A later vegas_batch_add that no longer
+ * fits the requested layout falls back to the default rule; get_shape reports
+ * the layout in effect. */
+typedef struct {
+    int32_t tile_samples;
+    int32_t threads;
+    int32_t layout;
+} vegas_batch_shape;
+vegas_status vegas_batch_set_shape(vegas_batch *b, const vegas_batch_shape *shape);
+vegas_status vegas_batch_get_shape(vegas_batch *b, vegas_batch_shape *out);
+/* Autotuner over launch shapes: for each candidate that fits, times reps
+ * launches of the sampling kernel on the current slots (their sums are
+ * discarded, slot state is unchanged), writes the mean time in ms to ms_out[k]
+ * (-1 for a candidate that was skipped; ms_out may be NULL), sets the fastest
+ * shape and its index in *best.  EINVAL if no candidate fits. */
+vegas_status vegas_batch_autotune_shapes(vegas_batch *b, const vegas_batch_shape *candidates, int32_t n_candidates,
+                                         int32_t reps, float *ms_out, int32_t *best);
 vegas_status vegas_batch_autotune(vegas_batch *b, const int32_t *candidates, int32_t n_candidates,
                                   int32_t reps, float *ms_out, int32_t *best);
 vegas_status vegas_batch_info(vegas_batch *b, int32_t *n_active, size_t *pool_free, size_t *pool_largest,

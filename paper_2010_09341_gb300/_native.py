@@ -46,6 +46,10 @@ class VegasResult(ctypes.Structure):
                 ("reserved", ctypes.c_int32)]
 
 
+class VegasBatchShape(ctypes.Structure):
+    _fields_ = [("tile_samples", ctypes.c_int32), ("threads", ctypes.c_int32), ("layout", ctypes.c_int32)]
+
+
 class VegasBatchResult(ctypes.Structure):
     _fields_ = [("slot", ctypes.c_int32), ("t", ctypes.c_int32), ("it", VegasIterResult),
                 ("comb", VegasResult)]
@@ -120,6 +124,11 @@ _SIGS = {
     "vegas_batch_get_grid": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
     "vegas_batch_set_events": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int64]),
     "vegas_batch_set_tile": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "vegas_batch_set_shape": (ctypes.c_int, [_P, ctypes.POINTER(VegasBatchShape)]),
+    "vegas_batch_get_shape": (ctypes.c_int, [_P, ctypes.POINTER(VegasBatchShape)]),
+    "vegas_batch_autotune_shapes": (ctypes.c_int, [_P, ctypes.POINTER(VegasBatchShape), ctypes.c_int32,
+                                                   ctypes.c_int32, ctypes.POINTER(ctypes.c_float),
+                                                   ctypes.POINTER(ctypes.c_int32)]),
     "vegas_batch_autotune": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
                                             ctypes.c_int32, ctypes.POINTER(ctypes.c_float),
                                             ctypes.POINTER(ctypes.c_int32)]),

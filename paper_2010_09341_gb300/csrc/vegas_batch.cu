@@ -284,6 +284,7 @@ struct vegas_batch {
     int sm_count = 0;
     size_t smem_optin = 0;
     int layout = 1;        // shared-memory layout of the sampling kernel
+    int layout_req = -1;   // requested layout (vegas_batch_set_shape); -1: the most copies that fit
     const void *kfn = nullptr;
     size_t smem = 0;
     int sample_blocks = 0;
@@ -300,13 +301,14 @@ vegas_status batch_invalidate_graph(vegas_batch *b) {
     return VEGAS_OK;
 }
 
-// Choose the sampling kernel and its launch for the current largest slot.
+// Choose the sampling kernel and its launch for the current largest slot:
+// the requested layout if it fits, else the most lane-private copies that fit.
 vegas_status batch_configure(vegas_batch *b, int cells) {
     const size_t budget = b->smem_optin > 2048 ? b->smem_optin - 2048 : 0;
-    // the most lane-private copies that fit
     int layout = 1;
     if (batch_sample_smem(b->mode, layout, cells) > budget) layout = 2;
     if (batch_sample_smem(b->mode, layout, cells) > budget) layout = 0;
+    if (b->layout_req >= 0 && batch_sample_smem(b->mode, b->layout_req, cells) <= budget) layout = b->layout_req;
     size_t smem = batch_sample_smem(b->mode, layout, cells);
     if (smem > budget) return VEGAS_EINVAL;
     const void *fn = batch_sample_kernel(b->mode, layout);
@@ -745,6 +747,96 @@ vegas_status vegas_batch_autotune(vegas_batch *b, const int32_t *cand, int32_t n
     b->tile_samples = best_tile;
     *best = best_tile;
     return VEGAS_OK;
+}
+
+vegas_status vegas_batch_get_shape(vegas_batch *b, vegas_batch_shape *out) {
+    if (!b || !out) return VEGAS_EINVAL;
+    out->tile_samples = b->tile_samples;
+    out->threads = b->threads;
+    out->layout = b->layout;
+    return VEGAS_OK;
+}
+
+vegas_status vegas_batch_set_shape(vegas_batch *b, const vegas_batch_shape *shape) {
+    if (!b || !shape) return VEGAS_EINVAL;
+    const vegas_batch_shape s = *shape;
+    if (s.tile_samples < 512 || s.tile_samples > (1 << 26) || s.tile_samples % 512 || s.threads < 128 ||
+        s.threads > kBatchThreads || s.threads % 32 || s.layout < -1 || s.layout > 2)
+        return VEGAS_EINVAL;
+    vegas_status st = batch_sync(b);
+    if (st != VEGAS_OK) return st;
+    const int keep_threads = b->threads, keep_req = b->layout_req;
+    b->threads = s.threads;
+    b->layout_req = s.layout;
+    st = batch_configure(b, b->max_cells);
+    if (st == VEGAS_OK && s.layout >= 0 && b->layout != s.layout) st = VEGAS_EINVAL;  // does not fit
+    if (st != VEGAS_OK) {
+        b->threads = keep_threads;
+        b->layout_req = keep_req;
+        batch_configure(b, b->max_cells);
+        return st;
+    }
+    b->tile_samples = s.tile_samples;
+    batch_invalidate_graph(b);
+    return VEGAS_OK;
+}
+
+vegas_status vegas_batch_autotune_shapes(vegas_batch *b, const vegas_batch_shape *cand, int32_t n_cand, int32_t reps,
+                                         float *ms_out, int32_t *best) {
+    if (!b || !cand || n_cand < 1 || reps < 1 || !best) return VEGAS_EINVAL;
+    vegas_batch_shape saved;
+    vegas_batch_get_shape(b, &saved);
+    saved.layout = b->layout_req;
+    const size_t plan_bytes = b->L.results - b->L.plan;
+    cudaEvent_t e0, e1;
+    VB_CK(cudaEventCreate(&e0));
+    VB_CK(cudaEventCreate(&e1));
+    float best_ms = -1.f;
+    int best_k = -1;
+    cudaError_t e = cudaSuccess;
+    for (int c = 0; c < n_cand && e == cudaSuccess; ++c) {
+        if (ms_out) ms_out[c] = -1.f;
+        if (vegas_batch_set_shape(b, &cand[c]) != VEGAS_OK) continue;  // out of range or does not fit
+        if (batch_build_plan(b) == 0) break;
+        e = cudaMemcpyAsync(b->ws + b->L.plan, b->h_plan, plan_bytes, cudaMemcpyHostToDevice, b->stream);
+        float total = 0.f;
+        void *params[] = {&b->args};
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+            e = cudaEventRecord(e0, b->stream);
+            if (e == cudaSuccess)
+                e = cudaLaunchKernel(b->kfn, dim3(b->sample_blocks), dim3(b->threads), params, b->smem, b->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+            // the trial's sums are discarded
+            if (e == cudaSuccess)
+                e = cudaLaunchKernel(reinterpret_cast<const void *>(&batch_reset_kernel), dim3(4 * b->sm_count),
+                                     dim3(128), params, 0, b->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            total += ms;
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        if (e != cudaSuccess) break;
+        const float avg = total / reps;
+        if (ms_out) ms_out[c] = avg;
+        if (best_k < 0 || avg < best_ms) {
+            best_ms = avg;
+            best_k = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) {
+        vegas_batch_set_shape(b, &saved);
+        snprintf(g_batch_error, sizeof(g_batch_error), "autotune: %s", cudaGetErrorString(e));
+        return VEGAS_ECUDA;
+    }
+    if (best_k < 0) {
+        vegas_batch_set_shape(b, &saved);
+        return VEGAS_EINVAL;  // no candidate fits
+    }
+    *best = best_k;
+    return vegas_batch_set_shape(b, &cand[best_k]);
 }
 
 vegas_status vegas_batch_info(vegas_batch *b, int32_t *n_active, size_t *pool_free, size_t *pool_largest,

@@ -423,6 +423,7 @@ class Batch:
         self.max_slots = int(max_slots)
         self._buf = (nat.VegasBatchResult * self.max_slots)()
         self.cfgs = {}
+        self.families = {}
 
     @staticmethod
     def slot_bytes(cfg: Config) -> int:
@@ -440,11 +441,13 @@ class Batch:
         check(nat.load().vegas_batch_add(self.handle, ctypes.byref(c), ctypes.byref(itg),
                                          ctypes.byref(slot)), "vegas_batch_add")
         self.cfgs[int(slot.value)] = cfg
+        self.families[int(slot.value)] = family
         return int(slot.value)
 
     def remove(self, slot: int) -> None:
         check(nat.load().vegas_batch_remove(self.handle, int(slot)), "vegas_batch_remove")
         self.cfgs.pop(int(slot), None)
+        self.families.pop(int(slot), None)
 
     def step(self) -> None:
         check(nat.load().vegas_batch_step(self.handle), "vegas_batch_step")
@@ -500,6 +503,63 @@ class Batch:
         check(nat.load().vegas_batch_autotune(self.handle, cand, len(candidates), int(reps), ms,
                                               ctypes.byref(best)), "vegas_batch_autotune")
         return int(best.value), [float(x) for x in ms]
+
+    def shape(self) -> dict:
+        """The sampling kernel's launch shape: tile_samples, threads, layout."""
+        sh = nat.VegasBatchShape()
+        check(nat.load().vegas_batch_get_shape(self.handle, ctypes.byref(sh)), "vegas_batch_get_shape")
+        return {"tile_samples": sh.tile_samples, "threads": sh.threads, "layout": sh.layout}
+
+    def set_shape(self, tile_samples: int, threads: int, layout: int = -1) -> None:
+        sh = nat.VegasBatchShape(int(tile_samples), int(threads), int(layout))
+        check(nat.load().vegas_batch_set_shape(self.handle, ctypes.byref(sh)), "vegas_batch_set_shape")
+
+    def tune_key(self) -> str:
+        """Key of the autotuner's cache: precision, then the active slots'
+        largest bin count and dimension and their families."""
+        cfgs = list(self.cfgs.values())
+        fams = sorted(set(self.families.values()))
+        n_max = max((c.n_bins for c in cfgs), default=0)
+        d_max = max((c.n_dim for c in cfgs), default=0)
+        return "%s|N%d|d%d|%s" % (self.precision, n_max, d_max, ",".join(fams))
+
+    def autotune_shapes(self, candidates, reps: int = 3, cache: str = None):
+        """Pick the sampling kernel's launch shape (tile samples, threads per
+        block, shared-memory layout) for the current slots.  ``candidates``:
+        (tile_samples, threads, layout) triples.  With ``cache`` (a JSON file
+        path) a shape stored under this batch's tune_key() is applied without
+        measuring, and a measured one is stored.  Returns (shape dict, times
+        in ms per candidate or None when taken from the cache)."""
+        import json
+        import os
+        key = self.tune_key()
+        table = {}
+        if cache and os.path.exists(cache):
+            with open(cache) as f:
+                table = json.load(f)
+            hit = table.get(key)
+            if hit is not None:
+                try:
+                    self.set_shape(hit["tile_samples"], hit["threads"], hit["layout"])
+                    return self.shape(), None
+                except nat.VegasError:
+                    pass  # no longer fits: measure again
+        arr = (nat.VegasBatchShape * len(candidates))(
+            *[nat.VegasBatchShape(int(t), int(th), int(lay)) for t, th, lay in candidates])
+        ms = (ctypes.c_float * len(candidates))()
+        best = ctypes.c_int32()
+        check(nat.load().vegas_batch_autotune_shapes(self.handle, arr, len(candidates), int(reps), ms,
+                                                     ctypes.byref(best)), "vegas_batch_autotune_shapes")
+        shape = self.shape()
+        times = [float(x) for x in ms]
+        if cache:
+            table[key] = dict(shape, ms=times[best.value])
+            os.makedirs(os.path.dirname(os.path.abspath(cache)), exist_ok=True)
+            tmp = cache + ".tmp%d" % os.getpid()
+            with open(tmp, "w") as f:
+                json.dump(table, f, indent=1, sort_keys=True)
+            os.replace(tmp, cache)
+        return shape, times
 
     def info(self):
         n = ctypes.c_int32()

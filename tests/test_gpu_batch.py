@@ -154,3 +154,51 @@ def test_batch_mix_512():
         pulls.append(((r["I"] - exact) / r["sigma"], it.family, it.d, it.n_events))
     worst = sorted(pulls, key=lambda x: -abs(x[0]))[:5]
     assert all(abs(p[0]) < 5.0 for p in pulls), worst
+
+
+def test_shape_autotune_with_cache(tmp_path):
+    """The launch-shape autotuner (tile samples, threads per block, shared-memory
+    layout): it times the candidates that fit, skips the rest, keeps the fastest,
+    stores it under the batch's key in a JSON cache and, for a batch with the
+    same key, applies the cached shape without measuring.  A tuned batch gives
+    the same iterations as one with the default shape (summation order only)."""
+    V = native()
+    from paper_2010_09341_gb300 import _native as nat
+    cases = [("genz_gauss", 5, 50, 200_000), ("genz_corner", 9, 40, 100_003), ("genz_prod", 3, 50, 50_000)]
+
+    def make():
+        b = V.Batch(max_slots=8, pool_bytes=16 << 20, precision="fp32_kahan")
+        for k, (fam, d, N, n) in enumerate(cases):
+            b.add(_cfg(V, d, N, n, 200 + k, "fp32_kahan"), fam, params_for(fam, d, seed=k))
+        return b
+
+    default = make()
+    assert default.shape() == {"tile_samples": default.shape()["tile_samples"], "threads": 768, "layout": 1}
+    with pytest.raises(nat.VegasError):
+        default.set_shape(8192, 100, 1)        # threads not a multiple of 32
+    with pytest.raises(nat.VegasError):
+        default.set_shape(1000, 512, 1)        # tile not a multiple of 512
+    with pytest.raises(nat.VegasError):
+        default.set_shape(8192, 512, 3)        # no such layout
+    assert default.shape()["threads"] == 768
+    cands = [(65536, 512, 1), (65536, 768, 2), (131072, 640, 1), (8192, 100, 1)]
+    cache = str(tmp_path / "tune.json")
+    tuned = make()
+    shape, ms = tuned.autotune_shapes(cands, reps=1, cache=cache)
+    assert ms[3] == -1.0 and all(m > 0 for m in ms[:3])
+    best = min(range(3), key=lambda k: ms[k])
+    assert (shape["tile_samples"], shape["threads"], shape["layout"]) == cands[best]
+    again = make()
+    shape2, ms2 = again.autotune_shapes(cands, reps=1, cache=cache)
+    assert ms2 is None and shape2 == shape
+    for _ in range(3):
+        r = {}
+        for b in (default, tuned, again):
+            b.step()
+            r[id(b)] = b.wait()
+        for s in r[id(default)]:
+            Ia = r[id(default)][s]["I_t"]
+            for b in (tuned, again):
+                assert abs(r[id(b)][s]["I_t"] - Ia) <= 1e-5 * abs(Ia)
+    for b in (default, tuned, again):
+        b.close()
