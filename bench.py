@@ -472,6 +472,23 @@ def _time_batched(V, torch, steps=8, warm=2):
             "timing": "wall clock per step incl. graph launch and result download"}
 
 
+def _served_roofline(reqs, wall_s, prec="fp32_kahan"):
+    """The served work at the issue bound: the sum over completed requests of
+    their samples over the bound of their family and dimension, against the
+    wall time (a load figure below saturation, where arrivals leave the GPU
+    idle; the kernel's efficiency on the served mix at saturation)."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    roof_s = 0.0
+    for r in reqs:
+        if r.done >= 0 and r.result:
+            b = roofline_samples_per_s(ops_per_sample(r.family, r.d, prec), sms, 2070e6)
+            roof_s += r.result["samples"] / min(b.values())
+    return {"bound": "alu", "roofline_s": roof_s, "frac_of_wall": roof_s / wall_s if wall_s > 0 else None,
+            "basis": "sum over completed requests of samples / issue bound of (family, d) at %d SMs x 2070 MHz"
+                     % sms}
+
+
 def _serving_compare(V, rate, n_requests, target, budget):
     """The same Poisson request stream through the batched FP32-Kahan server
     and through the plain FP64 single-integral form (one context at a time),
@@ -502,6 +519,7 @@ def _serving(V, rate, n_requests, target, budget, fp64_sample=0):
     st = srv.run(reqs, realtime=True, time_limit=120)
     srv.batch.close()
     out = {"rate_per_s": rate, "target_rel": target, "budget": budget, **st}
+    out["roofline"] = _served_roofline(reqs, st["wall_s"])
     if fp64_sample:
         # the same first requests, all queued at t = 0, through both forms
         def queued():
