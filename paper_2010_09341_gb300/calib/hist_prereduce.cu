@@ -15,6 +15,12 @@
 //   nvcc -gencode arch=compute_103a,code=sm_103a -O3 -std=c++17 -o hist_prereduce hist_prereduce.cu && ./hist_prereduce
 // Output: per shape (d, N) and variant, the kernel time (CUDA events, mean of
 // 5 launches after 2 warm-up launches) and the samples per second.
+//
+// A third variant keeps the lane-private cells with half as many copies
+// (8 table and 16 histogram copies per cell, two lanes per copy) and asks
+// for 4 blocks of 512 threads per SM instead of 2: twice the resident warps
+// for some two-way bank conflicts, a test of whether the loop is bound by
+// latency that more warps would hide.
 #include <cstdint>
 #include <cstdio>
 #include <vector>
@@ -25,22 +31,29 @@
 namespace {
 
 constexpr int kThreads = 512;
-constexpr int kTP = 16;        // table copies per cell (lane-private, as the library)
-constexpr int kHP = 32;        // histogram copies per cell in the lane-private variant
 
-template <int D, int N, bool PRE>
-__global__ void __launch_bounds__(kThreads) sample_hist(const float2 *gtab, unsigned long long *ghist, long long n,
-                                                        uint32_t key0, uint32_t key1, float s0, float hscale) {
+// Copies per cell: table TP, histogram HP (1 for the pre-reduction), and the
+// blocks per SM the launch bounds ask for.
+template <int V> struct Var;
+template <> struct Var<0> { static constexpr int TP = 16, HP = 32, MINB = 1; static constexpr bool PRE = false; };
+template <> struct Var<1> { static constexpr int TP = 16, HP = 1, MINB = 1; static constexpr bool PRE = true; };
+template <> struct Var<2> { static constexpr int TP = 8, HP = 16, MINB = 4; static constexpr bool PRE = false; };
+
+template <int D, int N, int V>
+__global__ void __launch_bounds__(kThreads, Var<V>::MINB)
+sample_hist(const float2 *gtab, unsigned long long *ghist, long long n, uint32_t key0, uint32_t key1, float s0,
+            float hscale) {
+    constexpr int kTP = Var<V>::TP, HC = Var<V>::HP;
+    constexpr bool PRE = Var<V>::PRE;
     extern __shared__ __align__(16) unsigned char smem[];
     float2 *tab = reinterpret_cast<float2 *>(smem);
     uint32_t *hist = reinterpret_cast<uint32_t *>(tab + D * N * kTP);
-    constexpr int HC = PRE ? 1 : kHP;
     for (int k = threadIdx.x; k < D * N * kTP; k += blockDim.x) tab[k] = gtab[k / kTP];
     for (int k = threadIdx.x; k < D * N * HC; k += blockDim.x) hist[k] = 0u;
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const float2 *tab_l = tab + (lane % kTP);
-    uint32_t *hist_l = hist + (PRE ? 0 : lane);
+    uint32_t *hist_l = hist + (PRE ? 0 : lane % HC);
     const long long per = (n + gridDim.x - 1) / gridDim.x;
     const long long lo = static_cast<long long>(blockIdx.x) * per;
     const long long hi = lo + per < n ? lo + per : n;
@@ -79,7 +92,7 @@ __global__ void __launch_bounds__(kThreads) sample_hist(const float2 *gtab, unsi
                 const unsigned sum = __reduce_add_sync(grp, qv);
                 if (lane == __ffs(grp) - 1 && sum) atomicAdd(hist_l + cell[j], sum);
             } else if (qv) {
-                atomicAdd(hist_l + cell[j] * kHP, qv);
+                atomicAdd(hist_l + cell[j] * HC, qv);
             }
         }
     }
@@ -91,15 +104,16 @@ __global__ void __launch_bounds__(kThreads) sample_hist(const float2 *gtab, unsi
     }
 }
 
-template <int D, int N, bool PRE>
+template <int D, int N, int V>
 bool run(const float2 *dtab, unsigned long long *dhist, long long n, int sms, float *ms_out,
-         std::vector<unsigned long long> &out) {
-    const size_t smem = static_cast<size_t>(D) * N * (kTP * sizeof(float2) + (PRE ? 1 : kHP) * sizeof(uint32_t));
-    auto k = sample_hist<D, N, PRE>;
+         std::vector<unsigned long long> &out, int *blocks_per_sm) {
+    const size_t smem = static_cast<size_t>(D) * N * (Var<V>::TP * sizeof(float2) + Var<V>::HP * sizeof(uint32_t));
+    auto k = sample_hist<D, N, V>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess)
         return false;
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kThreads, smem) != cudaSuccess || occ < 1) return false;
+    *blocks_per_sm = occ;
     const int blocks = occ * sms;
     // f = exp(-sum (x - 1/2)^2 / a^2) from acc = sum X^2, X = 2^32 (x - 1/2) (table about 1/2)
     const float s0 = -1.4426950408889634f / (0.1f * 0.1f) * 5.421010862427522e-20f;  // x 2^-64
@@ -146,25 +160,30 @@ int shape(int sms, long long n) {
         return 1;
     }
     cudaMemcpy(dtab, tab.data(), sizeof(float2) * D * N, cudaMemcpyHostToDevice);
-    float ms_priv = 0.f, ms_pre = 0.f;
-    std::vector<unsigned long long> h_priv, h_pre;
-    const bool ok = run<D, N, false>(dtab, dhist, n, sms, &ms_priv, h_priv) &&
-                    run<D, N, true>(dtab, dhist, n, sms, &ms_pre, h_pre);
+    float ms_priv = 0.f, ms_pre = 0.f, ms_half = 0.f;
+    int occ_priv = 0, occ_pre = 0, occ_half = 0;
+    std::vector<unsigned long long> h_priv, h_pre, h_half;
+    const bool ok = run<D, N, 0>(dtab, dhist, n, sms, &ms_priv, h_priv, &occ_priv) &&
+                    run<D, N, 1>(dtab, dhist, n, sms, &ms_pre, h_pre, &occ_pre) &&
+                    run<D, N, 2>(dtab, dhist, n, sms, &ms_half, h_half, &occ_half);
     cudaFree(dtab);
     cudaFree(dhist);
     if (!ok) {
         fprintf(stderr, "d=%d N=%d: %s\n", D, N, cudaGetErrorString(cudaGetLastError()));
         return 1;
     }
-    if (h_priv != h_pre) {
+    if (h_priv != h_pre || h_priv != h_half) {
         fprintf(stderr, "d=%d N=%d: the two variants' histograms differ\n", D, N);
         return 1;
     }
     unsigned long long tot = 0;
     for (auto x : h_priv) tot += x;
-    printf("d=%d N=%-4d lane-private cells : %8.3f ms  %7.2f G samples/s\n", D, N, ms_priv, n / (ms_priv * 1e6));
-    printf("d=%d N=%-4d warp pre-reduction : %8.3f ms  %7.2f G samples/s  (%.2fx the time)\n", D, N, ms_pre,
-           n / (ms_pre * 1e6), ms_pre / ms_priv);
+    printf("d=%d N=%-4d lane-private cells : %8.3f ms  %7.2f G samples/s  (%d blocks/SM)\n", D, N, ms_priv,
+           n / (ms_priv * 1e6), occ_priv);
+    printf("d=%d N=%-4d warp pre-reduction : %8.3f ms  %7.2f G samples/s  (%.2fx the time, %d blocks/SM)\n", D, N,
+           ms_pre, n / (ms_pre * 1e6), ms_pre / ms_priv, occ_pre);
+    printf("d=%d N=%-4d half the copies    : %8.3f ms  %7.2f G samples/s  (%.2fx the time, %d blocks/SM)\n", D, N,
+           ms_half, n / (ms_half * 1e6), ms_half / ms_priv, occ_half);
     printf("   histograms identical (sum %llu)\n", tot);
     return 0;
 }
