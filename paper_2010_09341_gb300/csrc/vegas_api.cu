@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "vegas_kernels.cuh"
+#include "vegas_nvtx.h"
 
 using namespace vegas;
 
@@ -447,12 +448,14 @@ static vegas_status create_impl(const vegas_config *cfg, const vegas_integrand *
 
 vegas_status vegas_create(const vegas_config *cfg, const vegas_integrand *itg, void *stream,
                           void *dev_workspace, size_t ws_bytes, vegas_ctx **out) {
+    VEGAS_NVTX_RANGE();
     return create_impl(cfg, itg, nullptr, stream, dev_workspace, ws_bytes, out);
 }
 
 vegas_status vegas_create_user(const vegas_config *cfg, const char *source, const double *params,
                                int32_t n_params, void *stream, void *dev_workspace, size_t ws_bytes,
                                vegas_ctx **out) {
+    VEGAS_NVTX_RANGE();
     if (!source || !cfg) return VEGAS_EINVAL;
     vegas_integrand itg;
     itg.family = VEGAS_F_USER;
@@ -663,6 +666,7 @@ static vegas_status finalize_iteration(vegas_ctx *c, vegas_iter_result *out) {
 }
 
 vegas_status vegas_iterate(vegas_ctx *c, vegas_iter_result *out) {
+    VEGAS_NVTX_RANGE();
     if (!c) return VEGAS_EINVAL;
     const vegas_status st = sample_samples(c, 0, c->cfg.n_events);
     if (st != VEGAS_OK) return st;
@@ -684,6 +688,7 @@ static RefineJob refine_job(vegas_ctx *c) {
 }
 
 vegas_status vegas_step(vegas_ctx *c, vegas_iter_result *out) {
+    VEGAS_NVTX_RANGE();
     if (!c) return VEGAS_EINVAL;
     const vegas_status st = sample_samples(c, 0, c->cfg.n_events);
     if (st != VEGAS_OK) return st;
@@ -693,6 +698,7 @@ vegas_status vegas_step(vegas_ctx *c, vegas_iter_result *out) {
 }
 
 vegas_status vegas_step_many(vegas_ctx *const *ctxs, int32_t n) {
+    VEGAS_NVTX_RANGE();
     if (!ctxs || n < 1 || n > VEGAS_MAX_STEP_MANY) return VEGAS_EINVAL;
     for (int k = 0; k < n; ++k) {
         if (!ctxs[k] || ctxs[k]->stream != ctxs[0]->stream) return VEGAS_EINVAL;
@@ -712,6 +718,7 @@ vegas_status vegas_step_many(vegas_ctx *const *ctxs, int32_t n) {
 }
 
 vegas_status vegas_sample_shard(vegas_ctx *c, int64_t s_begin, int64_t count) {
+    VEGAS_NVTX_RANGE();
     if (!c || s_begin < 0 || count < 0 || s_begin + count > c->cfg.n_events) return VEGAS_EINVAL;
     if (c->strat_req != 0) return VEGAS_EINVAL;  // stratified iterations are not sharded
     if (count == 0) return VEGAS_OK;
@@ -728,11 +735,13 @@ vegas_status vegas_accumulators(vegas_ctx *c, double **dev_sums, int64_t *n_sums
 }
 
 vegas_status vegas_finalize(vegas_ctx *c, vegas_iter_result *out) {
+    VEGAS_NVTX_RANGE();
     if (!c) return VEGAS_EINVAL;
     return finalize_iteration(c, out);
 }
 
 vegas_status vegas_refine(vegas_ctx *c) {
+    VEGAS_NVTX_RANGE();
     if (!c) return VEGAS_EINVAL;
     if (c->n_done == 0) return VEGAS_OK;  // nothing sampled yet: keep the grid
     VEGAS_CK(launch_refine(c->last, c->edges, c->table, c->center, c->mode, c->cfg.n_dim, c->cfg.n_bins,
@@ -741,6 +750,7 @@ vegas_status vegas_refine(vegas_ctx *c) {
 }
 
 vegas_status vegas_result(vegas_ctx *c, vegas_result_t *out) {
+    VEGAS_NVTX_RANGE();
     if (!c || !out) return VEGAS_EINVAL;
     CombRec r;
     VEGAS_CK(cudaMemcpyAsync(&r, c->comb, sizeof(r), cudaMemcpyDeviceToHost, c->stream));
@@ -768,6 +778,7 @@ static vegas_status read_records(vegas_ctx *c, int first, int count, IterRec *ds
 }
 
 vegas_status vegas_run(vegas_ctx *c, int32_t n_iter, vegas_iter_result *iters, vegas_result_t *out) {
+    VEGAS_NVTX_RANGE();
     if (!c || n_iter < 1 || !out) return VEGAS_EINVAL;
     if (iters && n_iter > kIterRing) return VEGAS_EINVAL;
     const int first = c->n_done;
@@ -790,6 +801,7 @@ vegas_status vegas_run(vegas_ctx *c, int32_t n_iter, vegas_iter_result *iters, v
 }
 
 vegas_status vegas_get_grid(vegas_ctx *c, double *edges_host) {
+    VEGAS_NVTX_RANGE();
     if (!c || !edges_host) return VEGAS_EINVAL;
     const size_t bytes = sizeof(double) * c->cfg.n_dim * (c->cfg.n_bins + 1);
     VEGAS_CK(cudaMemcpyAsync(edges_host, c->edges, bytes, cudaMemcpyDeviceToHost, c->stream));
@@ -798,6 +810,7 @@ vegas_status vegas_get_grid(vegas_ctx *c, double *edges_host) {
 }
 
 vegas_status vegas_set_grid(vegas_ctx *c, const double *e) {
+    VEGAS_NVTX_RANGE();
     if (!c || !e) return VEGAS_EINVAL;
     const int d = c->cfg.n_dim, N = c->cfg.n_bins;
     for (int j = 0; j < d; ++j) {
@@ -846,6 +859,7 @@ vegas_status vegas_set_iteration(vegas_ctx *c, int32_t t) {
 
 vegas_status vegas_trace(vegas_ctx *c, int32_t t, int64_t s_begin, int64_t count, int32_t *bins,
                          double *x, double *w) {
+    VEGAS_NVTX_RANGE();
     if (!c || t < 0 || s_begin < 0 || count < 0) return VEGAS_EINVAL;
     if (c->family == VEGAS_F_LO_PDF && !c->pdf) return VEGAS_EINVAL;
     if (count == 0) return VEGAS_OK;
@@ -864,6 +878,7 @@ vegas_status vegas_trace(vegas_ctx *c, int32_t t, int64_t s_begin, int64_t count
 
 vegas_status vegas_histogram(vegas_ctx *c, int32_t t, int32_t observable, int32_t nbins, double lo, double hi,
                              double *dev_out) {
+    VEGAS_NVTX_RANGE();
     if (!c || t < 0 || nbins < 1 || nbins > 1024 || !(hi > lo) || !std::isfinite(lo) || !std::isfinite(hi) ||
         !dev_out || (reinterpret_cast<uintptr_t>(dev_out) % alignof(double)) != 0)
         return VEGAS_EINVAL;
@@ -889,6 +904,7 @@ vegas_status vegas_histogram(vegas_ctx *c, int32_t t, int32_t observable, int32_
 }
 
 vegas_status vegas_set_strata(vegas_ctx *c, int32_t B) {
+    VEGAS_NVTX_RANGE();
     if (!c || B < -1 || B > 31) return VEGAS_EINVAL;
     if (B != 0 && !c->kfn_strat) {
         const void *fn = c->family == VEGAS_F_USER ? c->jit.strat
@@ -920,6 +936,7 @@ vegas_status vegas_set_strata(vegas_ctx *c, int32_t B) {
 
 vegas_status vegas_set_pdf_grid(vegas_ctx *c, const double *dev_xg, int32_t nx, int32_t nq, double u0,
                                 double u1, double v0, double v1) {
+    VEGAS_NVTX_RANGE();
     if (!c || c->family != VEGAS_F_LO_PDF || !dev_xg || nx < 2 || nq < 2 ||
         static_cast<long long>(nx + 2) * (nq + 2) > kMaxPdfValues || !(u1 > u0) || !(v1 > v0) || !std::isfinite(u0) ||
         !std::isfinite(u1) || !std::isfinite(v0) || !std::isfinite(v1) ||
@@ -991,6 +1008,7 @@ constexpr uint32_t kMagic = 0x56454741u;  // "VEGA"
 }  // namespace
 
 vegas_status vegas_export_state(vegas_ctx *c, void *buf, size_t *size) {
+    VEGAS_NVTX_RANGE();
     if (!c || !size) return VEGAS_EINVAL;
     const int d = c->cfg.n_dim, N = c->cfg.n_bins;
     const size_t ne = static_cast<size_t>(d) * (N + 1);
@@ -1037,6 +1055,7 @@ vegas_status vegas_export_state(vegas_ctx *c, void *buf, size_t *size) {
 }
 
 vegas_status vegas_import_state(vegas_ctx *c, const void *buf, size_t size) {
+    VEGAS_NVTX_RANGE();
     if (!c || !buf || size < sizeof(BlobHeader)) return VEGAS_EINVAL;
     const char *p = static_cast<const char *>(buf);
     BlobHeader h;
@@ -1081,6 +1100,7 @@ vegas_status vegas_import_state(vegas_ctx *c, const void *buf, size_t size) {
 
 vegas_status vegas_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int64_t n,
                           void *stream) {
+    VEGAS_NVTX_RANGE();
     if (n < 0 || (n > 0 && (!ctr || !key || !out))) return VEGAS_EINVAL;
     VEGAS_CK(launch_philox(ctr, key, out, n, static_cast<cudaStream_t>(stream)));
     return VEGAS_OK;

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "vegas_batch.cuh"
+#include "vegas_nvtx.h"
 #include "vegas_refine.cuh"
 
 namespace vegas {
@@ -455,6 +456,7 @@ size_t vegas_batch_slot_bytes(const vegas_config *cfg) {
 
 vegas_status vegas_batch_create(int32_t max_slots, int32_t precision, void *stream, void *dev_ws,
                                 size_t ws_bytes, vegas_batch **out) {
+    VEGAS_NVTX_RANGE();
     if (!out) return VEGAS_EINVAL;
     *out = nullptr;
     const int mode = prec_mode(precision);
@@ -512,6 +514,7 @@ vegas_status vegas_batch_create(int32_t max_slots, int32_t precision, void *stre
 
 vegas_status vegas_batch_add(vegas_batch *b, const vegas_config *cfg, const vegas_integrand *itg,
                              int32_t *slot_out) {
+    VEGAS_NVTX_RANGE();
     if (!b || !cfg || !itg || !slot_out) return VEGAS_EINVAL;
     const int d = cfg->n_dim, N = cfg->n_bins;
     if (d < 1 || d > VEGAS_MAX_DIM || N < 2 || N > VEGAS_MAX_BINS || cfg->n_events < 2 ||
@@ -611,6 +614,7 @@ vegas_status vegas_batch_add(vegas_batch *b, const vegas_config *cfg, const vega
 }
 
 vegas_status vegas_batch_remove(vegas_batch *b, int32_t slot) {
+    VEGAS_NVTX_RANGE();
     if (!b || slot < 0 || slot >= b->max_slots || !b->slots[slot].used) return VEGAS_EINVAL;
     const vegas_status st = batch_sync(b);
     if (st != VEGAS_OK) return st;
@@ -620,6 +624,7 @@ vegas_status vegas_batch_remove(vegas_batch *b, int32_t slot) {
 }
 
 vegas_status vegas_batch_step(vegas_batch *b) {
+    VEGAS_NVTX_RANGE();
     if (!b) return VEGAS_EINVAL;
     vegas_status st = batch_sync(b);
     if (st != VEGAS_OK) return st;
@@ -637,6 +642,7 @@ vegas_status vegas_batch_step(vegas_batch *b) {
 }
 
 vegas_status vegas_batch_wait(vegas_batch *b, vegas_batch_result *out, int32_t cap, int32_t *count) {
+    VEGAS_NVTX_RANGE();
     if (!b || !count || cap < 0 || (cap > 0 && !out)) return VEGAS_EINVAL;
     const vegas_status st = batch_sync(b);
     if (st != VEGAS_OK) return st;
@@ -674,6 +680,7 @@ vegas_status vegas_batch_get_grid(vegas_batch *b, int32_t slot, double *edges_ho
 }
 
 vegas_status vegas_batch_set_events(vegas_batch *b, int32_t slot, int64_t n_events) {
+    VEGAS_NVTX_RANGE();
     if (!b || slot < 0 || slot >= b->max_slots || !b->slots[slot].used || n_events < 2) return VEGAS_EINVAL;
     if (n_events == b->slots[slot].n) return VEGAS_OK;
     vegas_status st = batch_sync(b);
@@ -694,6 +701,7 @@ vegas_status vegas_batch_set_tile(vegas_batch *b, int32_t tile_samples) {
 
 vegas_status vegas_batch_autotune(vegas_batch *b, const int32_t *cand, int32_t n_cand, int32_t reps,
                                   float *ms_out, int32_t *best) {
+    VEGAS_NVTX_RANGE();
     if (!b || !cand || n_cand < 1 || reps < 1 || !best) return VEGAS_EINVAL;
     vegas_status st = batch_sync(b);
     if (st != VEGAS_OK) return st;
@@ -758,6 +766,7 @@ vegas_status vegas_batch_get_shape(vegas_batch *b, vegas_batch_shape *out) {
 }
 
 vegas_status vegas_batch_set_shape(vegas_batch *b, const vegas_batch_shape *shape) {
+    VEGAS_NVTX_RANGE();
     if (!b || !shape) return VEGAS_EINVAL;
     const vegas_batch_shape s = *shape;
     if (s.tile_samples < 512 || s.tile_samples > (1 << 26) || s.tile_samples % 512 || s.threads < 128 ||
@@ -783,6 +792,7 @@ vegas_status vegas_batch_set_shape(vegas_batch *b, const vegas_batch_shape *shap
 
 vegas_status vegas_batch_autotune_shapes(vegas_batch *b, const vegas_batch_shape *cand, int32_t n_cand, int32_t reps,
                                          float *ms_out, int32_t *best) {
+    VEGAS_NVTX_RANGE();
     if (!b || !cand || n_cand < 1 || reps < 1 || !best) return VEGAS_EINVAL;
     vegas_batch_shape saved;
     vegas_batch_get_shape(b, &saved);

@@ -21,6 +21,13 @@ import torch
 import torch.distributed as dist
 
 
+class ShardLost(RuntimeError):
+    """The exchange of an iteration failed: a rank of the group left, died or
+    did not answer within the process group's timeout.  The iteration's sums
+    are incomplete, so it is not finalized; the caller decides whether to
+    rebuild the group or give up."""
+
+
 def shard_range(n: int, rank: int, world: int):
     """(first sample, count) of rank's share of n samples."""
     s0 = (rank * n) // world
@@ -74,8 +81,11 @@ def sharded_iterate(shard, group=None):
     begin = getattr(shard, "exchange_begin", None)
     if begin is not None:
         begin()
-    dist.all_reduce(sums, op=dist.ReduceOp.SUM, group=group)
-    dist.all_reduce(nonfinite, op=dist.ReduceOp.SUM, group=group)
+    try:
+        dist.all_reduce(sums, op=dist.ReduceOp.SUM, group=group)
+        dist.all_reduce(nonfinite, op=dist.ReduceOp.SUM, group=group)
+    except RuntimeError as e:  # a lost peer or a timeout (the backends raise RuntimeError subclasses)
+        raise ShardLost("rank %d of %d: the iteration's exchange failed: %s" % (rank, world, e)) from e
     end = getattr(shard, "exchange_end", None)
     if end is not None:
         end()

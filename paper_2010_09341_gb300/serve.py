@@ -12,6 +12,11 @@ sample budget) arrive over time.  Every loop turn the server
      (sigma / |I| <= target after at least ``min_iters`` iterations) or whose
      budget is spent, and records its latency (arrival to retirement).
 
+A request may be cancelled between steps (``Server.cancel``): it leaves the
+queue or frees its slot at once and is reported as cancelled, not completed.
+The summary adds the admission refusals (slot or pool full), the longest
+queue and the fraction of the wall time spent waiting for batched steps.
+
 Samples per iteration: ``n_first`` for the first ``warm_iters`` iterations
 (grid adaptation), then what the target needs from the current estimate,
 n = total_needed / remaining_iterations, rounded up to a power of two and
@@ -58,6 +63,7 @@ class Request:
     result: dict = field(default_factory=dict)
     converged: bool = False
     gave_up: bool = False
+    cancelled: bool = False
 
 
 def _pow2_ceil(x: float) -> int:
@@ -155,6 +161,10 @@ class Server:
         self.queue = []       # arrived, not yet admitted (arrival order)
         self.steps = 0
         self.samples = 0
+        self.refusals = 0     # admissions refused because the slots or the pool were full
+        self.max_queue = 0
+        self.busy_s = 0.0     # wall time inside the batched steps (launch to results)
+        self.cancelled = []
         # per-slot state as arrays, for the vectorised step
         self.used = np.zeros(max_slots, dtype=np.int64)
         self.n_cur = np.zeros(max_slots, dtype=np.int64)
@@ -171,6 +181,7 @@ class Server:
                 slot = self.batch.add(cfg, r.family, r.params)
             except VegasError as e:
                 if e.status in (VEGAS_EBUSY, VEGAS_ENOMEM):
+                    self.refusals += 1
                     return  # full: wait for retirements
                 raise
             r.admitted = now
@@ -189,8 +200,10 @@ class Server:
         samples per iteration are touched one by one."""
         if not self.active:
             return []
+        t0 = time.perf_counter()
         self.batch.step()
         a = self.batch.wait_array()
+        self.busy_s += time.perf_counter() - t0
         self.steps += 1
         now = now_fn()
         slots = a["slot"].astype(np.int64)
@@ -229,11 +242,29 @@ class Server:
                 rec[2] = int(n_new)
         return retired
 
-    def run(self, requests, time_limit: float = 60.0, realtime: bool = True):
+    def cancel(self, r: Request, now: float) -> bool:
+        """Withdraw a queued or active request between steps; False if it is
+        neither (not yet arrived, or already retired)."""
+        k = next((k for k, q in enumerate(self.queue) if q is r), None)
+        if k is not None:
+            self.queue.pop(k)
+        else:
+            slot = next((s for s, rec in self.active.items() if rec[0] is r), None)
+            if slot is None:
+                return False
+            self.active.pop(slot)
+            self.batch.remove(slot)
+        r.cancelled = True
+        r.done = now
+        self.cancelled.append(r)
+        return True
+
+    def run(self, requests, time_limit: float = 60.0, realtime: bool = True, on_step=None):
         """Serve ``requests`` (sorted by arrival time, seconds from start).
 
         With ``realtime`` the arrivals follow the wall clock; otherwise every
-        request is queued at start.  Returns summary statistics.
+        request is queued at start.  ``on_step(server, now)`` runs after every
+        step (it may cancel requests).  Returns summary statistics.
         """
         pending = sorted(requests, key=lambda q: q.arrival)
         t0 = time.perf_counter()
@@ -245,6 +276,7 @@ class Server:
             while i < len(pending) and (not realtime or pending[i].arrival <= now):
                 self.queue.append(pending[i])
                 i += 1
+            self.max_queue = max(self.max_queue, len(self.queue))
             self._admit(now)
             if not self.active:
                 if i >= len(pending) and not self.queue:
@@ -253,10 +285,15 @@ class Server:
                     time.sleep(max(0.0, min(0.01, pending[i].arrival - clock())))
                 continue
             done.extend(self.step(clock))
+            if on_step is not None:
+                on_step(self, clock())
             if clock() > time_limit:
                 break
         wall = clock()
-        return summarize(done, wall, self.steps, self.samples, len(requests))
+        out = summarize(done, wall, self.steps, self.samples, len(requests))
+        out.update({"cancelled": len(self.cancelled), "admit_refusals": self.refusals,
+                    "max_queue": self.max_queue, "busy_frac": self.busy_s / wall if wall > 0 else 0.0})
+        return out
 
 
 def summarize(done, wall: float, steps: int, samples: int, n_requests: int) -> dict:

@@ -5,8 +5,10 @@ C-ABI context), so the sharding, the all-reduce of the accumulators and the
 identical finalize/refine on every rank run without a GPU.  Parity: the
 sharded run equals the single-rank oracle run to 1e-12.
 """
+import datetime
 import os
 import socket
+import time
 
 import numpy as np
 import pytest
@@ -125,3 +127,59 @@ def test_shard_ranges_partition_the_samples():
 def test_replica_ids_distinct():
     ids = [i for r in range(4) for i in D.replica_integral_ids(r, 2)]
     assert len(set(ids)) == len(ids) == 8
+
+
+def _leaving_worker(rank, world, port, q):
+    """Rank 1 takes part in one iteration and then leaves without a word;
+    rank 0 goes on to a second iteration, whose exchange must fail."""
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=20))
+    d, N, n = 3, 20, 10_001
+    p = W.genz_params("genz_gauss", d, seed=9)
+    sh = OracleShard("genz_gauss", d, N, n, p, seed=3, iid=5)
+    first = D.sharded_iterate(sh)
+    if rank == 1:
+        time.sleep(1.0)          # the peer's first exchange is complete by now
+        q.put((rank, "left", first, ""))
+        q.close()
+        q.join_thread()
+        os._exit(0)              # no goodbye: the process group is not destroyed
+    sh.refine()
+    t0 = time.time()
+    try:
+        D.sharded_iterate(sh)
+        q.put((rank, "no error", first, ""))
+    except D.ShardLost as e:
+        q.put((rank, "lost after %.1f s" % (time.time() - t0), first, str(e)))
+    q.close()
+    q.join_thread()
+    os._exit(0)
+
+
+def test_a_rank_that_leaves_is_detected():
+    """Failure detection on the host, no GPU involved: when a rank dies
+    between iterations, the survivor's next exchange raises ShardLost (the
+    dropped connection, or at worst the group's 20 s timeout) instead of
+    hanging, and the iteration before it is still the single-rank result."""
+    world = 2
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_leaving_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    out = [q.get(timeout=120) for _ in range(world)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    out = dict((r[0], r[1:]) for r in out)
+    assert out[1][0] == "left"
+    status, first, msg = out[0]
+    assert status.startswith("lost"), status
+    assert "exchange failed" in msg
+    d, N, n = 3, 20, 10_001
+    p = W.genz_params("genz_gauss", d, seed=9)
+    ref = O.integrate(d, N, "genz_gauss", p, n, 1, seed=3, integral_id=5)
+    Io, so = ref["iters"][0]
+    assert abs(first[0] - Io) <= 1e-12 * abs(Io) and out[1][1][0] == first[0]

@@ -458,3 +458,23 @@ def test_combination_chi2_without_cancellation():
     assert abs(last["sigma"] - so) <= 1e-12 * so
     assert co > 0.05 and abs(last["chi2_dof"] - co) <= 1e-6 * co, (last["chi2_dof"], co)
     b.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_histogram_rows_sum_to_s2(prec):
+    """Every sample adds its (J f)^2 once to one bin of every dimension, so each
+    row of an iteration's histograms sums to S2: a lost or doubled shared-memory
+    update in any dimension would break it.  Three iterations (the FP32 modes'
+    first in FP32 cells, then fixed-point cells), 1e6 + 3 samples, d = 8: rows
+    to 1e-12 (FP64) and 1e-6 (FP32: each v^2 is rounded to 2^-19 of the mean
+    in a fixed-point cell)."""
+    V = native()
+    d, N, n = 8, 50, 1_000_003
+    ctx, _ = _make(V, "genz_gauss", d, N, n, prec)
+    tol = 1e-12 if prec == "fp64" else 1e-6
+    for _ in range(3):
+        V.vegas_iterate(ctx)
+        _, S2, h = V.vegas_get_sums(ctx)
+        rows = np.asarray(h).reshape(d, N).sum(axis=1)
+        assert np.all(np.abs(rows - S2) <= tol * S2), (rows / S2 - 1.0)
+        V.vegas_refine(ctx)

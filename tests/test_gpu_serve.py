@@ -103,3 +103,36 @@ def test_single_fp64_form_same_schedule():
     assert st["completed"] == len(reqs)
     for r in reqs:
         assert r.converged and r.result["sigma"] <= 1e-3 * abs(r.result["I"])
+
+
+def test_serve_cancellation_and_metrics():
+    """Two requests withdrawn between steps, one queued (the pool holds about
+    three integrals) and one active: they free their place at once, are
+    reported as cancelled, and every other request completes as it would
+    have.  The summary counts the cancellations and the admission refusals."""
+    V = native()
+    from paper_2010_09341_gb300 import serve as S
+    reqs = _reqs(10, target=0.0, budget=4 << 14, seed=5, d_hi=6)
+    per = V.Batch.slot_bytes(V.Config(n_dim=8, n_events=2, n_bins=50))
+    victims = []
+
+    def cancel_two(srv, now):
+        if srv.steps == 1:
+            queued = srv.queue[-1]
+            active = next(iter(srv.active.values()))[0]
+            assert srv.cancel(queued, now) and srv.cancel(active, now)
+            assert not srv.cancel(queued, now)
+            victims.extend([queued, active])
+
+    srv = S.Server(max_slots=16, pool_bytes=3 * per, n_first=1 << 14, adaptive=False)
+    st = srv.run(reqs, realtime=False, on_step=cancel_two)
+    assert len(victims) == 2 and all(v.cancelled and not v.result for v in victims)
+    assert st["cancelled"] == 2 and st["completed"] == 8
+    assert st["admit_refusals"] > 0 and st["max_queue"] >= 7 and 0.0 < st["busy_frac"] <= 1.0
+    for r in reqs:
+        if any(r is v for v in victims):
+            continue
+        assert r.result["n_iter"] == 4
+        alone = _reqs(10, target=0.0, budget=4 << 14, seed=5, d_hi=6)[r.integral_id]
+        S.Server(max_slots=2, pool_bytes=4 << 20, n_first=1 << 14, adaptive=False).run([alone], realtime=False)
+        assert abs(alone.result["I"] - r.result["I"]) <= 1e-5 * abs(r.result["I"]) + 1e-300
