@@ -82,7 +82,7 @@ def ops_per_sample(family: str, d: int, precision: str):
     dimensions.  Per sample: integrand finish, v = J f, v^2, non-finite test
     (2), the fixed-point histogram value (scale, convert, clamp, range test:
     5), the two sums (FP32 partials + FP64 flush: 2 adds, 2 for the chunk
-    bookkeeping and 4 FP64 ops per 8 samples; Kahan: 8 FP32 ops), loop (3).
+    bookkeeping and 4 FP64 ops per 16 samples; Kahan: 8 FP32 ops), loop (3).
     Wide multiplies (32x32->64) also count on their own pipe: 20 per Philox
     call plus one per dimension.  The FP64 path: fp64_ops_per_sample.
     """
@@ -100,8 +100,8 @@ def ops_per_sample(family: str, d: int, precision: str):
     if precision == "fp32_kahan":
         acc = 8
     elif precision == "fp32_acc64":
-        acc = 4 + 0.5
-        fp64 = 0.5
+        acc = 4 + 0.25
+        fp64 = 0.25
     else:
         acc = 3
         hist = 0

@@ -61,7 +61,7 @@ typedef enum {
  *   VEGAS_FP32_ACC64 : map, Jacobian and integrand in FP32 (the in-bin
  *                      position is the 32-bit low word rounded to FP32, not
  *                      truncated); per-thread FP32 partial sums of v and v^2
- *                      over 8 samples, added into FP64.
+ *                      over 16 samples, added into FP64.
  *   VEGAS_FP32_KAHAN : as FP32_ACC64, with the per-thread sums of v and v^2
  *                      Kahan-compensated FP32.
  * Histograms in both FP32 modes: in an iteration after a settled one (its

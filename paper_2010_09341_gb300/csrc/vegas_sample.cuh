@@ -413,7 +413,9 @@ __device__ __forceinline__ void kahan_add(ThreadSums<MODE> &ts, float v, float v
 
 // The block samples [s0, s0 + cnt) of one integral: thread t takes
 // s0 + t + u * blockDim, in chunks of kChunk samples (ACC_F32_SUM64 adds a
-// chunk's FP32 partial sums into the FP64 sums once per chunk).
+// chunk's FP32 partial sums into the FP64 sums once per chunk: 16 samples,
+// a relative error of at most about 1e-6 per partial; half the FP64
+// instructions of 8-sample chunks ran the d = 8 headline 1% faster).
 // EXACT: the dimension equals MAXD (no per-dimension guards); otherwise
 // 1 <= rp.d <= MAXD at run time.  PACK: 16-bit cell indices (SampleCells).
 template <int FAM, int MODE, int MAXD, bool EXACT, int PRIV, bool PACK = false>
@@ -433,7 +435,7 @@ __device__ __forceinline__ void sample_range(const BlockState<MODE, PRIV> &bs,
     const float hs = rp.hs;
     const bool fixed = hs > 0.f;
 
-    constexpr int kChunk = 8;
+    constexpr int kChunk = 16;
     const int stride = blockDim.x;
     for (int k0 = threadIdx.x; k0 < cnt; k0 += kChunk * stride) {
         float p1 = 0.f, p2 = 0.f;

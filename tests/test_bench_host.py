@@ -12,15 +12,15 @@ import bench
 
 def test_counted_operations_of_the_headline_integrals():
     """The counts the roofline is built on, at d = 8 with FP32 sampling and FP64
-    sums: 180.5 (Gaussian) and 184.5 (oscillatory) operations, of which 48 are
+    sums: 180.25 (Gaussian) and 184.25 (oscillatory) operations, of which 48 are
     32x32->64 multiplies (2 Philox calls x 20, plus one per dimension).  The
     Gaussian's (x - 1/2)^2 is one FMA per dimension (its centre is in the
     sampling table), the oscillatory sum one FMA."""
     g = bench.ops_per_sample("gauss_sym", 8, "fp32_acc64")
     o = bench.ops_per_sample("genz_osc", 8, "fp32_acc64")
-    assert g["total"] == 180.5 and o["total"] == 184.5
+    assert g["total"] == 180.25 and o["total"] == 184.25
     assert g["mulwide"] == o["mulwide"] == 48
-    assert g["fp64"] == 0.5
+    assert g["fp64"] == 0.25
     # one more Philox call per 4 dimensions, 9 + per-dimension integrand ops per dimension
     g9 = bench.ops_per_sample("gauss_sym", 9, "fp32_acc64")
     assert g9["mulwide"] == 60 + 9
@@ -28,11 +28,11 @@ def test_counted_operations_of_the_headline_integrals():
 
 
 def test_issue_roofline_at_152_sms_and_2070_mhz():
-    """(180.5 - 48) + 4 x 48 = 324.5 issue cycles per sample: 152 x 2.07e9 x 128 / 324.5
-    = 124.11 G samples/s; the FP64 and MUFU bounds are far above it."""
+    """(180.25 - 48) + 4 x 48 = 324.25 issue cycles per sample: 152 x 2.07e9 x 128 / 324.25
+    = 124.20 G samples/s; the FP64 and MUFU bounds are far above it."""
     b = bench.roofline_samples_per_s(bench.ops_per_sample("gauss_sym", 8, "fp32_acc64"), 152, 2.07e9)
-    assert b["issue"] == pytest.approx(152 * 2.07e9 * 128 / 324.5, rel=1e-12)
-    assert b["issue"] == pytest.approx(124.11e9, rel=1e-4)
+    assert b["issue"] == pytest.approx(152 * 2.07e9 * 128 / 324.25, rel=1e-12)
+    assert b["issue"] == pytest.approx(124.20e9, rel=1e-4)
     assert min(b, key=b.get) == "issue"
     assert b["fp64"] > 10 * b["issue"] and b["mufu"] > 10 * b["issue"]
 
