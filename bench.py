@@ -110,10 +110,12 @@ def ops_per_sample(family: str, d: int, precision: str):
     return {"total": total, "fp64": fp64, "mufu": mufu, "mulwide": 20 * calls + d}
 
 
-# Cost of one call of an FP64 library function in DFMA issue slots of the
-# FP64 pipe: its measured cycles per warp instruction over a DFMA's (76),
-# from paper_2010_09341_gb300/calib/pipe_costs.cu on one GB300.
-FP64_CALL_DFMA = {"exp2": 17.0, "cos": 17.5, "log2": 30.4, "rcp": 4.7}
+# Cost of one call of an FP64 function in DFMA issue slots of the FP64 pipe:
+# its measured cycles per warp instruction over a DFMA's (76), from
+# paper_2010_09341_gb300/calib/pipe_costs.cu on one GB300.  exp2 is the
+# library's own table-driven 2^x (vegas::fexp2, 9 FP64 operations; CUDA's
+# exp2 costs 17.0), the others CUDA's functions.
+FP64_CALL_DFMA = {"exp2": 9.9, "cos": 17.5, "log2": 30.4, "rcp": 4.7}
 
 
 def fp64_ops_per_sample(family: str, d: int) -> float:

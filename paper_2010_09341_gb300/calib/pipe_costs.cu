@@ -16,13 +16,15 @@
 #include <cstdio>
 #include <cuda_runtime.h>
 
+#include "../csrc/vegas_device.cuh"
+
 constexpr int kIt = 2048;
 constexpr int kThreads = 1024;
 
 enum Kind : int {
     K_FFMA, K_IADD, K_LOP3, K_IMAD, K_MULHI, K_MULWIDE_XOR, K_MULWIDE_XOR_2FFMA, K_FFMA_LOP3,
     K_ATOMS_U32, K_ATOMS_F32, K_ATOMS_F64, K_DFMA, K_EX2, K_EXP64, K_I2F, K_I2F_2FFMA, K_SHF,
-    K_ATOMS_U64, K_MATCH_ANY, K_COS64, K_LOG2_64, K_EXP2_64, K_RCP64, K_COUNT
+    K_ATOMS_U64, K_MATCH_ANY, K_COS64, K_LOG2_64, K_EXP2_64, K_RCP64, K_FEXP2_64, K_COUNT
 };
 
 template <int V>
@@ -88,6 +90,8 @@ __global__ void __launch_bounds__(kThreads) chains(unsigned long long *cycles, u
                 g[c] = exp(-g[c]);  // stays in (0.3, 1]: converges to 0.567
             } else if (V == K_EXP2_64) {
                 g[c] = exp2(-g[c]);  // stays in (0.5, 1]: converges to 0.64
+            } else if (V == K_FEXP2_64) {
+                g[c] = vegas::fexp2(-g[c]);  // the library's table-driven 2^x
             } else if (V == K_COS64) {
                 g[c] = cos(g[c]);   // stays in [cos 1, 1]: converges to 0.739
             } else if (V == K_RCP64) {
@@ -171,6 +175,7 @@ int main() {
         {"cos (double, one call)", 1, chains<K_COS64>},
         {"log2 (double, one call + 2 dadd)", 1, chains<K_LOG2_64>},
         {"1/x (double, one division + dadd)", 1, chains<K_RCP64>},
+        {"vegas::fexp2 (double, table-driven)", 1, chains<K_FEXP2_64>},
     };
     unsigned long long *h = new unsigned long long[blocks];
     int rc = 0;

@@ -178,7 +178,74 @@ __device__ __forceinline__ float fexp2(float x) {
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
-__device__ __forceinline__ double fexp2(double x) { return exp2(x); }
+// 2^x for the FP64 path, from the table-driven method of P. T. P. Tang
+// ("Table-driven implementation of the exponential function in IEEE
+// floating-point arithmetic", ACM Trans. Math. Softw. 15 (1989) 144):
+// x = m + j/64 + r with integers m, j (0 <= j < 64) and |r| <= 1/128, so
+// 2^x = 2^m 2^(j/64) 2^r; 2^(j/64) comes from a table, 2^r from its Taylor
+// series 1 + sum_n (r ln 2)^n / n! to n = 5 (the first term left out is below
+// 4e-17 relative), and 2^m goes into the exponent field.  9 FP64 operations
+// in the normal range against the library exp2's 17 DFMA-equivalents; within
+// 2 ulp of it (tests/cuda/exp2_check.cu compares the two), with the same
+// subnormal results, 0, infinity and NaN outside the normal range.
+// kExp2Tab[j] = 2^(j/64) and kExp2Taylor[n-1] = (ln 2)^n / n!, each rounded to
+// the nearest double (exact decimal arithmetic; tests/test_oracle_pins.py
+// recomputes them).
+__device__ const double kExp2Tab[64] = {
+    0x1.0000000000000p+0, 0x1.02c9a3e778061p+0, 0x1.059b0d3158574p+0, 0x1.0874518759bc8p+0,
+    0x1.0b5586cf9890fp+0, 0x1.0e3ec32d3d1a2p+0, 0x1.11301d0125b51p+0, 0x1.1429aaea92de0p+0,
+    0x1.172b83c7d517bp+0, 0x1.1a35beb6fcb75p+0, 0x1.1d4873168b9aap+0, 0x1.2063b88628cd6p+0,
+    0x1.2387a6e756238p+0, 0x1.26b4565e27cddp+0, 0x1.29e9df51fdee1p+0, 0x1.2d285a6e4030bp+0,
+    0x1.306fe0a31b715p+0, 0x1.33c08b26416ffp+0, 0x1.371a7373aa9cbp+0, 0x1.3a7db34e59ff7p+0,
+    0x1.3dea64c123422p+0, 0x1.4160a21f72e2ap+0, 0x1.44e086061892dp+0, 0x1.486a2b5c13cd0p+0,
+    0x1.4bfdad5362a27p+0, 0x1.4f9b2769d2ca7p+0, 0x1.5342b569d4f82p+0, 0x1.56f4736b527dap+0,
+    0x1.5ab07dd485429p+0, 0x1.5e76f15ad2148p+0, 0x1.6247eb03a5585p+0, 0x1.6623882552225p+0,
+    0x1.6a09e667f3bcdp+0, 0x1.6dfb23c651a2fp+0, 0x1.71f75e8ec5f74p+0, 0x1.75feb564267c9p+0,
+    0x1.7a11473eb0187p+0, 0x1.7e2f336cf4e62p+0, 0x1.82589994cce13p+0, 0x1.868d99b4492edp+0,
+    0x1.8ace5422aa0dbp+0, 0x1.8f1ae99157736p+0, 0x1.93737b0cdc5e5p+0, 0x1.97d829fde4e50p+0,
+    0x1.9c49182a3f090p+0, 0x1.a0c667b5de565p+0, 0x1.a5503b23e255dp+0, 0x1.a9e6b5579fdbfp+0,
+    0x1.ae89f995ad3adp+0, 0x1.b33a2b84f15fbp+0, 0x1.b7f76f2fb5e47p+0, 0x1.bcc1e904bc1d2p+0,
+    0x1.c199bdd85529cp+0, 0x1.c67f12e57d14bp+0, 0x1.cb720dcef9069p+0, 0x1.d072d4a07897cp+0,
+    0x1.d5818dcfba487p+0, 0x1.da9e603db3285p+0, 0x1.dfc97337b9b5fp+0, 0x1.e502ee78b3ff6p+0,
+    0x1.ea4afa2a490dap+0, 0x1.efa1bee615a27p+0, 0x1.f50765b6e4540p+0, 0x1.fa7c1819e90d8p+0,
+};
+__device__ const double kExp2Taylor[5] = {0x1.62e42fefa39efp-1, 0x1.ebfbdff82c58fp-3, 0x1.c6b08d704a0c0p-5, 0x1.3b2ab6fba4e77p-7, 0x1.5d87fe78a6731p-10};
+
+// 2^(j/64) 2^r for k = rint(64 x) = 64 m + j (the steps above); *m = floor(k / 64).
+__device__ __forceinline__ double exp2_core(double x, int *m) {
+    const double kShift = 6755399441055744.0;           // 1.5 * 2^52: rounds 64 x to an integer
+    const double t = __fma_rn(x, 64.0, kShift);
+    const int k = __double2loint(t);                    // rint(64 x)
+    const double r = __fma_rn(t - kShift, -0.015625, x);  // x - k/64, exact
+    double p = kExp2Taylor[4];
+    p = __fma_rn(p, r, kExp2Taylor[3]);
+    p = __fma_rn(p, r, kExp2Taylor[2]);
+    p = __fma_rn(p, r, kExp2Taylor[1]);
+    p = __fma_rn(p, r, kExp2Taylor[0]);                  // (2^r - 1) / r
+    const double tj = __ldg(&kExp2Tab[k & 63]);
+    *m = k >> 6;
+    return __fma_rn(tj * r, p, tj);                      // in [0.99, 1.99)
+}
+
+__device__ __forceinline__ double fexp2(double x) {
+    // results in the normal range for -1021 <= x <= 1023, tested on the high
+    // word with integer operations (the FP64 pipe bounds this path); 2^m then
+    // goes straight into the exponent field
+    const int hx = __double2hiint(x);
+    const bool normal = hx >= 0 ? hx <= 0x408FF800 : (hx & 0x7FFFFFFF) <= 0x408FE800;  // 1023, 1021
+    int m;
+    if (normal) {
+        const double y = exp2_core(x, &m);
+        return __hiloint2double(__double2hiint(y) + (m << 20), __double2loint(y));
+    }
+    // NaN; otherwise scale in two steps, the second rounding to a subnormal
+    // result, to 0 (below 2^-1080) or to infinity (from 2^1024 up)
+    if (x != x) return x;
+    const double y = exp2_core(fmin(fmax(x, -1080.0), 1025.0), &m);
+    const bool up = m > 0;
+    return __hiloint2double(__double2hiint(y) + ((up ? m - 64 : m + 64) << 20), __double2loint(y)) *
+           (up ? 18446744073709551616.0 : 5.421010862427522e-20);  // 2^64, 2^-64
+}
 // log2 x for the FP32 path: the hardware approximation (absolute error about
 // 2^-22), subnormal arguments flushed to zero.
 __device__ __forceinline__ float flog2(float x) {
