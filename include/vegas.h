@@ -136,7 +136,7 @@ typedef struct {
     double I;               /* iteration estimate                             */
     double sigma;           /* its standard error                             */
     int64_t n;              /* samples with finite weight                     */
-    int64_t n_nonfinite;    /* samples skipped because v was NaN or Inf       */
+    int64_t n_nonfinite;    /* samples skipped: v (FP32: or v^2) NaN or Inf   */
 } vegas_iter_result;
 
 typedef struct {
@@ -193,7 +193,8 @@ const char *vegas_jit_log(void);
  * device.  Asynchronous if out == NULL; otherwise synchronises the stream and
  * fills *out.  NaN or infinite values of J f are counted in n_nonfinite and
  * left out of the sums and of n (stratified iterations: counted as 0, n keeps
- * every sample).  ENONFINITE (with *out filled) if no sample had a finite
+ * every sample); in the FP32 modes so is a finite J f whose square exceeds
+ * the FP32 range (the sums take (J f)^2).  ENONFINITE (with *out filled) if no sample had a finite
  * weight: that iteration has no estimate and is left out of the combination,
  * and a refinement after it keeps the grid (its histograms are zero).
  * The combination: Ibar = sum w_t I_t / sum w_t, w_t = 1/sigma_t^2,

@@ -301,8 +301,10 @@ template <int MAXD, bool PACK> struct SampleCells {
 
 // Grid map and integrand of sample s: its Philox words (placed in hypercube
 // h's strata when STRAT), each dimension's cell (recorded in cellj) and
-// v = J f, or 0 when v is not finite (counted in nonfinite).
-template <int FAM, int MODE, int MAXD, bool EXACT, int PRIV, bool PACK, bool STRAT>
+// v = J f.  CHECK: v is set to 0 and counted in nonfinite when it is not
+// finite, or, in FP32, when v^2 is not (CHECK false: the caller tests, see
+// hist_add_fixed).
+template <int FAM, int MODE, int MAXD, bool EXACT, int PRIV, bool PACK, bool STRAT, bool CHECK = true>
 __device__ __forceinline__ typename ModeTraits<MODE>::T map_sample(
     const typename BlockState<MODE, PRIV>::T2 *tab_l, const RangeParams<typename ModeTraits<MODE>::T> &rp,
     const FamConsts<typename ModeTraits<MODE>::T> &fc, const StratArgs *st, uint32_t h,
@@ -342,7 +344,7 @@ __device__ __forceinline__ typename ModeTraits<MODE>::T map_sample(
         }
     }
     T v = J * fam.finish(fc);
-    if (!isfinite(v)) {
+    if (CHECK && !isfinite(sizeof(T) == 4 ? v * v : v)) {
         v = T(0);
         ++nonfinite;
     }
@@ -398,6 +400,42 @@ __device__ __forceinline__ void hist_add(const BlockState<MODE, PRIV> &bs, typen
     }
 }
 
+// The fixed-point update of hist_add (FP32 modes, scale hs > 0) for a v that
+// map_sample did not test: a NaN or infinite v^2 fails qf < 2^23 as well, so
+// the test sits in that rare branch, which counts such a sample in nonfinite
+// and zeroes v and v2 (the caller adds them to the sums afterwards).  Saves
+// the per-sample test of the common path.
+template <int MODE, int PRIV, int MAXD, bool EXACT, bool PACK>
+__device__ __forceinline__ void hist_add_fixed(const BlockState<MODE, PRIV> &bs, typename BlockState<MODE, PRIV>::H *hist_l,
+                                               const RangeParams<float> &rp, const SampleCells<MAXD, PACK> &cellj,
+                                               float &v, float &v2, float hs, unsigned int &nonfinite) {
+    constexpr int HP = BlockState<MODE, PRIV>::HP;
+    const int d = EXACT ? MAXD : rp.d;
+    if (v2 == 0.f) return;
+    const float qf = v2 * hs;
+    if (qf < kFixedMax) {
+        const bool is_fine = qf < 1.0f;
+        const float t = __fmaf_rn(qf, is_fine ? kFineScale : 1.0f, 8388608.0f);
+        uint32_t q = __float_as_uint(t) - 0x4B000000u;
+        q = max(q, 1u);
+        unsigned int *base = is_fine ? bs.fine : reinterpret_cast<unsigned int *>(hist_l);
+        const uint32_t step = is_fine ? 1u : static_cast<uint32_t>(HP);
+#pragma unroll
+        for (int j = 0; j < MAXD; ++j) {
+            if (EXACT || j < d) atomicAdd(base + cellj.get(j) * step, q);
+        }
+    } else if (isfinite(v2)) {
+#pragma unroll
+        for (int j = 0; j < MAXD; ++j) {
+            if (EXACT || j < d) atomicAdd(rp.acc + 2 + cellj.get(j), static_cast<double>(v2));
+        }
+    } else {
+        v = 0.f;
+        v2 = 0.f;
+        ++nonfinite;
+    }
+}
+
 // Kahan step of the FP32-compensated sums of v and v^2.
 template <int MODE>
 __device__ __forceinline__ void kahan_add(ThreadSums<MODE> &ts, float v, float v2) {
@@ -418,11 +456,14 @@ __device__ __forceinline__ void kahan_add(ThreadSums<MODE> &ts, float v, float v
 // instructions of 8-sample chunks ran the d = 8 headline 1% faster).
 // EXACT: the dimension equals MAXD (no per-dimension guards); otherwise
 // 1 <= rp.d <= MAXD at run time.  PACK: 16-bit cell indices (SampleCells).
-template <int FAM, int MODE, int MAXD, bool EXACT, int PRIV, bool PACK = false>
-__device__ __forceinline__ void sample_range(const BlockState<MODE, PRIV> &bs,
-                                             const RangeParams<typename ModeTraits<MODE>::T> &rp,
-                                             const FamConsts<typename ModeTraits<MODE>::T> &fc,
-                                             ThreadSums<MODE> &ts, unsigned long long s0, int cnt) {
+// FOLD (FP32 modes with fixed-point cells): the non-finite test in the
+// histogram update's rare branch (hist_add_fixed) and the sums after it;
+// otherwise the test in map_sample and hist_add's general form.
+template <int FAM, int MODE, int MAXD, bool EXACT, int PRIV, bool PACK, bool FOLD>
+__device__ __forceinline__ void sample_loop(const BlockState<MODE, PRIV> &bs,
+                                            const RangeParams<typename ModeTraits<MODE>::T> &rp,
+                                            const FamConsts<typename ModeTraits<MODE>::T> &fc,
+                                            ThreadSums<MODE> &ts, unsigned long long s0, int cnt) {
     using BS = BlockState<MODE, PRIV>;
     using T = typename BS::T;
     using T2 = typename BS::T2;
@@ -448,9 +489,11 @@ __device__ __forceinline__ void sample_range(const BlockState<MODE, PRIV> &bs,
             if (k >= cnt) break;
             const unsigned long long s = s0 + static_cast<unsigned long long>(k);
             SampleCells<MAXD, PACK> cellj;
-            const T v = map_sample<FAM, MODE, MAXD, EXACT, PRIV, PACK, false>(tab_l, rp, fc, nullptr, 0u, s,
-                                                                              cellj, ts.nonfinite);
-            const T v2 = v * v;
+            T v = map_sample<FAM, MODE, MAXD, EXACT, PRIV, PACK, false, !FOLD>(tab_l, rp, fc, nullptr, 0u, s, cellj,
+                                                                             ts.nonfinite);
+            T v2 = v * v;
+            if constexpr (FOLD) hist_add_fixed<MODE, PRIV, MAXD, EXACT, PACK>(bs, hist_l, rp, cellj, v, v2, hs,
+                                                                              ts.nonfinite);
             if (MODE == ACC_F32_KAHAN) {
                 kahan_add(ts, static_cast<float>(v), static_cast<float>(v2));
             } else if (MODE == ACC_F32_SUM64) {
@@ -461,13 +504,29 @@ __device__ __forceinline__ void sample_range(const BlockState<MODE, PRIV> &bs,
                 ts.s1d += vd;
                 ts.s2d = __fma_rn(vd, vd, ts.s2d);
             }
-            hist_add<MODE, PRIV, MAXD, EXACT, PACK>(bs, hist_l, rp, cellj, v2, fixed, hs);
+            if constexpr (!FOLD) hist_add<MODE, PRIV, MAXD, EXACT, PACK>(bs, hist_l, rp, cellj, v2, fixed, hs);
         }
         if (MODE == ACC_F32_SUM64) {
             ts.s1d += static_cast<double>(p1);
             ts.s2d += static_cast<double>(p2);
         }
     }
+}
+
+// sample_loop in the form the iteration's cells take: FOLD where the FP32
+// cells hold fixed-point integers (every iteration after the first).
+template <int FAM, int MODE, int MAXD, bool EXACT, int PRIV, bool PACK = false>
+__device__ __forceinline__ void sample_range(const BlockState<MODE, PRIV> &bs,
+                                             const RangeParams<typename ModeTraits<MODE>::T> &rp,
+                                             const FamConsts<typename ModeTraits<MODE>::T> &fc,
+                                             ThreadSums<MODE> &ts, unsigned long long s0, int cnt) {
+    if constexpr (MODE != ACC_F64) {
+        if (rp.hs > 0.f) {
+            sample_loop<FAM, MODE, MAXD, EXACT, PRIV, PACK, true>(bs, rp, fc, ts, s0, cnt);
+            return;
+        }
+    }
+    sample_loop<FAM, MODE, MAXD, EXACT, PRIV, PACK, false>(bs, rp, fc, ts, s0, cnt);
 }
 
 // Adds the block's sums to the integral's FP64 accumulators: S1, S2 and the
