@@ -87,11 +87,11 @@ def ops_per_sample(family: str, d: int, precision: str):
     call plus one per dimension.  The FP64 path: fp64_ops_per_sample.
     """
     per_dim_f = {"gauss_sym": 1, "genz_osc": 1, "genz_gauss": 2, "genz_prod": 3,
-                 "genz_corner": 1, "sum": 1, "const": 0, "lo": 0}[family]
+                 "genz_corner": 1, "sum": 1, "const": 0, "lo": 0, "lo_pdf": 0}[family]
     finish = {"gauss_sym": 2, "genz_osc": 6, "genz_gauss": 2, "genz_prod": 1,
-              "genz_corner": 3, "sum": 0, "const": 0, "lo": 20}[family]
+              "genz_corner": 3, "sum": 0, "const": 0, "lo": 20, "lo_pdf": LO_PDF_FINISH}[family]
     mufu = {"gauss_sym": 1, "genz_osc": 1, "genz_gauss": 1, "genz_prod": 1,
-            "genz_corner": 2, "sum": 0, "const": 0, "lo": 2}[family]
+            "genz_corner": 2, "sum": 0, "const": 0, "lo": 2, "lo_pdf": 4}[family]
     calls = math.ceil(d / 4)
     philox = 40 * calls
     per_dim = (9 + per_dim_f) * d + d // 4
@@ -108,6 +108,28 @@ def ops_per_sample(family: str, d: int, precision: str):
         fp64 = fp64_ops_per_sample(family, d)
     total = philox + per_dim + finish + 2 + 2 + hist + acc + 3
     return {"total": total, "fp64": fp64, "mufu": mufu, "mulwide": 20 * calls + d}
+
+
+# The LO toy on a density grid (F_LO_PDF), FP32, per sample after the map:
+# the LO kinematics, cuts, Breit-Wigner and angular factor (20, as the LO
+# family, its power law replaced by the two densities); three grid coordinates
+# (log2 on the MUFU, subtract, scale, clamp (2), truncate, cap, convert back,
+# fraction: 9 each); three sets of cubic weights (13 each); two bicubic
+# lookups of 4 x 4 knots (16 shared-memory loads, 20 FMAs, 3 for the address:
+# 39 each); and the product of the two densities (2).
+LO_PDF_FINISH = 20 + 3 * 9 + 3 * 13 + 2 * 39 + 2
+
+
+def strat_ops_per_sample(family: str, d: int, precision: str, P: int):
+    """ops_per_sample for the stratified hybrid with P samples per hypercube:
+    per dimension the stratum word (a funnel shift, and the hypercube's bits
+    shifted once per hypercube); per sample the deviation from the hypercube's
+    first value and its two running sums (3); per hypercube the spread
+    b - a^2 / P clipped at 0 and added (4), the hypercube index and first
+    sample index (2) and its loop (3)."""
+    o = dict(ops_per_sample(family, d, precision))
+    o["total"] += d * (1 + 1 / P) + 3 + (4 + 2 + 3) / P
+    return o
 
 
 # Cost of one call of an FP64 function in DFMA issue slots of the FP64 pipe:
@@ -338,10 +360,17 @@ def _time_strat(V, torch, family, params, d, N, n, prec, iters=10, warm=5):
         V.vegas_destroy(ctx)
         k_ms = sum(kms) / len(kms)
         s_rms = math.sqrt(sum(x * x for x in sig) / len(sig))
+        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        ops = strat_ops_per_sample(family, d, prec, P) if P else ops_per_sample(family, d, prec)
+        bounds = roofline_samples_per_s(ops, sms, 2070e6)
+        pipe = min(bounds, key=bounds.get)
         out["stratified" if B else "plain"] = {
             "hypercubes": 2 ** Bt if P else 0, "samples_per_hypercube": P, "samples": used,
             "kernel_ms": k_ms, "samples_per_s": used / (k_ms / 1e3),
-            "sigma_sqrt_n": s_rms * math.sqrt(used), "I": res["I"], "sigma": res["sigma"]}
+            "sigma_sqrt_n": s_rms * math.sqrt(used), "I": res["I"], "sigma": res["sigma"],
+            "roofline": {"bound": "alu" if pipe == "issue" else pipe, "pipe": pipe,
+                         "ops_per_sample": ops["total"], "roofline_samples_per_s": bounds[pipe],
+                         "frac": (used / (k_ms / 1e3)) / bounds[pipe]}}
     a, b = out["plain"], out["stratified"]
     out["time_to_equal_sigma_vs_plain"] = (b["sigma_sqrt_n"] ** 2 / b["samples_per_s"]) / \
         (a["sigma_sqrt_n"] ** 2 / a["samples_per_s"])
@@ -387,6 +416,17 @@ def _time_user(V, torch, d=8, N=NBINS, n=NEVENTS, prec=PRECISION, iters=10, warm
         k_ms = sum(kms) / len(kms)
         out[kind] = {"create_s": t_create, "kernel_ms": k_ms, "samples_per_s": n / (k_ms / 1e3),
                      "I": res["I"], "sigma": res["sigma"]}
+    # both against the built-in family's counted operations (the algorithmic
+    # work of this integrand; the user source also subtracts the centre and
+    # scales x per dimension)
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    bounds = roofline_samples_per_s(ops_per_sample("genz_gauss", d, prec), sms, 2070e6)
+    pipe = min(bounds, key=bounds.get)
+    for kind in ("user", "builtin"):
+        out[kind]["roofline"] = {"bound": "alu" if pipe == "issue" else pipe, "pipe": pipe,
+                                 "roofline_samples_per_s": bounds[pipe],
+                                 "frac": out[kind]["samples_per_s"] / bounds[pipe],
+                                 "basis": "the built-in Genz Gaussian's counted operations"}
     out["workload"] = "Genz Gaussian d=%d, %d bins, %g samples/iter, %s; user source vs built-in family" % (
         d, N, n, prec)
     return out
@@ -418,11 +458,17 @@ def _time_lo_pdf(V, torch, n=100_000_000, iters=10, warm=2, prec="fp32_kahan"):
     res = V.vegas_result(ctx)
     V.vegas_destroy(ctx)
     k_ms = sum(kms) / len(kms)
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    ops = ops_per_sample("lo_pdf", 3, prec)
+    bounds = roofline_samples_per_s(ops, sms, 2070e6)
+    pipe = min(bounds, key=bounds.get)
     return {"workload": "LO toy d=3, density from a 96x48 (ln x, ln Q^2) grid at Q^2 = shat, 100 bins, "
                         "%g samples/iter, %s" % (n, prec),
             "samples_per_s": n * iters / (ms / 1e3), "kernel_ms": k_ms,
             "kernel_samples_per_s": n / (k_ms / 1e3), "ms_per_iter": ms / iters,
-            "I": res["I"], "sigma": res["sigma"]}
+            "I": res["I"], "sigma": res["sigma"],
+            "roofline": {"bound": "alu" if pipe == "issue" else pipe, "pipe": pipe, "ops_per_sample": ops["total"],
+                         "roofline_samples_per_s": bounds[pipe], "frac": (n / (k_ms / 1e3)) / bounds[pipe]}}
 
 
 def _time_batched(V, torch, steps=8, warm=2):

@@ -125,7 +125,7 @@ __device__ __forceinline__ void sample_range_strat_any(const BlockState<MODE, PR
 // hypercubes (the same points as above), not behind a test inside the loop:
 // the compiler predicates a short conditional block, and a predicated-off FP64
 // instruction still holds the FP64 unit for its ~76 cycles on GB300.
-template <int FAM, int MODE, int MAXD, bool EXACT, int PRIV>
+template <int FAM, int MODE, int MAXD, bool EXACT, int PRIV, bool FOLD>
 __device__ __forceinline__ void sample_range_strat_grouped(const BlockState<MODE, PRIV> &bs,
                                                      const RangeParams<typename ModeTraits<MODE>::T> &rp,
                                                      const FamConsts<typename ModeTraits<MODE>::T> &fc,
@@ -174,36 +174,35 @@ __device__ __forceinline__ void sample_range_strat_grouped(const BlockState<MODE
             ts.s2d = __fma_rn(vd, vd, ts.s2d);
         }
     };
+    // one sample's update: with FOLD (FP32 fixed-point cells) the histogram
+    // first, whose rare branch zeroes a non-finite v (hist_add_fixed), then
+    // the sums and the hypercube's spread
+    auto update = [&](T v, T v2, const SampleCells<MAXD, kPack> &cj, bool first, T &c, T &a, T &b) {
+        if constexpr (FOLD) hist_add_fixed<MODE, PRIV, MAXD, EXACT, kPack>(bs, hist_l, rp, cj, v, v2, hs, ts.nonfinite);
+        add_sums(v, v2);
+        if (first) c = v;
+        const T dv = v - c;
+        a += dv;
+        b = ffma(dv, dv, b);
+        if constexpr (!FOLD) hist_add<MODE, PRIV, MAXD, EXACT, kPack>(bs, hist_l, rp, cj, v2, fixed, hs);
+    };
     // samples [pb, pe) of hypercube h (first sample index sb), into A, B
     auto run = [&](uint32_t h, unsigned long long sb, uint32_t pb, uint32_t pe, T &c, T &a, T &b) {
         uint32_t p = pb;
         for (; p + 1 < pe; p += 2) {
             SampleCells<MAXD, kPack> ca, cb;
-            const T va = map_sample<FAM, MODE, MAXD, EXACT, PRIV, kPack, true>(tab_l, rp, fc, &st, h, sb + p, ca,
-                                                                               ts.nonfinite);
-            const T vb = map_sample<FAM, MODE, MAXD, EXACT, PRIV, kPack, true>(tab_l, rp, fc, &st, h, sb + p + 1,
-                                                                               cb, ts.nonfinite);
-            const T va2 = va * va, vb2 = vb * vb;
-            add_sums(va, va2);
-            add_sums(vb, vb2);
-            if (p == 0) c = va;
-            const T da = va - c, db = vb - c;
-            a += da + db;
-            b = ffma(da, da, ffma(db, db, b));
-            hist_add<MODE, PRIV, MAXD, EXACT, kPack>(bs, hist_l, rp, ca, va2, fixed, hs);
-            hist_add<MODE, PRIV, MAXD, EXACT, kPack>(bs, hist_l, rp, cb, vb2, fixed, hs);
+            const T va = map_sample<FAM, MODE, MAXD, EXACT, PRIV, kPack, true, !FOLD>(tab_l, rp, fc, &st, h, sb + p,
+                                                                                      ca, ts.nonfinite);
+            const T vb = map_sample<FAM, MODE, MAXD, EXACT, PRIV, kPack, true, !FOLD>(tab_l, rp, fc, &st, h,
+                                                                                      sb + p + 1, cb, ts.nonfinite);
+            update(va, va * va, ca, p == 0, c, a, b);
+            update(vb, vb * vb, cb, false, c, a, b);
         }
         if (p < pe) {
             SampleCells<MAXD, kPack> ca;
-            const T va = map_sample<FAM, MODE, MAXD, EXACT, PRIV, kPack, true>(tab_l, rp, fc, &st, h, sb + p, ca,
-                                                                               ts.nonfinite);
-            const T va2 = va * va;
-            add_sums(va, va2);
-            if (p == 0) c = va;
-            const T da = va - c;
-            a += da;
-            b = ffma(da, da, b);
-            hist_add<MODE, PRIV, MAXD, EXACT, kPack>(bs, hist_l, rp, ca, va2, fixed, hs);
+            const T va = map_sample<FAM, MODE, MAXD, EXACT, PRIV, kPack, true, !FOLD>(tab_l, rp, fc, &st, h, sb + p,
+                                                                                      ca, ts.nonfinite);
+            update(va, va * va, ca, p == 0, c, a, b);
         }
     };
     auto finish = [&](T a, T b) {
@@ -238,7 +237,10 @@ __device__ __forceinline__ void sample_range_strat(const BlockState<MODE, PRIV> 
     // push the 32-dimension tier past its 128 registers)
     if constexpr (EXACT) {
         if (st.P <= 8u) {
-            sample_range_strat_grouped<FAM, MODE, MAXD, EXACT, PRIV>(bs, rp, fc, st, ts, h0, cnt);
+            if (MODE != ACC_F64 && rp.hs > 0.f)
+                sample_range_strat_grouped<FAM, MODE, MAXD, EXACT, PRIV, MODE != ACC_F64>(bs, rp, fc, st, ts, h0, cnt);
+            else
+                sample_range_strat_grouped<FAM, MODE, MAXD, EXACT, PRIV, false>(bs, rp, fc, st, ts, h0, cnt);
             return;
         }
     }
@@ -247,10 +249,13 @@ __device__ __forceinline__ void sample_range_strat(const BlockState<MODE, PRIV> 
 
 // Stratified form: hypercubes [a.s_begin, a.s_begin + a.n) of P = a.st.P
 // samples each; each block takes a contiguous range of hypercubes.
-// Above 8 dimensions a block's lane-private cells take most of an SM's shared
-// memory, so one block per SM: its threads may use up to 128 registers.
+// Blocks per SM as for the plain kernel (kSampleMinBlocks: one, whose threads
+// may use up to 128 registers, except for the LO families); above 8
+// dimensions a block's lane-private cells take most of an SM's shared memory
+// anyway.  At d = 8 one block ran the stratified Gaussian 3.5% faster than
+// two, the oscillatory integral 1% slower.
 template <int FAM, int MODE, int MAXD, bool EXACT, bool PRIV>
-__global__ void __launch_bounds__(512, MAXD > 8 ? 1 : 2)
+__global__ void __launch_bounds__(512, kSampleMinBlocks<FAM>)
 vegas_sample_strat_kernel(const SampleArgs a) {
     pdl_begin();
     using BS = BlockState<MODE, PRIV>;

@@ -77,3 +77,17 @@ def test_traffic_is_reported_only_for_the_profiled_sources(tmp_path, monkeypatch
     assert bench._traffic_from_profile() is None
     os.remove(root / "profiles" / "sample_kernel_d8_gauss.md")
     assert bench._traffic_from_profile() is None
+
+
+def test_counted_operations_of_the_density_grid_and_stratified_lines():
+    """The LO toy on the density grid: Philox (40) + 3 dimensions x 9 + the
+    per-sample terms of the FP32 Kahan mode (2 + 2 + 5 + 8 + 3) + its finish
+    (LO kinematics 20, three grid coordinates 27, three weight sets 39, two
+    bicubic lookups 78, product 2); 23 wide multiplies.  The stratified hybrid
+    with P = 2 at d = 8 adds 8 x 1.5 + 3 + 9 / 2 = 19.5 to the plain count."""
+    o = bench.ops_per_sample("lo_pdf", 3, "fp32_kahan")
+    assert bench.LO_PDF_FINISH == 166
+    assert o["total"] == 40 + 27 + 20 + 166 and o["mulwide"] == 23 and o["mufu"] == 4
+    s = bench.strat_ops_per_sample("gauss_sym", 8, "fp32_acc64", 2)
+    assert s["total"] == pytest.approx(bench.ops_per_sample("gauss_sym", 8, "fp32_acc64")["total"] + 19.5)
+    assert s["mulwide"] == 48

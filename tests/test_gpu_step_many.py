@@ -72,6 +72,30 @@ def test_step_many_equals_step_on_twins():
         assert V.vegas_get_iteration(a) == V.vegas_get_iteration(b) == 4
 
 
+def test_step_many_on_a_user_stream():
+    """Contexts on a caller's (non-default) stream: back-to-back steps with no
+    host synchronisation, and a read on that stream right after them, see the
+    same results as vegas_step on twins on the default stream (the twin
+    tolerances above)."""
+    V = native()
+    import torch
+    s = torch.cuda.Stream()
+    mix = MIX[:3]
+    many = [_make(V, *m, iid=k, stream=s) for k, m in enumerate(mix)]
+    twins = [_make(V, *m, iid=k) for k, m in enumerate(mix)]
+    for _ in range(4):
+        V.vegas_step_many(many)
+    for _ in range(4):
+        for c in twins:
+            V.vegas_step(c, sync=False)
+    for a, b, m in zip(many, twins, mix):
+        tr, tg = _tols(m[4])
+        ra, rb = V.vegas_result(a), V.vegas_result(b)
+        assert ra["n_iter"] == rb["n_iter"] == 4
+        assert _close(ra["I"], rb["I"], tr) and _close(ra["sigma"], rb["sigma"], tr), (ra, rb)
+        assert np.max(np.abs(V.vegas_get_grid(a) - V.vegas_get_grid(b))) <= tg
+
+
 def test_step_many_first_iteration_matches_oracle():
     V = native()
     fam, d, N, n = "genz_gauss", 6, 40, 200_000
