@@ -952,9 +952,8 @@ vegas_status vegas_set_pdf_grid(vegas_ctx *c, const double *dev_xg, int32_t nx, 
         (reinterpret_cast<uintptr_t>(dev_xg) % alignof(double)) != 0)
         return VEGAS_EINVAL;
     // shared memory: the block's cells and the grid in the path's precision
-    const size_t tsize = c->mode == ACC_F64 ? sizeof(double) : sizeof(float);
-    const size_t smem = sample_smem(c->mode, c->priv ? 1 : 0, c->cfg.n_dim, c->cfg.n_bins) +
-                        static_cast<size_t>(nx + 2) * (nq + 2) * tsize;
+    const size_t smem = pdf_grid_offset(sample_smem(c->mode, c->priv ? 1 : 0, c->cfg.n_dim, c->cfg.n_bins)) +
+                        pdf_grid_bytes(c->mode, nx, nq);
     cudaError_t err;
     const DeviceInfo di = device_info(&err);
     if (err != cudaSuccess) {

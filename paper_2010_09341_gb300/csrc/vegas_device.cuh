@@ -309,20 +309,32 @@ template <class T> __device__ __forceinline__ int grid_cell(T r, int n, T *t) {
 
 // x g(x, Q^2) from a density grid (F_LO_PDF): bicubic Hermite in
 // (log2 x, log2 Q^2) with central-difference tangents.  tbl is the grid padded
-// by one knot on every side, (nx + 2) x (nq + 2) row-major, the padding the
-// linear ghost value 2 f_edge - f_next (which makes the tangent at the first
-// and last knot one-sided); so the 4 x 4 knots around any cell are in the
-// table.  iu / wu: the cell and weights along x, jv / wv along Q^2, pitch =
-// nq + 2.
+// by one knot on every side, the padding the linear ghost value
+// 2 f_edge - f_next (which makes the tangent at the first and last knot
+// one-sided); so the 4 x 4 knots around any cell are in the table.  FP64:
+// (nx + 2) x (nq + 2) knots row-major; FP32: (nx + 2) x (nq + 1) pairs of
+// neighbouring knots (knot (r, c), knot (r, c + 1)), a row's four knots read
+// as two pairs.  iu / wu: the cell and weights along x, jv / wv along Q^2.
 template <class T>
-__device__ __forceinline__ T grid_xg(const T *tbl, int pitch, int iu, const CubicWeights<T> &wu, int jv,
+__device__ __forceinline__ T grid_xg(const T *tbl, int nq, int iu, const CubicWeights<T> &wu, int jv,
                                      const CubicWeights<T> &wv) {
-    const T *r = tbl + iu * pitch + jv;
     T acc[4];
+    if constexpr (sizeof(T) == sizeof(double)) {
+        const int pitch = nq + 2;
+        const T *r = tbl + iu * pitch + jv;
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        const T *row = r + a * pitch;
-        acc[a] = ffma(wv.w3, row[3], ffma(wv.w2, row[2], ffma(wv.w1, row[1], wv.w0 * row[0])));
+        for (int a = 0; a < 4; ++a) {
+            const T *row = r + a * pitch;
+            acc[a] = ffma(wv.w3, row[3], ffma(wv.w2, row[2], ffma(wv.w1, row[1], wv.w0 * row[0])));
+        }
+    } else {
+        const int pitch = nq + 1;
+        const float2 *r = reinterpret_cast<const float2 *>(tbl) + iu * pitch + jv;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const float2 p = r[a * pitch], q = r[a * pitch + 2];
+            acc[a] = ffma(wv.w3, q.y, ffma(wv.w2, q.x, ffma(wv.w1, p.y, wv.w0 * p.x)));
+        }
     }
     return ffma(wu.w3, acc[3], ffma(wu.w2, acc[2], ffma(wu.w1, acc[1], wu.w0 * acc[0])));
 }
@@ -418,8 +430,8 @@ template <int FAM, class T, int MAXD> struct Integrand {
             const int i1 = grid_cell((flog2(x0) - fc.p[0]) * fc.p[1], nx, &t1);
             const int i2 = grid_cell((flog2(x1) - fc.p[0]) * fc.p[1], nx, &t2);
             const CubicWeights<T> wv(tv), w1(t1), w2(t2);
-            const T g1 = grid_xg(tbl, nq + 2, i1, w1, jv, wv);
-            const T g2 = grid_xg(tbl, nq + 2, i2, w2, jv, wv);
+            const T g1 = grid_xg(tbl, nq, i1, w1, jv, wv);
+            const T g2 = grid_xg(tbl, nq, i2, w2, jv, wv);
             const T dm = shat - s1;
             const T den = ffma(dm, dm, s2) * shat * x0 * x1;
             const T val = g1 * g2 * ffma(c, c, T(1)) * frcp(den);

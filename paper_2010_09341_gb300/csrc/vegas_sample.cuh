@@ -134,28 +134,56 @@ __host__ __device__ constexpr size_t sample_smem_bytes(int d, int N) {
             (MODE != ACC_F64 ? sizeof(uint32_t) : 0));  // single-copy fine cells
 }
 
-// F_LO_PDF: the density grid (nx x nq FP64, row-major) copied to t in the
-// path's precision, padded by one knot on every side with the linear ghost
-// values 2 f_edge - f_next (a corner: the ghost of the ghost row); every
+// F_LO_PDF: the density grid (nx x nq FP64, row-major) padded by one knot on
+// every side with the linear ghost values 2 f_edge - f_next (a corner: the
+// ghost of the ghost row); knot (r, c) of the padded grid, 0 <= r < nx + 2,
+// 0 <= c < nq + 2.
+__device__ __forceinline__ double padded_knot(const double *g, int nx, int nq, int r, int c) {
+    // the row (and column) of g and its neighbour the ghost extrapolates from
+    const int ri = min(max(r - 1, 0), nx - 1), rn = r == 0 ? 1 : nx - 2;
+    const int ci = min(max(c - 1, 0), nq - 1), cn = c == 0 ? 1 : nq - 2;
+    const bool gr = r == 0 || r == nx + 1, gc = c == 0 || c == nq + 1;
+    double v = g[ri * nq + ci];
+    if (gr) v = 2.0 * v - g[rn * nq + ci];
+    if (gc) {
+        double w = g[ri * nq + cn];
+        if (gr) w = 2.0 * w - g[rn * nq + cn];
+        v = 2.0 * v - w;
+    }
+    return v;
+}
+
+// Bytes of the staged grid in the path's precision (mode): FP64 keeps the
+// (nx + 2) x (nq + 2) padded knots; FP32 keeps (nx + 2) x (nq + 1) pairs
+// (knot (r, c), knot (r, c + 1)), so that the four knots of a row that a
+// bicubic lookup reads are two 8-byte loads (grid_xg), not four.
+__host__ __device__ constexpr size_t pdf_grid_bytes(int mode, int nx, int nq) {
+    return mode == ACC_F64 ? static_cast<size_t>(nx + 2) * (nq + 2) * sizeof(double)
+                           : static_cast<size_t>(nx + 2) * (nq + 1) * 2 * sizeof(float);
+}
+
+// Offset of the staged grid after `before` bytes of shared memory (16-byte
+// aligned: the FP32 pairs are read as 8-byte vectors).
+__host__ __device__ constexpr size_t pdf_grid_offset(size_t before) { return (before + 15) / 16 * 16; }
+
+// Stages the padded grid into t in the layout of pdf_grid_bytes for T; every
 // thread of the block calls this, the caller synchronises.
 template <class T>
 __device__ __forceinline__ void stage_grid(T *t, const double *g, int nx, int nq) {
-    const int P = nq + 2;
-    const int total = (nx + 2) * P;
-    for (int k = threadIdx.x; k < total; k += blockDim.x) {
-        const int r = k / P, c = k - r * P;
-        // the row (and column) of g and its neighbour the ghost extrapolates from
-        const int ri = min(max(r - 1, 0), nx - 1), rn = r == 0 ? 1 : nx - 2;
-        const int ci = min(max(c - 1, 0), nq - 1), cn = c == 0 ? 1 : nq - 2;
-        const bool gr = r == 0 || r == nx + 1, gc = c == 0 || c == nq + 1;
-        double v = g[ri * nq + ci];
-        if (gr) v = 2.0 * v - g[rn * nq + ci];
-        if (gc) {
-            double w = g[ri * nq + cn];
-            if (gr) w = 2.0 * w - g[rn * nq + cn];
-            v = 2.0 * v - w;
+    if constexpr (sizeof(T) == sizeof(double)) {
+        const int P = nq + 2;
+        for (int k = threadIdx.x; k < (nx + 2) * P; k += blockDim.x) {
+            const int r = k / P, c = k - r * P;
+            t[k] = static_cast<T>(padded_knot(g, nx, nq, r, c));
         }
-        t[k] = static_cast<T>(v);
+    } else {
+        const int P = nq + 1;
+        float2 *t2 = reinterpret_cast<float2 *>(t);
+        for (int k = threadIdx.x; k < (nx + 2) * P; k += blockDim.x) {
+            const int r = k / P, c = k - r * P;
+            t2[k] = make_float2(static_cast<float>(padded_knot(g, nx, nq, r, c)),
+                                static_cast<float>(padded_knot(g, nx, nq, r, c + 1)));
+        }
     }
 }
 
@@ -166,7 +194,7 @@ __device__ __forceinline__ const typename ModeTraits<MODE>::T *stage_pdf(unsigne
                                                                           int d) {
     using T = typename ModeTraits<MODE>::T;
     if (FAM != F_LO_PDF) return nullptr;
-    T *t = reinterpret_cast<T *>(raw + sample_smem_bytes<MODE, PRIV>(d, a.N));
+    T *t = reinterpret_cast<T *>(raw + pdf_grid_offset(sample_smem_bytes<MODE, PRIV>(d, a.N)));
     stage_grid(t, a.pdf, a.pdf_nx, a.pdf_nq);
     return t;
 }
@@ -666,12 +694,14 @@ template <class T> __device__ __forceinline__ void block_scalars(const SampleArg
 }
 
 // Blocks of 512 threads an SM should hold, which sets the registers the
-// compiler may give a thread: the two LO families at 2 (64 registers: their
-// short integrand chains, and the density lookups' shared-memory loads, want
-// the warps; measured 6-8% faster than at one block), every other kernel at 1
-// (up to 128 registers: fewer instructions per sample; the d = 8 families ran
-// 2.4-6.4% faster, d = 12 8%, the FP64 d = 4 iteration of 1e5 samples 14%).
-template <int FAM> constexpr int kSampleMinBlocks = (FAM == F_LO || FAM == F_LO_PDF) ? 2 : 1;
+// compiler may give a thread: the LO toy at 2 (64 registers: its short
+// integrand chain wants the warps; measured 6-8% faster than at one block),
+// every other kernel at 1 (up to 128 registers: fewer instructions per
+// sample; the d = 8 families ran 2.4-6.4% faster, d = 12 8%, the FP64 d = 4
+// iteration of 1e5 samples 14%).  The density-grid family's paired grid
+// (pdf_grid_bytes) leaves room for one block anyway; with 116 registers it ran
+// 7% faster than the single-knot grid at two blocks of 64.
+template <int FAM> constexpr int kSampleMinBlocks = FAM == F_LO ? 2 : 1;
 
 // One integral, samples [a.s_begin, a.s_begin + a.n): each block takes a
 // contiguous range of them.

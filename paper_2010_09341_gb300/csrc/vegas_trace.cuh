@@ -41,7 +41,7 @@ __global__ void trace_kernel(const SampleArgs a, double inv_scale, int32_t *bins
         T *t = reinterpret_cast<T *>(raw);
         stage_grid(t, a.pdf, a.pdf_nx, a.pdf_nq);
         fam.tbl = t;
-        raw += (static_cast<size_t>(a.pdf_nx + 2) * (a.pdf_nq + 2) * sizeof(T) + 15) / 16 * 16;
+        raw += pdf_grid_offset(pdf_grid_bytes(MODE, a.pdf_nx, a.pdf_nq));
     }
     double *hs = h.out ? reinterpret_cast<double *>(raw) : nullptr;
     const int hn = 2 * (h.nb + 2);
