@@ -66,6 +66,35 @@ def test_nonfinite_counted_and_excluded_like_the_oracle(prec, warm, strata):
         assert abs(sigma - math.sqrt(var)) <= 1e-9 * math.sqrt(var)
 
 
+@pytest.mark.parametrize("prec", PRECS)
+def test_fp32_square_overflow_counts_as_nonfinite(prec):
+    """A finite J f whose square exceeds the FP32 range (1e20 where x_0 > 31/32,
+    first iteration, uniform grid: J = 1, no rescale yet): the FP32 modes, whose
+    sums take (J f)^2, count those samples in n_nonfinite and leave them out;
+    the FP64 path keeps them and equals the oracle, which counts none."""
+    V = native()
+    d, N, n = 3, 32, 60_001
+    O.set_user(U.host_function(U.HUGE))
+    ctx = _make(V, U.HUGE, d, N, n, prec)
+    e = O.uniform_edges(d, N)
+    I, sigma, n_ok, n_nf = V.vegas_iterate(ctx)
+    acc = O.iterate(d, N, e, "user", [], 0, 0, 0, n, threads=8)
+    assert acc["n_nonfinite"] == 0
+    if prec == "fp64":
+        Io, _ = O.iteration_result(acc["S1"], acc["S2"], n)
+        assert n_nf == 0 and n_ok == n
+        assert abs(I - Io) <= TOL[prec] * abs(Io), (I, Io)
+    else:
+        _, x, _ = O.trace(d, N, e, "user", [], 0, 0, 0, 0, n, threads=8)
+        huge = int(np.count_nonzero(x[:, 0] > 0.96875))
+        assert 1000 < huge < 3000            # about 1/32 of the samples
+        assert n_nf == huge and n_ok == n - huge
+        # the rest: 1 + x_1 over the samples with x_0 <= 31/32, each weighted by 1
+        keep = x[:, 0] <= 0.96875
+        Io = float(np.sum(1.0 + x[keep, 1])) / (n - huge)
+        assert abs(I - Io) <= TOL[prec] * abs(Io), (I, Io)
+
+
 @pytest.mark.parametrize("strata", [0, -1])
 @pytest.mark.parametrize("prec", PRECS)
 def test_all_nonfinite_iteration_is_left_out(prec, strata):

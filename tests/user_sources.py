@@ -67,6 +67,14 @@ template <class T> __device__ T user_integrand(const T *x, int d, const T *p) {
 }
 """
 
+# finite everywhere, but (J f)^2 exceeds the FP32 range where x_0 > 31/32
+HUGE = r"""
+template <class T> __device__ T user_integrand(const T *x, int d, const T *p) {
+    if (x[0] > T(0.96875)) return T(1e20);
+    return T(1) + x[1];
+}
+"""
+
 # NaN everywhere
 ALL_NAN = r"""
 template <class T> __device__ T user_integrand(const T *x, int d, const T *p) {
