@@ -100,6 +100,33 @@ def test_pdf_iteration_parity_on_shared_grid(prec, strata):
         assert abs(sigma - math.sqrt(var)) <= 1e-9 * math.sqrt(var)
 
 
+@pytest.mark.parametrize("strata", [0, -1])
+@pytest.mark.parametrize("prec", PRECS)
+def test_pdf_odd_cell_count_and_small_odd_grid(prec, strata):
+    """d N = 99 cells (the FP32 cells end 4 bytes past an 8-byte boundary: the
+    density grid after them starts at the next 16-byte boundary) and a 15 x 9
+    knot grid (odd in both directions; the FP32 path's pairs reach the last
+    padded column): the iteration after one refinement equals the oracle's."""
+    V = native()
+    grid = _grid(nx=15, nq=9)
+    N, n = 33, 150_001
+    ctx = _make(V, N, n, prec, grid, strata=strata)
+    V.vegas_step(ctx)
+    e = V.vegas_get_grid(ctx)
+    I, sigma, n_ok, _ = V.vegas_iterate(ctx)
+    p = W.lo_params()
+    if strata:
+        Bt, P, used = V.vegas_get_strata(ctx)
+        acc = O.iterate_strat(3, N, e, "lo_pdf", p, 0, 0, 1, Bt, P, threads=8)
+        Io, var = O.strat_result(acc["S1"], acc["Q"], 2 ** Bt, P)
+    else:
+        acc = O.iterate(3, N, e, "lo_pdf", p, 0, 0, 1, n, threads=8)
+        Io, var = O.iteration_result(acc["S1"], acc["S2"], n)
+    tol = TOL_IT[prec]
+    assert Io != 0.0
+    assert abs(I - Io) <= tol * abs(Io), (I, Io)
+
+
 def test_pdf_full_run_fp64_matches_oracle_every_iteration():
     V = native()
     grid = _grid()
