@@ -250,7 +250,7 @@ __device__ __forceinline__ void sample_range_strat(const BlockState<MODE, PRIV> 
 // Stratified form: hypercubes [a.s_begin, a.s_begin + a.n) of P = a.st.P
 // samples each; each block takes a contiguous range of hypercubes.
 // Blocks per SM as for the plain kernel (kSampleMinBlocks: one, whose threads
-// may use up to 128 registers, except for the LO families); above 8
+// may use up to 128 registers, except for the LO toy); above 8
 // dimensions a block's lane-private cells take most of an SM's shared memory
 // anyway.  At d = 8 one block ran the stratified Gaussian 3.5% faster than
 // two, the oscillatory integral 1% slower.
