@@ -50,7 +50,7 @@ __device__ __noinline__ void batch_range(typename BlockState<MODE, PRIV>::T2 *ta
     rp.hs = hs;
     rp.acc = acc;
     ThreadSums<MODE> ts = *tsp;
-    sample_range<FAM, MODE, MAXD, EXACT, PRIV, (MAXD > 16)>(bs, rp, batch_fc<typename ModeTraits<MODE>::T>(), ts, s0, cnt);
+    sample_range<FAM, MODE, MAXD, EXACT, PRIV, (MAXD > 16), false>(bs, rp, batch_fc<typename ModeTraits<MODE>::T>(), ts, s0, cnt);
     *tsp = ts;
 }
 
