@@ -4,4 +4,5 @@
 namespace vegas {
 const void *sample_kernel_f64_genz_prod(int d, bool priv) { return pick_family<ACC_F64, F_GENZ_PROD>(d, priv); }
 const void *sample_strat_kernel_f64_genz_prod(int d, bool priv) { return pick_strat<ACC_F64, F_GENZ_PROD>(d, priv); }
+const void *sample_kernel_f64_genz_prod_wide(int d) { return pick_family_wide<ACC_F64, F_GENZ_PROD>(d); }
 }  // namespace vegas

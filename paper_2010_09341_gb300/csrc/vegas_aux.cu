@@ -297,6 +297,7 @@ cudaError_t launch_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *ou
 
 template <int MODE>
 static size_t smem_of(int layout, int d, int N) {
+    if (layout == kLayoutWide) return sample_smem_bytes<MODE, kLayoutWide>(d, N);
     return layout == 1 ? sample_smem_bytes<MODE, 1>(d, N)
                        : (layout == 2 ? sample_smem_bytes<MODE, 2>(d, N) : sample_smem_bytes<MODE, 0>(d, N));
 }

@@ -102,11 +102,15 @@ __host__ __device__ inline CombRec comb_result(const CombState &st, bool last_co
 const void *sample_kernel(int mode, int fam, int d, bool priv);
 // Stratified sampling kernel for the same arguments (vegas_sample_strat_kernel).
 const void *sample_strat_kernel(int mode, int fam, int d, bool priv);
+// FP64 sampling kernel with one histogram copy per lane (layout kLayoutWide);
+// nullptr where there is none.
+const void *sample_kernel_wide(int mode, int fam, int d);
 
 inline int tier_of(int d) { return d <= 4 ? 0 : (d <= 8 ? 1 : (d <= 16 ? 2 : 3)); }
 
 // Shared memory of one sampling block in layout 0 (one copy per cell), 1
-// (lane-private copies) or 2 (half as many copies).
+// (lane-private copies), 2 (half as many copies) or kLayoutWide (FP64: one
+// histogram copy per lane).
 size_t sample_smem(int mode, int layout, int d, int N);
 
 // FP32 modes: samples one block may add to its fixed-point histogram cells

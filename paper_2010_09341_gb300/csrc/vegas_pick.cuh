@@ -50,6 +50,23 @@ static const void *pick_family(int d, bool priv) {
     }
 }
 
+// FP64 kernels with one histogram copy per lane (kLayoutWide; the host takes
+// them where the layout fits and an iteration has many samples per block):
+// the generic tiers of 8 and 16 dimensions, the LO toy's tier of 4; none above
+// 16 dimensions, whose cells would not fit.
+template <int MODE, int FAM>
+static const void *pick_family_wide(int d) {
+    static_assert(MODE == ACC_F64, "the wide histogram layout is the FP64 path's");
+    if constexpr (FAM == F_LO) {
+        if (d != 3) return nullptr;
+        return reinterpret_cast<const void *>(&vegas_sample_kernel<FAM, MODE, 4, false, true, true>);
+    } else {
+        if (d <= 8) return reinterpret_cast<const void *>(&vegas_sample_kernel<FAM, MODE, 8, false, true, true>);
+        if (d <= 16) return reinterpret_cast<const void *>(&vegas_sample_kernel<FAM, MODE, 16, false, true, true>);
+        return nullptr;
+    }
+}
+
 // Stratified kernels: as above, exact-dimension kernels for d <= 8 in the
 // FP32 modes with the lane-private layout, generic tiers otherwise.
 template <int MODE, int FAM, int MAXD, bool EXACT>

@@ -120,10 +120,15 @@ template <> struct ModeTraits<ACC_F32_KAHAN> {
 };
 
 // Copies per (dimension, bin) cell of the table entry (TP) and of the
-// histogram cell (HP) in layout PRIV (0, 1 or 2).
+// histogram cell (HP) in layout PRIV: 0 one copy, 1 ModeTraits' copies, 2 half
+// as many, 3 (kLayoutWide, the FP64 path) ModeTraits' table copies and one
+// histogram copy per lane.
+constexpr int kLayoutWide = 3;
 template <int MODE, int PRIV> struct Copies {
-    static constexpr int TP = PRIV == 0 ? 1 : (PRIV == 1 ? ModeTraits<MODE>::TP : ModeTraits<MODE>::TP / 2);
-    static constexpr int HP = PRIV == 0 ? 1 : (PRIV == 1 ? ModeTraits<MODE>::HP : ModeTraits<MODE>::HP / 2);
+    static constexpr int TP = PRIV == 0 ? 1 : (PRIV == 2 ? ModeTraits<MODE>::TP / 2 : ModeTraits<MODE>::TP);
+    static constexpr int HP = PRIV == 0 ? 1
+                                        : (PRIV == 1 ? ModeTraits<MODE>::HP
+                                                     : (PRIV == 2 ? ModeTraits<MODE>::HP / 2 : 32));
 };
 
 template <int MODE, int PRIV>
@@ -725,11 +730,19 @@ template <int FAM> constexpr int kSampleMinBlocks = FAM == F_LO ? 2 : 1;
 
 // One integral, samples [a.s_begin, a.s_begin + a.n): each block takes a
 // contiguous range of them.
-template <int FAM, int MODE, int MAXD, bool EXACT, bool PRIV>
+// WIDEH (FP64 path, layout PRIV = 1 only): one histogram copy per lane
+// (kLayoutWide) instead of one per lane pair, so that no two lanes of a warp
+// update the same FP64 cell and its compare-and-swap loop never retries
+// within a warp (lanes l and l + 16 of a pair hit the same cell with
+// probability 1/N per dimension: 38% of the warp instructions retried at d = 8,
+// N = 50); the flush then sums twice the copies, so the host takes it for
+// iterations of many samples per block only.
+template <int FAM, int MODE, int MAXD, bool EXACT, bool PRIV, bool WIDEH = false>
 __global__ void __launch_bounds__(512, kSampleMinBlocks<FAM>)
 vegas_sample_kernel(const SampleArgs a) {
     pdl_begin();
-    using BS = BlockState<MODE, PRIV>;
+    constexpr int LAY = WIDEH ? kLayoutWide : (PRIV ? 1 : 0);
+    using BS = BlockState<MODE, LAY>;
     using T = typename BS::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int d = EXACT ? MAXD : a.d;
@@ -737,7 +750,7 @@ vegas_sample_kernel(const SampleArgs a) {
     bs.carve(smem_raw, d * a.N);
     bs.stage(a.table);
     RangeParams<T> rp;
-    rp.aux = stage_pdf<FAM, MODE, PRIV>(smem_raw, a, d);
+    rp.aux = stage_pdf<FAM, MODE, LAY>(smem_raw, a, d);
     rp.d = d;
     rp.N = a.N;
     rp.key0 = a.key0;
@@ -756,10 +769,10 @@ vegas_sample_kernel(const SampleArgs a) {
     const long long hi = min(a.n, lo + per);
     ThreadSums<MODE> ts;
     if (hi > lo)
-        sample_range<FAM, MODE, MAXD, EXACT, PRIV>(bs, rp, consts<T>(a), ts,
+        sample_range<FAM, MODE, MAXD, EXACT, LAY>(bs, rp, consts<T>(a), ts,
                                                    static_cast<unsigned long long>(a.s_begin + lo),
                                                    static_cast<int>(hi - lo));
-    flush_block<MODE, PRIV>(bs, ts, rp.hs, a.acc, a.n_nonfinite, nullptr, true);
+    flush_block<MODE, LAY>(bs, ts, rp.hs, a.acc, a.n_nonfinite, nullptr, true);
 }
 
 }  // namespace vegas
