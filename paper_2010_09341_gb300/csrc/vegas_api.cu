@@ -373,13 +373,17 @@ static vegas_status create_impl(const vegas_config *cfg, const vegas_integrand *
     const void *fn = user ? jit.sample : sample_kernel(mode, itg->family, d, priv);
     if (!fn) return VEGAS_EINVAL;
     // FP64: one histogram copy per lane (no compare-and-swap retries within a
-    // warp) where the cells fit and an iteration has enough samples per block
-    // for the retries it saves to outweigh the flush's second set of copies
+    // warp) where the cells fit and a launch has enough samples per block for
+    // the retries it saves to outweigh the flush's second set of copies
     // (measured at d = 4..12, N = 50: 4.6-6% faster at 1e7 samples, 4.5%
-    // slower at 1e5; the two balance near 3e5).  Not for the density-grid
-    // family, whose grid sits after the cells in the stratified kernel's layout.
+    // slower at 1e5; the two balance near 3e5).  Every launch flushes, so the
+    // samples per launch count (events_limit splits an iteration).  Not for the
+    // density-grid family, whose grid sits after the cells in the stratified
+    // kernel's layout.
     constexpr long long kWideMinEvents = 1000000;
-    if (!user && priv && mode == ACC_F64 && itg->family != VEGAS_F_LO_PDF && cfg->n_events >= kWideMinEvents) {
+    const long long per_launch =
+        cfg->events_limit > 0 ? std::min<long long>(cfg->events_limit, cfg->n_events) : cfg->n_events;
+    if (!user && priv && mode == ACC_F64 && itg->family != VEGAS_F_LO_PDF && per_launch >= kWideMinEvents) {
         const void *fw = sample_kernel_wide(mode, itg->family, d);
         const size_t smem_w = sample_smem(mode, kLayoutWide, d, N);
         if (fw && smem_w <= budget) {
